@@ -1,0 +1,365 @@
+"""Seeded synthetic inputs for the Hadamard-spectral-code shading path.
+
+This module is shared by the CPU oracle, the tests and the benchmark.  It holds
+no arithmetic of the method itself (no encoding, shading, decoding or colour
+science): only seeded random draws and the closed-form spectra that stand in
+for the paper's measured data.  The paper trains and renders with Munsell
+reflectances, LSPDD lamp spectra and Mitsuba scenes (Sec. 3.4, Sec. 5.1), none
+of which is available here; every array below is a synthetic stand-in with the
+shapes and value ranges those data have.
+
+Conventions
+-----------
+* Spectra are sampled on a uniform grid ``lambda_i = lambda0 + i * dlambda``.
+* Every array handed to a device is float32 (int32 for material indices); the
+  oracle reads the same float32 values and widens them to float64, so both
+  sides start from bit-identical inputs.
+* All randomness flows from ``numpy.random.SeedSequence(seed)``; each consumer
+  takes its own spawned stream so adding a draw in one place does not shift
+  another.
+"""
+from __future__ import annotations
+
+import math
+import os
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+MASTER_SEED = 2602_18741
+
+# Wavelength grids (lambda0 [nm], dlambda [nm], n).
+GRID_31 = (400.0, 10.0, 31)   # 400..700 nm at 10 nm
+GRID_81 = (380.0, 5.0, 81)    # 380..780 nm at 5 nm
+
+CODEC_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "codecs")
+
+
+def streams(seed: int, count: int) -> list:
+    """``count`` independent numpy Generators spawned from one seed."""
+    return [np.random.default_rng(s) for s in np.random.SeedSequence(seed).spawn(count)]
+
+
+def grid(lambda0: float, dlambda: float, n: int) -> np.ndarray:
+    """Wavelength samples in nm (float64)."""
+    return lambda0 + dlambda * np.arange(n, dtype=np.float64)
+
+
+# ----------------------------------------------------------------------------
+# Spectra
+# ----------------------------------------------------------------------------
+
+def smooth_reflectances(rng, lam: np.ndarray, count: int) -> np.ndarray:
+    """Sum of three Gaussians (centre U[400,700] nm, std U[20,80] nm, amplitude
+    U[0,1]) clipped to [0, 1]: a smooth, Munsell-like reflectance."""
+    c = rng.uniform(400.0, 700.0, size=(count, 3, 1))
+    w = rng.uniform(20.0, 80.0, size=(count, 3, 1))
+    a = rng.uniform(0.0, 1.0, size=(count, 3, 1))
+    s = (a * np.exp(-0.5 * ((lam[None, None, :] - c) / w) ** 2)).sum(axis=1)
+    return np.clip(s, 0.0, 1.0)
+
+
+def sawtooth_reflectances(rng, lam: np.ndarray, count: int) -> np.ndarray:
+    """High-frequency reflectances: clip(a + b*frac((lambda - phi)/period), 0, 1)
+    with period U[10,40] nm, phase U[0,period], a U[0,0.3], b U[0.4,0.7]."""
+    period = rng.uniform(10.0, 40.0, size=(count, 1))
+    phi = rng.uniform(0.0, 1.0, size=(count, 1)) * period
+    a = rng.uniform(0.0, 0.3, size=(count, 1))
+    b = rng.uniform(0.4, 0.7, size=(count, 1))
+    t = (lam[None, :] - phi) / period
+    return np.clip(a + b * (t - np.floor(t)), 0.0, 1.0)
+
+
+# SI-exact constants (2019 SI definitions).
+_H = 6.62607015e-34
+_C = 299792458.0
+_KB = 1.380649e-23
+
+
+def blackbody(lam: np.ndarray, temperature_k) -> np.ndarray:
+    """Planck radiance at the grid wavelengths, normalised to unit peak on the
+    grid (the paper normalises its lights to unit peak, Sec. 3.4)."""
+    t = np.atleast_1d(np.asarray(temperature_k, dtype=np.float64))[:, None]
+    lm = lam[None, :] * 1e-9
+    b = (2.0 * _H * _C ** 2) / (lm ** 5 * np.expm1(_H * _C / (lm * _KB * t)))
+    return b / b.max(axis=1, keepdims=True)
+
+
+def narrowband(lam: np.ndarray, mu, sigma) -> np.ndarray:
+    """Unit-peak Gaussian band(s), standard deviation ``sigma`` nm."""
+    mu = np.atleast_1d(np.asarray(mu, dtype=np.float64))[:, None]
+    sigma = np.atleast_1d(np.asarray(sigma, dtype=np.float64))[:, None]
+    return np.exp(-0.5 * ((lam[None, :] - mu) / sigma) ** 2)
+
+
+# ----------------------------------------------------------------------------
+# Geometry
+# ----------------------------------------------------------------------------
+
+def _unit_hemisphere_z(rng, count: int) -> np.ndarray:
+    z = rng.uniform(0.0, 1.0, size=count)
+    phi = rng.uniform(0.0, 2.0 * math.pi, size=count)
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    return np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+
+
+def _unit_sphere(rng, count: int) -> np.ndarray:
+    z = rng.uniform(-1.0, 1.0, size=count)
+    phi = rng.uniform(0.0, 2.0 * math.pi, size=count)
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    return np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+
+
+def _normalize_f32(v: np.ndarray) -> np.ndarray:
+    v = v / np.linalg.norm(v, axis=1, keepdims=True)
+    return v.astype(np.float32)
+
+
+@dataclass
+class GBuffer:
+    """Per-pixel shading points: unit normal (P,3), position (P,3), material (P,)."""
+    normal: np.ndarray
+    pos: np.ndarray
+    mat: np.ndarray
+
+    @property
+    def pixels(self) -> int:
+        return int(self.mat.shape[0])
+
+
+def gbuffers(rng, pixels: int, n_mat: int, secondary: bool):
+    """Primary G-buffer (normals uniform on the +z hemisphere, positions
+    U[0,1]^3, material index uniform) and, optionally, a secondary G-buffer:
+    the point one indirect bounce reaches, at U[0,1]^3 with a normal drawn
+    around the direction back to the primary point, so most pairs face each
+    other."""
+    n1 = _normalize_f32(_unit_hemisphere_z(rng, pixels))
+    x1 = rng.uniform(0.0, 1.0, size=(pixels, 3)).astype(np.float32)
+    m1 = rng.integers(0, n_mat, size=pixels, dtype=np.int32)
+    g1 = GBuffer(n1, x1, m1)
+    if not secondary:
+        return g1, None
+    x2 = rng.uniform(0.0, 1.0, size=(pixels, 3)).astype(np.float32)
+    back = x1.astype(np.float64) - x2.astype(np.float64)
+    back /= np.maximum(np.linalg.norm(back, axis=1, keepdims=True), 1e-6)
+    n2 = _normalize_f32(back + 0.8 * _unit_sphere(rng, pixels))
+    m2 = rng.integers(0, n_mat, size=pixels, dtype=np.int32)
+    return g1, GBuffer(n2, x2, m2)
+
+
+def light_positions(rng, count: int):
+    """Point lights above the unit cube: x, y U[-0.5,1.5], z U[1.5,2.5]
+    (so every light is at least 0.5 from every shading point); intensity
+    U[0.5,2]."""
+    pos = np.stack([rng.uniform(-0.5, 1.5, size=count),
+                    rng.uniform(-0.5, 1.5, size=count),
+                    rng.uniform(1.5, 2.5, size=count)], axis=1).astype(np.float32)
+    inten = rng.uniform(0.5, 2.0, size=count).astype(np.float32)
+    return pos, inten
+
+
+# ----------------------------------------------------------------------------
+# Frames
+# ----------------------------------------------------------------------------
+
+@dataclass
+class Frame:
+    """One G-buffer frame with its spectral assets (all float32 / int32)."""
+    width: int
+    height: int
+    grid: tuple                       # (lambda0, dlambda, n)
+    mat_spectra: np.ndarray           # (m, n) reflectances in [0,1]
+    light_spd: np.ndarray             # (L, n) unit-peak SPDs
+    light_pos: np.ndarray             # (L, 3)
+    light_intensity: np.ndarray       # (L,)
+    g1: GBuffer
+    g2: Optional[GBuffer] = None
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def pixels(self) -> int:
+        return self.width * self.height
+
+    @property
+    def n(self) -> int:
+        return int(self.grid[2])
+
+    @property
+    def lights(self) -> int:
+        return int(self.light_pos.shape[0])
+
+    @property
+    def evals(self) -> int:
+        """Pixel-light evaluations: one (shading point, light) pair each."""
+        return self.pixels * self.lights * (2 if self.g2 is not None else 1)
+
+
+def make_frame(seed: int, width: int, height: int, grid_spec=GRID_81,
+               n_smooth: int = 256, n_saw: int = 32,
+               lights: int = 64, secondary: bool = True,
+               spd_kinds=None) -> Frame:
+    """General seeded frame.  Lights: the first half blackbodies at U[2000,
+    10000] K, the second half Gaussian bands (centre U[400,700] nm, std
+    U[5,20] nm), unless ``spd_kinds`` gives explicit SPDs."""
+    r_geo, r_mat, r_light, r_spd = streams(seed, 4)
+    lam = grid(*grid_spec)
+    mats = np.concatenate([smooth_reflectances(r_mat, lam, n_smooth),
+                           sawtooth_reflectances(r_mat, lam, n_saw)], axis=0)
+    if spd_kinds is not None:
+        spd = spd_kinds(lam)
+        lights = spd.shape[0]
+    else:
+        n_bb = lights // 2
+        n_nb = lights - n_bb
+        spd = np.concatenate([
+            blackbody(lam, r_spd.uniform(2000.0, 10000.0, size=n_bb)),
+            narrowband(lam, r_spd.uniform(400.0, 700.0, size=n_nb),
+                       r_spd.uniform(5.0, 20.0, size=n_nb))], axis=0)
+    lpos, linten = light_positions(r_light, lights)
+    g1, g2 = gbuffers(r_geo, width * height, mats.shape[0], secondary)
+    return Frame(width, height, tuple(grid_spec), mats.astype(np.float32),
+                 spd.astype(np.float32), lpos, linten, g1, g2)
+
+
+def _config1_spds(lam):
+    return np.concatenate([blackbody(lam, [2700.0, 6500.0]),
+                           narrowband(lam, [450.0, 610.0], [15.0, 15.0])], axis=0)
+
+
+def frame_config1(seed: int = MASTER_SEED) -> Frame:
+    """256x256, n=31 (400-700 nm @ 10 nm), 16 smooth materials, 4 lights
+    (blackbody 2700 K and 6500 K, Gaussian bands of std 15 nm at 450 and
+    610 nm), direct lighting only."""
+    f = make_frame(seed, 256, 256, GRID_31, n_smooth=16, n_saw=0,
+                   secondary=False, spd_kinds=_config1_spds)
+    f.meta["name"] = "256x256 n=31 L=4 direct"
+    return f
+
+
+def frame_config2(seed: int = MASTER_SEED + 2, width: int = 1920, height: int = 1080) -> Frame:
+    """1920x1080, n=81 (380-780 nm @ 5 nm), 256 smooth + 32 saw-tooth
+    materials, 64 lights (32 blackbody, 32 Gaussian bands), primary plus one
+    indirect bounce from a secondary G-buffer."""
+    f = make_frame(seed, width, height, GRID_81, 256, 32, 64, True)
+    f.meta["name"] = f"{width}x{height} n=81 L=64 direct+indirect"
+    return f
+
+
+def frame_config3(seed: int = MASTER_SEED + 3) -> Frame:
+    """3840x2160 with the 1920x1080 frame's scene model."""
+    f = make_frame(seed, 3840, 2160, GRID_81, 256, 32, 64, True)
+    f.meta["name"] = "3840x2160 n=81 L=64 direct+indirect"
+    return f
+
+
+# ----------------------------------------------------------------------------
+# Codec training set and stored codecs
+# ----------------------------------------------------------------------------
+
+@dataclass
+class TrainingSet:
+    R: np.ndarray        # (N_R, n) reflectances
+    L: np.ndarray        # (N_L, n) unit-peak lights
+    pair_r: np.ndarray   # (P,) index into R
+    pair_l: np.ndarray   # (P,) index into L
+    pair_scale: np.ndarray  # (P,) light scale augmentation U[0.5, 1]
+
+
+def training_set(grid_spec, seed: int = MASTER_SEED + 100, n_smooth: int = 1024,
+                 n_saw: int = 128, n_bb: int = 256, n_nb: int = 256,
+                 pairs: int = 4096) -> TrainingSet:
+    """Seeded stand-in for the paper's training spectra (Sec. 3.4): smooth and
+    saw-tooth reflectances, blackbody (2000-10000 K) and narrow-band (std 5-20
+    nm) unit-peak lights, random reflectance-light pairs with a light scale
+    augmentation U[0.5, 1]."""
+    r_ref, r_light, r_pair = streams(seed, 3)
+    lam = grid(*grid_spec)
+    R = np.concatenate([smooth_reflectances(r_ref, lam, n_smooth),
+                        sawtooth_reflectances(r_ref, lam, n_saw)], axis=0)
+    L = np.concatenate([
+        blackbody(lam, r_light.uniform(2000.0, 10000.0, size=n_bb)),
+        narrowband(lam, r_light.uniform(lam[0], lam[-1], size=n_nb),
+                   r_light.uniform(5.0, 20.0, size=n_nb))], axis=0)
+    pr = r_pair.integers(0, R.shape[0], size=pairs)
+    pl = r_pair.integers(0, L.shape[0], size=pairs)
+    ps = r_pair.uniform(0.5, 1.0, size=pairs)
+    return TrainingSet(R, L, pr, pl, ps)
+
+
+def codec_path(k: int, n: int) -> str:
+    return os.path.join(CODEC_DIR, f"codec_k{k}_n{n}.npz")
+
+
+def load_codec(k: int, n: int):
+    """Stored (E, D) for code length k over n samples, float32 (k,n) and (n,k).
+    The files are written by the oracle's codec-fitting script."""
+    with np.load(codec_path(k, n)) as z:
+        return z["E"].astype(np.float32), z["D"].astype(np.float32)
+
+
+# ----------------------------------------------------------------------------
+# Batched frames and request streams
+# ----------------------------------------------------------------------------
+
+def batched_frames(seed: int = MASTER_SEED + 4, count: int = 64, min_side: int = 256,
+                   max_side: int = 2048, min_lights: int = 4, max_lights: int = 256,
+                   ks=(6, 9), grids=(GRID_31, GRID_81), secondary: bool = False):
+    """Frames of uneven size for a batched launch: W, H independent uniform
+    integers in [min_side, max_side], L uniform in [min_lights, max_lights],
+    k and n uniform over the given choices; each frame carries its own codec,
+    a stored base codec times a seeded multiplicative jitter U[0.9, 1.1]."""
+    (r,) = streams(seed, 1)
+    out = []
+    for i in range(count):
+        w = int(r.integers(min_side, max_side + 1))
+        h = int(r.integers(min_side, max_side + 1))
+        L = int(r.integers(min_lights, max_lights + 1))
+        k = int(ks[r.integers(0, len(ks))])
+        g = grids[r.integers(0, len(grids))]
+        fseed = int(r.integers(0, 2**31 - 1))
+        f = make_frame(fseed, w, h, g, n_smooth=48, n_saw=16, lights=L, secondary=secondary)
+        E, D = load_codec(k, g[2])
+        jE = r.uniform(0.9, 1.1, size=E.shape).astype(np.float32)
+        jD = r.uniform(0.9, 1.1, size=D.shape).astype(np.float32)
+        f.meta.update(k=k, E=(E * jE).astype(np.float32), D=(D * jD).astype(np.float32),
+                      name=f"batch[{i}] {w}x{h} L={L} k={k} n={g[2]}")
+        out.append(f)
+    return out
+
+
+SERVE_SIZES = ((512, 512), (1024, 1024), (1920, 1080), (2048, 2048), (3840, 2160))
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival_s: float
+    width: int
+    height: int
+    k: int
+    n: int
+    lights: int
+    scene: int
+    seed: int
+
+
+def request_stream(seed: int = MASTER_SEED + 5, rate_hz: float = 200.0,
+                   duration_s: float = 30.0, sizes=SERVE_SIZES, ks=(6, 9),
+                   ns=(31, 81), min_lights: int = 16, max_lights: int = 128,
+                   scenes: int = 8):
+    """Poisson arrivals (exponential gaps, mean 1/rate) of render-plus-decode
+    requests over ``duration_s``; size, k, n, light count and scene uniform."""
+    (r,) = streams(seed, 1)
+    t = 0.0
+    out = []
+    while True:
+        t += float(r.exponential(1.0 / rate_hz))
+        if t >= duration_s:
+            break
+        w, h = sizes[r.integers(0, len(sizes))]
+        out.append(Request(len(out), t, int(w), int(h), int(ks[r.integers(0, len(ks))]),
+                           int(ns[r.integers(0, len(ns))]),
+                           int(r.integers(min_lights, max_lights + 1)),
+                           int(r.integers(0, scenes)), int(r.integers(0, 2**31 - 1))))
+    return out

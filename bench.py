@@ -1,0 +1,521 @@
+"""Benchmark of the Hadamard-spectral-code shading path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hsc|reference]
+
+Workload (one step = one frame): a 1920x1080 G-buffer with a secondary
+G-buffer for one indirect bounce, n = 81 samples (380-780 nm at 5 nm), k = 6,
+64 point lights (32 blackbody, 32 narrow-band), 288 materials; seeded
+synthetic inputs.  The latent frame is: encode materials and lights, fused
+k-channel shading writing the latent image and XYZ, decode to 8-bit sRGB.
+``value`` is pixel-light evaluations per second of that frame (2 x 64 per
+pixel).  The other parts of the metric are measured in the same run on the
+same frame: n-sample spectral shading (the comparison), the k/3-pass form,
+k = 9, the FP32 and tensor-core spectral decodes (GB/s) and the frame-time
+percentiles.  L2 is flushed (256 MB write) before every timed iteration.
+
+``--impl reference`` times the FP64 CPU oracle on a band of rows of the same
+frame (the only reference implementation this project has).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import hsc_inputs as hi  # noqa: E402
+
+METRIC = "pixel-light evals/s latent vs n-sample spectral; decode GB/s; p50/p99 frame ms"
+UNIT = "pixel-light evals/s"
+WORKLOAD = "1920x1080 G-buffer + secondary bounce, n=81, k=6, 64 lights, 288 materials: latent frame (encode, fused shade + XYZ, sRGB8)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="hsc", choices=["hsc", "reference"])
+    ap.add_argument("--k", type=int, default=6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-rows", action="store_true", help="skip the secondary rows (spectral, passes, decodes)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- oracle leg
+
+def oracle_rate(seconds: float, k: int, threads: int = 1, max_rows: int = 1080):
+    """Run the FP64 oracle's latent frame (encode, shading, decode to XYZ) on
+    consecutive 32-row bands of the 1920x1080 frame in a child process with
+    ``threads`` BLAS/OpenMP threads until ``seconds`` elapse; returns
+    (evals per second, rows done, seconds)."""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = str(threads)
+    code = (
+        "import sys, time, json, numpy as np\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "import hsc_inputs as hi\n"
+        "from oracle import cmf, shade\n"
+        "f = hi.frame_config2()\n"
+        f"E, D = hi.load_codec({k}, 81)\n"
+        "T = cmf.cmf_weights(*f.grid)\n"
+        "W = f.width\n"
+        "band = 32\n"
+        "rows = 0; evals = 0\n"
+        "t0 = time.perf_counter()\n"
+        f"while rows < {max_rows} and time.perf_counter() - t0 < {seconds}:\n"
+        "    idx = np.arange(rows * W, (rows + band) * W)\n"
+        "    g1 = hi.GBuffer(f.g1.normal[idx], f.g1.pos[idx], f.g1.mat[idx])\n"
+        "    g2 = hi.GBuffer(f.g2.normal[idx], f.g2.pos[idx], f.g2.mat[idx])\n"
+        "    sf = hi.Frame(len(idx), 1, f.grid, f.mat_spectra, f.light_spd, f.light_pos, f.light_intensity, g1, g2)\n"
+        "    z = shade.shade_latent(sf, E.astype(np.float64))\n"
+        "    xyz = shade.decode_xyz(z, D.astype(np.float64), T)\n"
+        "    rows += band; evals += sf.evals\n"
+        "dt = time.perf_counter() - t0\n"
+        "print(json.dumps({'rows': rows, 'evals': evals, 'seconds': dt}))\n")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle leg failed: " + r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["evals"] / d["seconds"], d["rows"], d["seconds"]
+
+
+# --------------------------------------------------------------------------- GPU leg
+
+def run_hsc(args, rank: int, world: int):
+    import torch
+    import torch.distributed as dist
+    import paper_2602_18741_gb300 as hsc
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    ctx = hsc.Context(dev.index)
+    stream = torch.cuda.current_stream()
+    k = args.k
+
+    f = hi.frame_config2(seed=hi.MASTER_SEED + 2 + rank)
+    E, D = hi.load_codec(k, 81)
+
+    def t(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    g1 = hsc.GBuffer(t(f.g1.normal), t(f.g1.pos), t(f.g1.mat))
+    g2 = hsc.GBuffer(t(f.g2.normal), t(f.g2.pos), t(f.g2.mat))
+    lights = hsc.Lights(t(f.light_pos), t(f.light_intensity))
+    mats, spd = t(f.mat_spectra), t(f.light_spd)
+    Ed, Dd = t(E), t(D)
+    P = f.pixels
+    T = torch.empty(3, 81, device=dev)
+    hsc.hsc_cmf_weights(ctx, 81, f.grid[0], f.grid[1], T)
+    M = torch.empty(3, k, device=dev)
+    hsc.hsc_fold_xyz(ctx, T, Dd, M)
+    zm = torch.empty(mats.shape[0], k, device=dev)
+    zl = torch.empty(spd.shape[0], k, device=dev)
+    lat = torch.empty(P, k, device=dev)
+    xyz = torch.empty(P, 3, device=dev)
+    rgb = torch.empty(P, 3, device=dev, dtype=torch.uint8)
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)
+    evals = f.evals
+    gpu_launches_per_step = 4
+
+    def frame(ev=None):
+        hsc.hsc_encode(ctx, Ed, mats, zm)
+        hsc.hsc_encode(ctx, Ed, spd, zl)
+        if ev is not None:
+            ev[0].record(stream)
+        hsc.hsc_shade_latent(ctx, g1, g2, zm, lights, zl, hsc.HSC_FUSED, lat, xyz_out=xyz, M_xyz=M)
+        if ev is not None:
+            ev[1].record(stream)
+        hsc.hsc_decode_xyz(ctx, lat, M, None, srgb8_out=rgb)
+
+    def timed(fn, steps, warmup, inner_events=False):
+        """Per-iteration device times (ms) with an L2 flush before each."""
+        for _ in range(warmup):
+            flush.zero_()
+            fn(None) if inner_events else fn()
+        torch.cuda.synchronize()
+        outer, inner = [], []
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ie = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) if inner_events else None
+            a.record(stream)
+            fn(ie) if inner_events else fn()
+            b.record(stream)
+            evs.append((a, b, ie))
+        torch.cuda.synchronize()
+        for a, b, ie in evs:
+            outer.append(a.elapsed_time(b))
+            if ie is not None:
+                inner.append(ie[0].elapsed_time(ie[1]))
+        return outer, inner
+
+    # ---------------- main timed region
+    for _ in range(args.warmup):
+        flush.zero_()
+        frame()
+    torch.cuda.synchronize()
+    hsc.hsc_sync(ctx)
+    clocks = ClockSampler(dev.index) if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    wall0 = time.perf_counter()
+    per_step, shade_ms = timed(frame, args.steps, 0, inner_events=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    hsc.hsc_sync(ctx)
+    total_ms = sum(per_step)
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    value = world * evals * args.steps / (total_ms * 1e-3)
+
+    result = None
+    if rank == 0:
+        rows = {}
+        if not args.no_rows:
+            rows = secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T, Dd, zm, zl, lat,
+                                  timed, flush)
+        clk = clocks.stop() if clocks else None
+        # roofline of the dominant kernel: the fused shading launch
+        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_mhz = _peak_sm_mhz()
+        ops_per_eval = 14 + k          # 13 FP32 geometry ops + 1 MUFU + k FMAs
+        ops = evals * ops_per_eval
+        shade_avg_s = statistics.mean(shade_ms) * 1e-3
+        achieved = ops / shade_avg_s / 1e12
+        peak = sm_count * 128 * peak_mhz * 1e6 / 1e12
+        roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
+                    "frac": round(achieved / peak, 4), "traffic": _traffic_from_profile(),
+                    "kernel": "shade_codes_kernel<6,PPT,true> (fused latent shade + XYZ)",
+                    "ops_per_eval": ops_per_eval, "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x {peak_mhz:.0f} MHz"}
+        e2e = e2e_leg(args, hsc, ctx, f, dev, stream, Ed, M, evals)
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            rate, nrows, secs = oracle_rate(args.cpu_seconds, k, threads=1)
+            cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"FP64 NumPy oracle latent frame (encode, shading, XYZ decode) on the first {nrows} rows "
+                             f"of the same 1920x1080 frame ({secs:.1f} s, one thread)"}
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded G-buffers, spectra, lights)",
+            "config": {"workload": WORKLOAD, "pixels": f.pixels, "lights": f.lights, "k": k, "n": 81,
+                       "evals_per_step": evals, "l2": "flushed before every timed step (256 MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "frame_ms": {"p50": _pct(per_step, 50), "p99": _pct(per_step, 99), "min": min(per_step)},
+            "gpu_launches": gpu_launches_per_step * args.steps,
+            "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "rows": rows,
+            "wall_s_timed_region": round(wall, 4),
+        }
+    ctx.close()
+    return result
+
+
+def _pct(xs, q):
+    v = sorted(xs)
+    return v[max(int(math.ceil(q / 100.0 * len(v))) - 1, 0)]
+
+
+def _peak_sm_mhz():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh).get("sm_max_mhz", 2070.0))
+    except (OSError, ValueError):
+        return 2070.0
+
+
+def _traffic_from_profile():
+    """DRAM bytes per launch of the fused shading kernel from the committed
+    ncu summary (profiles/shade_codes_fused_1080p.txt), or None."""
+    p = os.path.join(ROOT, "profiles", "shade_codes_fused_1080p.json")
+    try:
+        with open(p) as fh:
+            return json.load(fh).get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        return None
+
+
+def secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T, Dd, zm, zl, lat, timed, flush):
+    import torch
+    P = f.pixels
+    evals = f.evals
+    K, W = args.steps, args.warmup
+    rows = {}
+    xyz_s = torch.empty(P, 3, device=dev)
+    xyz_l = torch.empty(P, 3, device=dev)
+
+    def spectral():
+        hsc.hsc_shade_spectral(ctx, g1, g2, mats, lights, spd, T, xyz_s)
+
+    ms, _ = timed(spectral, K, W)
+    spec_ms = statistics.mean(ms)
+    rows["spectral_n81"] = {"ms": spec_ms, "evals_per_s": evals / (spec_ms * 1e-3),
+                            "ops_per_eval": 14 + 81}
+
+    Mk = _M(hsc, ctx, T, Dd)
+
+    def fused():
+        hsc.hsc_shade_latent(ctx, g1, g2, zm, lights, zl, hsc.HSC_FUSED, lat, xyz_out=xyz_l, M_xyz=Mk)
+
+    ms, _ = timed(fused, K, W)
+    fused_ms = statistics.mean(ms)
+    rows[f"latent_fused_k{args.k}_xyz"] = {"ms": fused_ms, "evals_per_s": evals / (fused_ms * 1e-3),
+                                            "ops_per_eval": 14 + args.k}
+    rows["speedup_latent_fused_vs_spectral"] = spec_ms / fused_ms
+
+    lat_p = torch.empty_like(lat)
+    xyz_p = torch.empty(P, 3, device=dev)
+    hsc.hsc_reserve(ctx, hsc.hsc_shade_latent_scratch_bytes(P, args.k, hsc.HSC_PASSES, hsc.HSC_F32))
+
+    def passes():
+        hsc.hsc_shade_latent(ctx, g1, g2, zm, lights, zl, hsc.HSC_PASSES, lat_p, xyz_out=xyz_p, M_xyz=Mk)
+
+    ms, _ = timed(passes, K, W)
+    pms = statistics.mean(ms)
+    rows[f"latent_passes_k{args.k}_xyz"] = {"ms": pms, "evals_per_s": evals / (pms * 1e-3),
+                                             "bit_identical_to_fused": bool(torch.equal(lat_p, lat))}
+    rows["speedup_latent_passes_vs_spectral"] = spec_ms / pms
+
+    # k = 9
+    E9, D9 = hi.load_codec(9, 81)
+    E9d, D9d = torch.from_numpy(E9).to(dev), torch.from_numpy(D9).to(dev)
+    zm9 = torch.empty(mats.shape[0], 9, device=dev)
+    zl9 = torch.empty(spd.shape[0], 9, device=dev)
+    hsc.hsc_encode(ctx, E9d, mats, zm9)
+    hsc.hsc_encode(ctx, E9d, spd, zl9)
+    M9 = torch.empty(3, 9, device=dev)
+    hsc.hsc_fold_xyz(ctx, T, D9d, M9)
+    lat9 = torch.empty(P, 9, device=dev)
+
+    def fused9():
+        hsc.hsc_shade_latent(ctx, g1, g2, zm9, lights, zl9, hsc.HSC_FUSED, lat9, xyz_out=xyz_l, M_xyz=M9)
+
+    ms, _ = timed(fused9, K, W)
+    f9 = statistics.mean(ms)
+    rows["latent_fused_k9_xyz"] = {"ms": f9, "evals_per_s": evals / (f9 * 1e-3), "ops_per_eval": 23}
+    rows["speedup_latent_fused_k9_vs_spectral"] = spec_ms / f9
+
+    # decode to spectra (FP32 CUDA cores): P x 81 float32 out
+    spec_out = torch.empty(P, 81, device=dev)
+
+    def dec():
+        hsc.hsc_decode_spectra(ctx, lat, Dd, spec_out)
+
+    ms, _ = timed(dec, K, W)
+    dms = statistics.mean(ms)
+    dbytes = P * (args.k * 4 + 81 * 4)
+    rows["decode_spectra_f32"] = {"ms": dms, "GB_per_s": dbytes / (dms * 1e-3) / 1e9,
+                                  "Mpx_per_s": P / (dms * 1e-3) / 1e6, "bytes": dbytes}
+
+    xyz_only = torch.empty(P, 3, device=dev)
+
+    def decx():
+        hsc.hsc_decode_xyz(ctx, lat, Mk, xyz_only)
+
+    ms, _ = timed(decx, K, W)
+    xms = statistics.mean(ms)
+    xbytes = P * (args.k * 4 + 12)
+    rows["decode_xyz_f32"] = {"ms": xms, "GB_per_s": xbytes / (xms * 1e-3) / 1e9, "bytes": xbytes}
+
+    # Delta E 2000 of the latent render against the spectral one
+    st = torch.zeros(8, device=dev, dtype=torch.float64)
+    fused()
+    spectral()
+
+    def de():
+        hsc.hsc_delta_e(ctx, xyz_l, xyz_s, T, st)
+
+    fused()
+    ms, _ = timed(de, K, W)
+    hsc.hsc_sync(ctx)
+    s = st.cpu().numpy()
+    rows["delta_e_latent_vs_spectral"] = {"ms": statistics.mean(ms), "de2000_mean": float(s[0]),
+                                          "de2000_p95": float(s[1]), "de94_mean": float(s[2]),
+                                          "de76_mean": float(s[3])}
+    hsc.hsc_sync(ctx)
+    return rows
+
+
+def _M(hsc, ctx, T, Dd):
+    import torch
+    k = Dd.shape[1]
+    M = torch.empty(3, k, device=Dd.device)
+    hsc.hsc_fold_xyz(ctx, T, Dd, M)
+    return M
+
+
+def e2e_leg(args, hsc, ctx, f, dev, stream, Ed, M, evals):
+    """Same latent frame through the public API with host buffers: pinned
+    host G-buffers, lights and spectra copied in, XYZ and sRGB8 copied out,
+    all inside the timed region."""
+    import torch
+    K, W = max(3, args.steps // 2), 2
+    h = {}
+    for name, a in (("n1", f.g1.normal), ("x1", f.g1.pos), ("m1", f.g1.mat), ("n2", f.g2.normal),
+                    ("x2", f.g2.pos), ("m2", f.g2.mat), ("lp", f.light_pos), ("li", f.light_intensity),
+                    ("mats", f.mat_spectra), ("spd", f.light_spd)):
+        h[name] = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    d = {name: torch.empty_like(t, device=dev) for name, t in h.items()}
+    P = f.pixels
+    k = args.k
+    zm = torch.empty(f.mat_spectra.shape[0], k, device=dev)
+    zl = torch.empty(f.lights, k, device=dev)
+    lat = torch.empty(P, k, device=dev)
+    xyz = torch.empty(P, 3, device=dev)
+    rgb = torch.empty(P, 3, device=dev, dtype=torch.uint8)
+    xyz_h = torch.empty(P, 3).pin_memory()
+    rgb_h = torch.empty(P, 3, dtype=torch.uint8).pin_memory()
+    g1 = hsc.GBuffer(d["n1"], d["x1"], d["m1"])
+    g2 = hsc.GBuffer(d["n2"], d["x2"], d["m2"])
+    lights = hsc.Lights(d["lp"], d["li"])
+    h2d = sum(t.numel() * t.element_size() for t in h.values())
+    d2h = xyz_h.numel() * 4 + rgb_h.numel()
+
+    def step():
+        for name in h:
+            d[name].copy_(h[name], non_blocking=True)
+        hsc.hsc_encode(ctx, Ed, d["mats"], zm)
+        hsc.hsc_encode(ctx, Ed, d["spd"], zl)
+        hsc.hsc_shade_latent(ctx, g1, g2, zm, lights, zl, hsc.HSC_FUSED, lat, xyz_out=xyz, M_xyz=M)
+        hsc.hsc_decode_xyz(ctx, lat, M, None, srgb8_out=rgb)
+        xyz_h.copy_(xyz, non_blocking=True)
+        rgb_h.copy_(rgb, non_blocking=True)
+
+    for _ in range(W):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / K
+    return {"value": evals / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": dt * 1e3, "steps": K}
+
+
+# --------------------------------------------------------------------------- reference arm
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return None
+    K, W = args.steps, args.warmup
+    per = []
+    ncores = 1
+    # each step: one 32-row band (61,440 pixels x 128 evaluations) through the oracle
+    for i in range(W + K):
+        rate, nrows, secs = oracle_rate(0.0, args.k, threads=ncores, max_rows=32)
+        if i >= W:
+            per.append((nrows * 1920 * 128, secs))
+    ev = sum(e for e, _ in per)
+    tot = sum(s for _, s in per)
+    value = ev / tot
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": tot / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (seeded G-buffers, spectra, lights)", "impl": "reference",
+            "config": {"workload": WORKLOAD, "pixels": 1920 * 1080, "lights": 64, "k": args.k, "n": 81,
+                       "sample": "each step: one 32-row band of the frame (61,440 pixels)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncores, "kind": "oracle",
+                             "sample": "32-row band of the 1920x1080 frame per step, FP64 NumPy, one thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "hsc" else "gloo")
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        res = run_hsc(args, rank, world)
+    if rank == 0 and res is not None:
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

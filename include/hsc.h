@@ -1,0 +1,247 @@
+/*
+ * hsc.h -- C ABI of libhsc, GB300 (sm_103a) kernels for deferred G-buffer
+ * shading with Hadamard spectral codes ("Compact Hadamard Latent Codes for
+ * Efficient Spectral Rendering", arXiv 2602.18741).
+ *
+ * The method (Sec. 3-5 of the paper): a non-negative linear encoder E (k x n)
+ * and decoder D (n x k) map n-sample spectra to k-codes, k = 3B (Eq. 4);
+ * scaling and addition stay exact in code space and the element-wise
+ * (Hadamard) product of spectra is replaced by the blockwise product of codes
+ * (Eq. 5).  Assets are encoded once, the k-code image is rendered as B RGB
+ * passes and reassembled, then decoded once to spectra, XYZ or sRGB (Fig. 2b).
+ *
+ * Shading model (the paper path-traces in Mitsuba, Sec. 5.1; this library
+ * shades a G-buffer instead): point lights l at p_l with intensity I_l, Lambert
+ * BRDF rho/pi, inverse-square falloff, no visibility, plus an optional
+ * indirect bounce through a secondary G-buffer point treated as a virtual
+ * point light with clamp eps = 1e-2:
+ *   g(x, n, l) = max(0, n.(p_l - x)) / |p_l - x|^3
+ *   A(x, n)    = sum_l g(x, n, l) * (I_l / pi) * V_l          (V_l: SPD or code)
+ *   h          = max(0, n1.d) max(0, -n2.d) / (|d|^2 max(|d|^2, eps)) / pi,  d = x2 - x1
+ *   out        = R_m1 (.) (A(x1, n1) + h * (R_m2 (.) A(x2, n2)))
+ * with (.) the element-wise product on n samples (spectral) or k channels
+ * (latent, Eq. 5).
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - Pointers marked "device" must point to device memory of the context's
+ *   GPU; the caller owns and frees all of them.  The library never frees or
+ *   reallocates caller memory.  Float arrays need 4-byte alignment; the latent
+ *   and output images of the vectorised kernels need 16-byte alignment where
+ *   noted.
+ * - Row-major layouts: a "P x c" array holds c consecutive values per pixel.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Every call only enqueues work on that stream and returns; nothing
+ *   synchronises unless stated.  Results are ready once the stream reaches
+ *   that point.
+ * - Errors are returned as hsc_status; hsc_last_error() gives a message for
+ *   the calling thread.  Arguments are validated on the host before any
+ *   launch (HSC_ERR_INVALID_ARG).  Problems found on the device (material
+ *   index out of range) set a device error word; hsc_sync() reports it as
+ *   HSC_ERR_DEVICE_CHECK and clears it.  No kernel traps or aborts.
+ * - A context is not thread-safe: use one per host thread.  Calls on one
+ *   context that share the context's scratch (noted below) must be ordered
+ *   on one stream.
+ */
+#ifndef HSC_H_
+#define HSC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define HSC_API __attribute__((visibility("default")))
+#else
+#define HSC_API
+#endif
+
+#define HSC_VERSION 1
+#define HSC_MAX_K 96      /* code length limit (multiple of 3)            */
+#define HSC_MAX_N 128     /* spectral sample limit                        */
+#define HSC_MAX_MAT (1 << 24)
+
+typedef struct hsc_ctx hsc_ctx;
+
+typedef enum {
+  HSC_OK = 0,
+  HSC_ERR_INVALID_ARG = 1,   /* bad size, null or misaligned pointer, bad enum   */
+  HSC_ERR_CUDA = 2,          /* a CUDA runtime call failed (message has details) */
+  HSC_ERR_OOM = 3,           /* context scratch could not be allocated           */
+  HSC_ERR_UNSUPPORTED = 4,   /* valid request this build does not implement      */
+  HSC_ERR_TIMEOUT = 5,       /* a bounded device wait ran out                    */
+  HSC_ERR_DEVICE_CHECK = 6   /* a kernel flagged bad input (see hsc_sync)        */
+} hsc_status;
+
+typedef enum { HSC_F32 = 0, HSC_BF16 = 1, HSC_F16 = 2, HSC_FP8_E4M3 = 3 } hsc_dtype;
+
+/* PASSES: the k-code image is produced as k/3 three-channel passes and
+ * reassembled (Fig. 2b).  FUSED: one launch shades all k channels, sharing
+ * the geometry term; per channel it performs exactly the same FP32 operations
+ * in the same order, so the two modes give bit-identical latent images.      */
+typedef enum { HSC_PASSES = 0, HSC_FUSED = 1 } hsc_mode;
+
+/* One G-buffer: per pixel a unit normal, a position and a material index.   */
+typedef struct {
+  const float* normal;   /* device, P x 3 float32                                 */
+  const float* pos;      /* device, P x 3 float32                                 */
+  const int32_t* mat;    /* device, P int32 in [0, n_mat); others set the error word */
+} hsc_gbuffer;
+
+/* Point lights.                                                              */
+typedef struct {
+  const float* pos;        /* device, L x 3 float32                           */
+  const float* intensity;  /* device, L float32 (scales the unit-peak SPD)    */
+  int32_t count;           /* L >= 1                                          */
+} hsc_lights;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` (made current on the calling
+ * thread).  Allocates a small fixed scratch block (error word, reduction
+ * workspace); larger scratch for PASSES images and the fp8 path grows on
+ * demand inside the calls that need it (see hsc_reserve).                  */
+HSC_API hsc_status hsc_create(hsc_ctx** out, int device);
+HSC_API void hsc_destroy(hsc_ctx* ctx);
+/* Message for the last failing call on this thread ("" if none).  Valid
+ * until the next call on this thread.                                       */
+HSC_API const char* hsc_last_error(void);
+/* Synchronise `stream`, surface asynchronous CUDA errors and the device error
+ * word (HSC_ERR_DEVICE_CHECK, cleared on read).                              */
+HSC_API hsc_status hsc_sync(hsc_ctx* ctx, void* stream);
+/* Pre-allocate context scratch of at least `bytes` so later calls do not
+ * allocate (required before capturing PASSES or fp8 calls in a CUDA graph).  */
+HSC_API hsc_status hsc_reserve(hsc_ctx* ctx, size_t bytes);
+/* Scratch bytes hsc_shade_latent needs for P pixels, code length k, `mode`
+ * and `latent_dt`.                                                           */
+HSC_API size_t hsc_shade_latent_scratch_bytes(int64_t pixels, int k, hsc_mode mode, hsc_dtype latent_dt);
+
+/* ----------------------------------------------------- colour projection */
+
+/* Integration weights of the CIE 1931 2-degree observer on the grid
+ * lambda_i = lambda0 + i*dlambda, i < n (paper: T_cmf in R^{3 x n}, colour
+ * loss of Sec. 3.3).  The CMFs are the analytic multi-lobe Gaussian fit of
+ * Wyman, Sloan and Shirley (JCGT 2013), evaluated in FP32;
+ * T[c][i] = cmf_c(lambda_i) dlambda / sum_j ybar(lambda_j) dlambda with the
+ * normalising sum accumulated in FP64, so the unit spectrum has Y = 1.
+ *   T_out: device, 3 x n float32.                                           */
+HSC_API hsc_status hsc_cmf_weights(hsc_ctx* ctx, int n, float lambda0, float dlambda,
+                           float* T_out, void* stream);
+
+/* Fold the colour projection into the decoder: M = T D (3 x k), so that
+ * XYZ = T (D z) = M z (decode to XYZ, Fig. 2b).  FP32, sums over i in order.
+ *   T: device 3 x n;  D: device n x k (decoder W_dec, Eq. 4);  M_out: device 3 x k. */
+HSC_API hsc_status hsc_fold_xyz(hsc_ctx* ctx, const float* T, const float* D, int k, int n,
+                        float* M_out, void* stream);
+
+/* ------------------------------------------------------------------ encode */
+
+/* Encode m spectra (Eq. 4, z = W_enc s); the paper encodes every spectral
+ * asset a single time per scene (Fig. 2b): codes[j][c] = sum_i E[c][i] spectra[j][i], FP32 sums in
+ * order of i, stored as `out_dt` (F32, BF16 or F16, round-to-nearest-even).
+ *   E: device k x n float32;  spectra: device m x n float32;
+ *   codes_out: device m x k of out_dt.  1 <= n <= HSC_MAX_N, 1 <= k <= HSC_MAX_K. */
+HSC_API hsc_status hsc_encode(hsc_ctx* ctx, const float* E, int k, int n, const float* spectra, int m,
+                      void* codes_out, hsc_dtype out_dt, void* stream);
+
+/* ----------------------------------------------------------- latent shade */
+
+/* Shade one RGB pass: code channels 3b..3b+2 of every pixel (Fig. 2b: the
+ * k-code is split into B three-channel blocks, each rendered on its own).
+ *   g1: primary G-buffer (P pixels); g2: secondary G-buffer or NULL (direct only);
+ *   mat_codes: device n_mat x k of code_dt;  light_codes: device L x k of code_dt;
+ *   code_dt: F32, BF16 or F16 (converted to FP32 on load, FP32 accumulation);
+ *   rgb_out: device P x 3 float32.                                           */
+HSC_API hsc_status hsc_shade_pass(hsc_ctx* ctx, const hsc_gbuffer* g1, const hsc_gbuffer* g2, int64_t pixels,
+                          const void* mat_codes, int n_mat, const hsc_lights* lights,
+                          const void* light_codes, int k, hsc_dtype code_dt, int b,
+                          float* rgb_out, void* stream);
+
+/* Reassemble B pass images into the k-channel latent image (Fig. 2b): latent[p][3b + j] = pass_b[p][j].
+ *   passes: host array of B device pointers, each P x 3 float32;
+ *   latent_out: device P x 3B float32.                                       */
+HSC_API hsc_status hsc_reassemble(hsc_ctx* ctx, const float* const* passes, int B, int64_t pixels,
+                          float* latent_out, void* stream);
+
+/* Latent shading of a whole frame (Sec. 3-5, Fig. 2b).
+ *   mode: HSC_PASSES (B shade passes into context scratch + reassembly) or
+ *         HSC_FUSED (one launch for k <= 15; larger k in chunks of 15).
+ *   latent_out: device P x k, latent_dt F32 (16-byte aligned) or FP8_E4M3
+ *         (then latent_scales, device k float32, receives the per-channel
+ *         scales max_p z_c / 448 and the codes are RNE(z / scale), saturating).
+ *   xyz_out: NULL, or device P x 3 float32 receiving XYZ = M_xyz z computed
+ *         from the FP32 latent (fused for FUSED and k <= 15);  M_xyz: device
+ *         3 x k from hsc_fold_xyz (required when xyz_out is set).
+ * Uses context scratch for PASSES images and for the fp8 path.               */
+HSC_API hsc_status hsc_shade_latent(hsc_ctx* ctx, const hsc_gbuffer* g1, const hsc_gbuffer* g2, int64_t pixels,
+                            const void* mat_codes, int n_mat, const hsc_lights* lights,
+                            const void* light_codes, int k, hsc_dtype code_dt, hsc_mode mode,
+                            void* latent_out, hsc_dtype latent_dt, float* latent_scales,
+                            float* xyz_out, const float* M_xyz, void* stream);
+
+/* Per-channel fp8 quantisation of an FP32 latent image: scale_c = max_p z_c / 448
+ * (1 for an all-zero channel), code = RNE_e4m3(z * (1/scale_c)) saturating.
+ *   latent: device P x k float32;  codes_out: device P x k bytes;  scales_out: device k.
+ * Uses the context's reduction scratch.                                      */
+HSC_API hsc_status hsc_quantize_fp8(hsc_ctx* ctx, const float* latent, int64_t pixels, int k,
+                            uint8_t* codes_out, float* scales_out, void* stream);
+
+/* ------------------------------------------------------------------ decode */
+
+/* Decode a latent image to XYZ (and optionally 8-bit sRGB) with the folded
+ * 3 x k matrix (the final decode of Fig. 2b):
+ *   xyz = M_xyz z;  srgb = OETF(clamp(M_sRGB xyz, 0, 1)), u8 = floor(255 srgb + 0.5)
+ * with M_sRGB the IEC 61966-2-1 matrix.
+ *   latent: device P x k of dt (F32, BF16, F16 or FP8_E4M3 + scales);
+ *   scales: device k float32 for FP8 (else ignored);
+ *   xyz_out: device P x 3 float32, or NULL when only srgb8_out is wanted;
+ *   srgb8_out: NULL or device P x 3 bytes (at least one output must be set). */
+HSC_API hsc_status hsc_decode_xyz(hsc_ctx* ctx, const void* latent, hsc_dtype dt, const float* scales,
+                          int64_t pixels, int k, const float* M_xyz, float* xyz_out,
+                          uint8_t* srgb8_out, void* stream);
+
+/* Decode a latent image to n-sample spectra, s_hat = W_dec z (Eq. 4).
+ *   dt = F32: FP32 FMAs on CUDA cores, sums over channels in order.
+ *   dt = BF16 or FP8_E4M3 (+ scales): tensor-core contraction
+ *        [P x 16 (k zero-padded)] x [16 x n] with BF16 operands (z exact in
+ *        bf16 for fp8 codes; D * scale rounded to bf16) and FP32 accumulation.
+ *   D: device n x k float32;  spectra_out: device P x n float32 (16-byte aligned). */
+HSC_API hsc_status hsc_decode_spectra(hsc_ctx* ctx, const void* latent, hsc_dtype dt, const float* scales,
+                              int64_t pixels, int k, const float* D, int n,
+                              float* spectra_out, void* stream);
+
+/* --------------------------------------------------------- spectral shade */
+
+/* Naive n-sample spectral shading, the paper's ground truth whose cost is
+ * linear in n (Sec. 1, Sec. 5): the shading model above on n samples, with
+ * XYZ = T S fused.
+ *   mat_spectra: device n_mat x n;  light_spd: device L x n (unit peak);
+ *   T: device 3 x n from hsc_cmf_weights;  xyz_out: device P x 3;
+ *   spectra_out: NULL or device P x n float32.                               */
+HSC_API hsc_status hsc_shade_spectral(hsc_ctx* ctx, const hsc_gbuffer* g1, const hsc_gbuffer* g2, int64_t pixels,
+                              const float* mat_spectra, int n_mat, const hsc_lights* lights,
+                              const float* light_spd, int n, const float* T,
+                              float* xyz_out, float* spectra_out, void* stream);
+
+/* ----------------------------------------------------------------- metrics */
+
+/* Colour difference of a test image against a reference image.  Both are
+ * divided by Y_ref = max_p Y of the reference, converted to CIELAB with white
+ * (T @ 1) (CIE 1976), and compared per pixel by CIEDE2000 (kL = kC = kH = 1),
+ * CIE94 (graphic arts; the paper's codec-selection metric, Sec. 3.5) and
+ * Delta E 76 (the paper's upsampler loss, Sec. 4.2).
+ *   stats_out: device 8 doubles = {mean dE2000, p95 dE2000 (nearest rank),
+ *              mean dE94, mean dE76, Y_ref, max dE2000, pixels, 0}.
+ *   de_out: NULL or device P float32 per-pixel dE2000.
+ * Uses the context's reduction scratch.                                      */
+HSC_API hsc_status hsc_delta_e(hsc_ctx* ctx, const float* xyz_test, const float* xyz_ref, int64_t pixels,
+                       const float* T, int n, float* de_out, double* stats_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSC_H_ */

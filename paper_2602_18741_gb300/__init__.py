@@ -1,0 +1,297 @@
+"""Python binding of libhsc: Hadamard-spectral-code G-buffer shading on GB300.
+
+Thin ctypes layer over the C ABI in ``include/hsc.h``: every function here
+has the C entry point's name, takes torch CUDA tensors, checks shapes and
+dtypes, and passes raw device pointers and the current CUDA stream to the
+library.  All arithmetic runs in the library's CUDA kernels; there is no
+fallback.  Importing raises ``ImportError`` when ``libhsc.so`` has not been
+built (``python -m paper_2602_18741_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhsc.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libhsc.so is not built at {LIB_PATH}; run `python -m paper_2602_18741_gb300.build`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# --------------------------------------------------------------------- enums
+HSC_OK, HSC_ERR_INVALID_ARG, HSC_ERR_CUDA, HSC_ERR_OOM, HSC_ERR_UNSUPPORTED, HSC_ERR_TIMEOUT, \
+    HSC_ERR_DEVICE_CHECK = range(7)
+HSC_F32, HSC_BF16, HSC_F16, HSC_FP8_E4M3 = range(4)
+HSC_PASSES, HSC_FUSED = range(2)
+HSC_MAX_K = 96
+HSC_MAX_N = 128
+
+STATUS_NAMES = {0: "HSC_OK", 1: "HSC_ERR_INVALID_ARG", 2: "HSC_ERR_CUDA", 3: "HSC_ERR_OOM",
+                4: "HSC_ERR_UNSUPPORTED", 5: "HSC_ERR_TIMEOUT", 6: "HSC_ERR_DEVICE_CHECK"}
+
+_DT_OF_TORCH = {torch.float32: HSC_F32, torch.bfloat16: HSC_BF16, torch.float16: HSC_F16,
+                torch.float8_e4m3fn: HSC_FP8_E4M3, torch.uint8: HSC_FP8_E4M3}
+
+
+class HscError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class _GBuffer(ctypes.Structure):
+    _fields_ = [("normal", ctypes.c_void_p), ("pos", ctypes.c_void_p), ("mat", ctypes.c_void_p)]
+
+
+class _Lights(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_void_p), ("intensity", ctypes.c_void_p), ("count", ctypes.c_int32)]
+
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int
+_i64 = ctypes.c_int64
+_f32 = ctypes.c_float
+_GB = ctypes.POINTER(_GBuffer)
+_LI = ctypes.POINTER(_Lights)
+
+_SIGS = {
+    "hsc_create": ([ctypes.POINTER(_vp), _i32], _i32),
+    "hsc_destroy": ([_vp], None),
+    "hsc_last_error": ([], ctypes.c_char_p),
+    "hsc_sync": ([_vp, _vp], _i32),
+    "hsc_reserve": ([_vp, ctypes.c_size_t], _i32),
+    "hsc_shade_latent_scratch_bytes": ([_i64, _i32, _i32, _i32], ctypes.c_size_t),
+    "hsc_cmf_weights": ([_vp, _i32, _f32, _f32, _vp, _vp], _i32),
+    "hsc_fold_xyz": ([_vp, _vp, _vp, _i32, _i32, _vp, _vp], _i32),
+    "hsc_encode": ([_vp, _vp, _i32, _i32, _vp, _i32, _vp, _i32, _vp], _i32),
+    "hsc_shade_pass": ([_vp, _GB, _GB, _i64, _vp, _i32, _LI, _vp, _i32, _i32, _i32, _vp, _vp], _i32),
+    "hsc_reassemble": ([_vp, ctypes.POINTER(_vp), _i32, _i64, _vp, _vp], _i32),
+    "hsc_shade_latent": ([_vp, _GB, _GB, _i64, _vp, _i32, _LI, _vp, _i32, _i32, _i32, _vp, _i32, _vp, _vp, _vp,
+                          _vp], _i32),
+    "hsc_quantize_fp8": ([_vp, _vp, _i64, _i32, _vp, _vp, _vp], _i32),
+    "hsc_decode_xyz": ([_vp, _vp, _i32, _vp, _i64, _i32, _vp, _vp, _vp, _vp], _i32),
+    "hsc_decode_spectra": ([_vp, _vp, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _vp], _i32),
+    "hsc_shade_spectral": ([_vp, _GB, _GB, _i64, _vp, _i32, _LI, _vp, _i32, _vp, _vp, _vp, _vp], _i32),
+    "hsc_delta_e": ([_vp, _vp, _vp, _i64, _vp, _i32, _vp, _vp, _vp], _i32),
+}
+
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+EXPORTED = tuple(_SIGS)
+
+
+def _check(status: int):
+    if status != HSC_OK:
+        raise HscError(status, _lib.hsc_last_error().decode(errors="replace"))
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensor must be on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _dt(t: torch.Tensor) -> int:
+    try:
+        return _DT_OF_TORCH[t.dtype]
+    except KeyError:
+        raise ValueError(f"unsupported dtype {t.dtype}") from None
+
+
+class Context:
+    """Owns an ``hsc_ctx`` (scratch, error word) on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self._h = _vp()
+        _check(_lib.hsc_create(ctypes.byref(self._h), int(device)))
+        self.device = int(device)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _lib.hsc_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class GBuffer:
+    """Device G-buffer: normal (P,3) f32, pos (P,3) f32, mat (P,) int32."""
+
+    def __init__(self, normal: torch.Tensor, pos: torch.Tensor, mat: torch.Tensor):
+        for t, nm in ((normal, "normal"), (pos, "pos")):
+            if t.dtype != torch.float32 or t.dim() != 2 or t.shape[1] != 3:
+                raise ValueError(f"{nm} must be (P,3) float32")
+        if mat.dtype != torch.int32 or mat.dim() != 1:
+            raise ValueError("mat must be (P,) int32")
+        if not (normal.shape[0] == pos.shape[0] == mat.shape[0]):
+            raise ValueError("G-buffer arrays disagree on P")
+        self.normal, self.pos, self.mat = normal, pos, mat
+        self._s = _GBuffer(_ptr(normal), _ptr(pos), _ptr(mat))
+
+    @property
+    def pixels(self) -> int:
+        return int(self.mat.shape[0])
+
+
+class Lights:
+    """Device point lights: pos (L,3) f32, intensity (L,) f32."""
+
+    def __init__(self, pos: torch.Tensor, intensity: torch.Tensor):
+        if pos.dtype != torch.float32 or pos.dim() != 2 or pos.shape[1] != 3:
+            raise ValueError("light pos must be (L,3) float32")
+        if intensity.dtype != torch.float32 or intensity.shape != (pos.shape[0],):
+            raise ValueError("light intensity must be (L,) float32")
+        self.pos, self.intensity = pos, intensity
+        self._s = _Lights(_ptr(pos), _ptr(intensity), int(pos.shape[0]))
+
+    @property
+    def count(self) -> int:
+        return int(self.pos.shape[0])
+
+
+def _gb(g: Optional[GBuffer]):
+    return ctypes.byref(g._s) if g is not None else None
+
+
+# ------------------------------------------------------------------- calls
+
+def hsc_sync(ctx: Context, stream=None):
+    _check(_lib.hsc_sync(ctx.handle, _stream(stream)))
+
+
+def hsc_reserve(ctx: Context, nbytes: int):
+    _check(_lib.hsc_reserve(ctx.handle, int(nbytes)))
+
+
+def hsc_shade_latent_scratch_bytes(pixels: int, k: int, mode: int, latent_dt: int) -> int:
+    return int(_lib.hsc_shade_latent_scratch_bytes(int(pixels), int(k), int(mode), int(latent_dt)))
+
+
+def hsc_cmf_weights(ctx: Context, n: int, lambda0: float, dlambda: float, T_out: torch.Tensor, stream=None):
+    if T_out.dtype != torch.float32 or T_out.shape != (3, n):
+        raise ValueError("T_out must be (3, n) float32")
+    _check(_lib.hsc_cmf_weights(ctx.handle, int(n), float(lambda0), float(dlambda), _ptr(T_out), _stream(stream)))
+
+
+def hsc_fold_xyz(ctx: Context, T: torch.Tensor, D: torch.Tensor, M_out: torch.Tensor, stream=None):
+    n, k = D.shape
+    if T.shape != (3, n) or M_out.shape != (3, k):
+        raise ValueError("shapes: T (3,n), D (n,k), M_out (3,k)")
+    _check(_lib.hsc_fold_xyz(ctx.handle, _ptr(T), _ptr(D), int(k), int(n), _ptr(M_out), _stream(stream)))
+
+
+def hsc_encode(ctx: Context, E: torch.Tensor, spectra: torch.Tensor, codes_out: torch.Tensor, stream=None):
+    k, n = E.shape
+    m = spectra.shape[0]
+    if spectra.shape != (m, n) or codes_out.shape != (m, k):
+        raise ValueError("shapes: E (k,n), spectra (m,n), codes_out (m,k)")
+    if E.dtype != torch.float32 or spectra.dtype != torch.float32:
+        raise ValueError("E and spectra must be float32")
+    _check(_lib.hsc_encode(ctx.handle, _ptr(E), int(k), int(n), _ptr(spectra), int(m), _ptr(codes_out),
+                           _dt(codes_out), _stream(stream)))
+
+
+def hsc_shade_pass(ctx: Context, g1: GBuffer, g2: Optional[GBuffer], mat_codes: torch.Tensor, lights: Lights,
+                   light_codes: torch.Tensor, b: int, rgb_out: torch.Tensor, stream=None):
+    k = mat_codes.shape[1]
+    if rgb_out.shape != (g1.pixels, 3) or rgb_out.dtype != torch.float32:
+        raise ValueError("rgb_out must be (P,3) float32")
+    _check(_lib.hsc_shade_pass(ctx.handle, _gb(g1), _gb(g2), g1.pixels, _ptr(mat_codes), int(mat_codes.shape[0]),
+                               ctypes.byref(lights._s), _ptr(light_codes), int(k), _dt(mat_codes), int(b),
+                               _ptr(rgb_out), _stream(stream)))
+
+
+def hsc_reassemble(ctx: Context, passes: Sequence[torch.Tensor], latent_out: torch.Tensor, stream=None):
+    B = len(passes)
+    P = latent_out.shape[0]
+    arr = (_vp * B)(*[_ptr(p) for p in passes])
+    _check(_lib.hsc_reassemble(ctx.handle, arr, B, int(P), _ptr(latent_out), _stream(stream)))
+
+
+def hsc_shade_latent(ctx: Context, g1: GBuffer, g2: Optional[GBuffer], mat_codes: torch.Tensor, lights: Lights,
+                     light_codes: torch.Tensor, mode: int, latent_out: torch.Tensor,
+                     latent_scales: Optional[torch.Tensor] = None, xyz_out: Optional[torch.Tensor] = None,
+                     M_xyz: Optional[torch.Tensor] = None, stream=None):
+    k = mat_codes.shape[1]
+    if light_codes.shape != (lights.count, k) or light_codes.dtype != mat_codes.dtype:
+        raise ValueError("light_codes must be (L,k) with the material codes' dtype")
+    if latent_out.shape != (g1.pixels, k):
+        raise ValueError("latent_out must be (P,k)")
+    _check(_lib.hsc_shade_latent(ctx.handle, _gb(g1), _gb(g2), g1.pixels, _ptr(mat_codes), int(mat_codes.shape[0]),
+                                 ctypes.byref(lights._s), _ptr(light_codes), int(k), _dt(mat_codes), int(mode),
+                                 _ptr(latent_out), _dt(latent_out), _ptr(latent_scales), _ptr(xyz_out), _ptr(M_xyz),
+                                 _stream(stream)))
+
+
+def hsc_quantize_fp8(ctx: Context, latent: torch.Tensor, codes_out: torch.Tensor, scales_out: torch.Tensor,
+                     stream=None):
+    P, k = latent.shape
+    _check(_lib.hsc_quantize_fp8(ctx.handle, _ptr(latent), int(P), int(k), _ptr(codes_out), _ptr(scales_out),
+                                 _stream(stream)))
+
+
+def hsc_decode_xyz(ctx: Context, latent: torch.Tensor, M_xyz: torch.Tensor, xyz_out: torch.Tensor,
+                   scales: Optional[torch.Tensor] = None, srgb8_out: Optional[torch.Tensor] = None, stream=None):
+    P, k = latent.shape
+    if (xyz_out is not None and xyz_out.shape != (P, 3)) or M_xyz.shape != (3, k):
+        raise ValueError("shapes: latent (P,k), M_xyz (3,k), xyz_out (P,3)")
+    _check(_lib.hsc_decode_xyz(ctx.handle, _ptr(latent), _dt(latent), _ptr(scales), int(P), int(k), _ptr(M_xyz),
+                               _ptr(xyz_out), _ptr(srgb8_out), _stream(stream)))
+
+
+def hsc_decode_spectra(ctx: Context, latent: torch.Tensor, D: torch.Tensor, spectra_out: torch.Tensor,
+                       scales: Optional[torch.Tensor] = None, stream=None):
+    P, k = latent.shape
+    n = D.shape[0]
+    if D.shape != (n, k) or spectra_out.shape != (P, n):
+        raise ValueError("shapes: latent (P,k), D (n,k), spectra_out (P,n)")
+    _check(_lib.hsc_decode_spectra(ctx.handle, _ptr(latent), _dt(latent), _ptr(scales), int(P), int(k), _ptr(D),
+                                   int(n), _ptr(spectra_out), _stream(stream)))
+
+
+def hsc_shade_spectral(ctx: Context, g1: GBuffer, g2: Optional[GBuffer], mat_spectra: torch.Tensor, lights: Lights,
+                       light_spd: torch.Tensor, T: torch.Tensor, xyz_out: torch.Tensor,
+                       spectra_out: Optional[torch.Tensor] = None, stream=None):
+    n = mat_spectra.shape[1]
+    if light_spd.shape != (lights.count, n) or T.shape != (3, n) or xyz_out.shape != (g1.pixels, 3):
+        raise ValueError("shapes: mat_spectra (m,n), light_spd (L,n), T (3,n), xyz_out (P,3)")
+    _check(_lib.hsc_shade_spectral(ctx.handle, _gb(g1), _gb(g2), g1.pixels, _ptr(mat_spectra),
+                                   int(mat_spectra.shape[0]), ctypes.byref(lights._s), _ptr(light_spd), int(n),
+                                   _ptr(T), _ptr(xyz_out), _ptr(spectra_out), _stream(stream)))
+
+
+def hsc_delta_e(ctx: Context, xyz_test: torch.Tensor, xyz_ref: torch.Tensor, T: torch.Tensor,
+                stats_out: torch.Tensor, de_out: Optional[torch.Tensor] = None, stream=None):
+    P = xyz_ref.shape[0]
+    if stats_out.dtype != torch.float64 or stats_out.numel() < 8:
+        raise ValueError("stats_out must hold 8 float64")
+    _check(_lib.hsc_delta_e(ctx.handle, _ptr(xyz_test), _ptr(xyz_ref), int(P), _ptr(T), int(T.shape[1]),
+                            _ptr(de_out), _ptr(stats_out), _stream(stream)))

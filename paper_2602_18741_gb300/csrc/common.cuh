@@ -1,0 +1,194 @@
+// Shared host/device helpers of libhsc (GB300, sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <string>
+
+#include "../../include/hsc.h"
+
+// ---------------------------------------------------------------- context
+
+// Fixed scratch block, allocated once per context (bytes).
+#define HSC_SMALL_SCRATCH (1u << 20)
+// Offsets inside the fixed scratch block.
+#define HSC_OFF_CHANMAX 0u          // HSC_MAX_K uint32 (fp8 per-channel max)
+#define HSC_OFF_REDUCE 4096u        // reduction workspace for hsc_delta_e
+
+struct hsc_ctx {
+  int device = 0;
+  int sm_count = 0;
+  int max_smem_optin = 0;
+  unsigned int* d_err = nullptr;   // device error word (bit flags)
+  unsigned char* d_small = nullptr;
+  unsigned char* d_big = nullptr;  // growable scratch (PASSES images, fp32 latent)
+  size_t big_bytes = 0;
+};
+
+// Device error flags.
+#define HSC_DEVERR_MATERIAL 1u
+
+namespace hsc {
+
+hsc_status set_error(hsc_status st, const char* fmt, ...);
+hsc_status clear_error();
+hsc_status check_launch(const char* what);
+hsc_status ensure_big(hsc_ctx* ctx, size_t bytes, cudaStream_t stream);
+
+// Makes ctx->device current for the scope of a call and restores the
+// caller's device afterwards.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = (cudaSetDevice(dev) == cudaSuccess);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+inline int ceil_div_i(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace hsc
+
+#define HSC_CHECK_CTX(ctx)                                                        \
+  do {                                                                            \
+    if ((ctx) == nullptr) return hsc::set_error(HSC_ERR_INVALID_ARG, "null context"); \
+  } while (0)
+
+#define HSC_REQUIRE(cond, ...)                                                    \
+  do {                                                                            \
+    if (!(cond)) return hsc::set_error(HSC_ERR_INVALID_ARG, __VA_ARGS__);         \
+  } while (0)
+
+#define HSC_CUDA(call)                                                            \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess)                                                        \
+      return hsc::set_error(HSC_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define HSC_TRY(expr)                                                             \
+  do {                                                                            \
+    hsc_status s_ = (expr);                                                       \
+    if (s_ != HSC_OK) return s_;                                                  \
+  } while (0)
+
+#define HSC_GUARD(ctx)                                                            \
+  hsc::DeviceGuard guard_((ctx)->device);                                         \
+  if (!guard_.ok) return hsc::set_error(HSC_ERR_CUDA, "cannot select device %d", (ctx)->device)
+
+// ---------------------------------------------------------------- device
+
+namespace hsc {
+
+// 1/pi rounded to float32.
+constexpr float kInvPi = 0.318309886183790671538f;
+
+// MUFU reciprocal square root (approximate, flush-to-zero), one instruction.
+__device__ __forceinline__ float rsqrt_mufu(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Geometry term of one (shading point, light) pair:
+//   g = max(0, n.(p - x)) / |p - x|^3
+// Explicit round-to-nearest intrinsics fix the instruction sequence so that
+// every kernel that calls this produces bit-identical g.
+__device__ __forceinline__ float geometry_term(float x, float y, float z, float nx, float ny, float nz,
+                                               float px, float py, float pz) {
+  const float dx = __fsub_rn(px, x);
+  const float dy = __fsub_rn(py, y);
+  const float dz = __fsub_rn(pz, z);
+  const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+  float c = __fmaf_rn(nz, dz, __fmaf_rn(ny, dy, __fmul_rn(nx, dx)));
+  c = fmaxf(c, 0.0f);
+  const float ri = rsqrt_mufu(r2);
+  return __fmul_rn(__fmul_rn(c, ri), __fmul_rn(ri, ri));
+}
+
+// Virtual-point-light transfer from the secondary point to the primary,
+// divided by pi (the secondary reflectance's Lambert 1/pi):
+//   h = max(0, n1.d) max(0, -n2.d) / (|d|^2 max(|d|^2, 1e-2)) / pi,  d = x2 - x1
+__device__ __forceinline__ float bounce_term(float x1, float y1, float z1, float nx1, float ny1, float nz1,
+                                             float x2, float y2, float z2, float nx2, float ny2, float nz2) {
+  const float dx = __fsub_rn(x2, x1);
+  const float dy = __fsub_rn(y2, y1);
+  const float dz = __fsub_rn(z2, z1);
+  const float dd = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+  float c1 = __fmaf_rn(nz1, dz, __fmaf_rn(ny1, dy, __fmul_rn(nx1, dx)));
+  float c2 = __fmaf_rn(nz2, dz, __fmaf_rn(ny2, dy, __fmul_rn(nx2, dx)));
+  c1 = fmaxf(c1, 0.0f);
+  c2 = fmaxf(-c2, 0.0f);
+  const float den = __fmul_rn(dd, fmaxf(dd, 1e-2f));
+  const float h = __fdiv_rn(__fmul_rn(c1, c2), den);
+  return (den > 0.0f) ? __fmul_rn(h, kInvPi) : 0.0f;
+}
+
+// Load element i of a code array stored as F32 / BF16 / F16 as float.
+__device__ __forceinline__ float load_code(const void* base, int dt, int64_t i) {
+  if (dt == HSC_F32) return __ldg(reinterpret_cast<const float*>(base) + i);
+  if (dt == HSC_BF16) {
+    const unsigned short u = __ldg(reinterpret_cast<const unsigned short*>(base) + i);
+    return __uint_as_float(((unsigned int)u) << 16);
+  }
+  const unsigned short u = __ldg(reinterpret_cast<const unsigned short*>(base) + i);
+  return __half2float(__ushort_as_half(u));
+}
+
+// fp8 e4m3 (OCP FP8, bias 7, 3 mantissa bits, no infinities) -> float, exact:
+// exponent field 0 is subnormal (mant * 2^-9); S.1111.111 is NaN.
+__device__ __forceinline__ float fp8_e4m3_to_float(unsigned int b) {
+  const unsigned int s = (b >> 7) & 1u, e = (b >> 3) & 15u, m = b & 7u;
+  float v;
+  if (e == 0u) {
+    v = (float)m * 0.001953125f;  // 2^-9
+  } else if (e == 15u && m == 7u) {
+    v = __uint_as_float(0x7fc00000u);
+  } else {
+    v = __uint_as_float(((e + 120u) << 23) | (m << 20));
+  }
+  return s ? -v : v;
+}
+
+// float -> fp8 e4m3 byte, round to nearest even, saturating to +-448.  Both
+// halves of the packed conversion get the same value, so the byte order of
+// the packed result does not matter.
+__device__ __forceinline__ unsigned int float_to_fp8_e4m3(float x) {
+  unsigned short r;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %1;" : "=h"(r) : "f"(x));
+  return (unsigned int)(r & 0xFFu);
+}
+
+// float -> bf16 / f16 bits, round to nearest even.
+__device__ __forceinline__ unsigned short float_to_bf16_bits(float x) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+__device__ __forceinline__ unsigned short float_to_f16_bits(float x) {
+  return __half_as_ushort(__float2half_rn(x));
+}
+
+// Load element i of a latent image of dtype dt as float (fp8 dequantised with
+// the channel's scale).
+__device__ __forceinline__ float load_latent(const void* base, int dt, int64_t i, const float* scales, int c) {
+  if (dt == HSC_FP8_E4M3) {
+    const unsigned int b = __ldg(reinterpret_cast<const unsigned char*>(base) + i);
+    return __fmul_rn(fp8_e4m3_to_float(b), __ldg(scales + c));
+  }
+  return load_code(base, dt, i);
+}
+
+}  // namespace hsc

@@ -1,0 +1,171 @@
+// Decoding the latent image once per frame (Fig. 2b): to XYZ with the folded
+// 3 x k matrix M = T D, to 8-bit sRGB, and to n-sample spectra s_hat = W_dec z
+// (Eq. 4).  All three are HBM streams: per pixel a few dozen bytes in and 12
+// (XYZ) or 4n (spectra) bytes out against a handful of FMAs per output.
+#include "common.cuh"
+#include "shade_latent.cuh"
+
+namespace hsc {
+
+namespace {
+
+constexpr int kDBlock = 256;
+
+// IEC 61966-2-1 XYZ -> linear sRGB.
+__constant__ float c_srgb[9] = {3.2406f, -1.5372f, -0.4986f, -0.9689f, 1.8758f, 0.0415f, 0.0557f, -0.2040f, 1.0570f};
+
+__device__ __forceinline__ float srgb_encode(float v) {
+  v = fminf(fmaxf(v, 0.0f), 1.0f);
+  return (v <= 0.0031308f) ? 12.92f * v : 1.055f * powf(v, 1.0f / 2.4f) - 0.055f;
+}
+
+__global__ void __launch_bounds__(kDBlock) decode_xyz_kernel(const void* __restrict__ latent, int dt,
+                                                             const float* __restrict__ scales, int64_t P, int k,
+                                                             const float* __restrict__ M, float* __restrict__ xyz,
+                                                             uint8_t* __restrict__ srgb8) {
+  __shared__ float s_M[3 * HSC_MAX_K];
+  for (int i = threadIdx.x; i < 3 * k; i += blockDim.x) s_M[i] = M[i];
+  __syncthreads();
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+    float X = 0.0f, Y = 0.0f, Z = 0.0f;
+    for (int c = 0; c < k; ++c) {
+      const float z = load_latent(latent, dt, p * k + c, scales, c);
+      X = __fmaf_rn(s_M[c], z, X);
+      Y = __fmaf_rn(s_M[k + c], z, Y);
+      Z = __fmaf_rn(s_M[2 * k + c], z, Z);
+    }
+    if (xyz) {
+      xyz[3 * p + 0] = X;
+      xyz[3 * p + 1] = Y;
+      xyz[3 * p + 2] = Z;
+    }
+    if (srgb8) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const float lin = __fmaf_rn(c_srgb[3 * r + 2], Z, __fmaf_rn(c_srgb[3 * r + 1], Y, __fmul_rn(c_srgb[3 * r], X)));
+        srgb8[3 * p + r] = (uint8_t)floorf(srgb_encode(lin) * 255.0f + 0.5f);
+      }
+    }
+  }
+}
+
+// Spectral decode on CUDA cores (FP32 latent).  A CTA owns a tile of TP
+// pixels: z (TP x k) and D (n x k) sit in shared memory and the TP*n outputs of
+// the tile are written in flat order, so consecutive threads store
+// consecutive addresses.
+constexpr int kTP = 64;
+
+__global__ void __launch_bounds__(kDBlock) decode_spectra_f32_kernel(const float* __restrict__ z, int64_t P, int k,
+                                                                     const float* __restrict__ D, int n,
+                                                                     float* __restrict__ out) {
+  extern __shared__ float s_mem[];
+  float* s_D = s_mem;             // n x k
+  float* s_z = s_mem + n * k;     // kTP x k
+  for (int i = threadIdx.x; i < n * k; i += blockDim.x) s_D[i] = __ldg(D + i);
+  const int64_t tiles = (P + kTP - 1) / kTP;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t p0 = tile * kTP;
+    const int tp = (int)min((int64_t)kTP, P - p0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < tp * k; i += blockDim.x) s_z[i] = __ldg(z + p0 * k + i);
+    __syncthreads();
+    const int total = tp * n;
+    int f = threadIdx.x;
+    int pl = f / n, i = f - pl * n;
+    const int dp = kDBlock / n, di = kDBlock - dp * n;
+    float* o = out + p0 * n;
+    for (; f < total; f += kDBlock) {
+      const float* zz = s_z + pl * k;
+      const float* dd = s_D + i * k;
+      float s = 0.0f;
+      for (int c = 0; c < k; ++c) s = __fmaf_rn(dd[c], zz[c], s);
+      o[f] = s;
+      pl += dp;
+      i += di;
+      if (i >= n) {
+        i -= n;
+        ++pl;
+      }
+    }
+  }
+}
+
+int64_t stream_grid(int64_t work, int block, int sm_count, int per_sm) {
+  int64_t g = (work + block - 1) / block;
+  const int64_t cap = (int64_t)sm_count * per_sm;
+  if (g > cap) g = cap;
+  return g < 1 ? 1 : g;
+}
+
+}  // namespace
+
+hsc_status launch_decode_xyz(const void* latent, int dt, const float* scales, int64_t P, int k, const float* M,
+                             float* xyz, uint8_t* srgb8, int sm_count, cudaStream_t s) {
+  const int64_t grid = stream_grid(P, kDBlock, sm_count, 8);
+  decode_xyz_kernel<<<(unsigned)grid, kDBlock, 0, s>>>(latent, dt, scales, P, k, M, xyz, srgb8);
+  return check_launch("decode_xyz_kernel");
+}
+
+hsc_status launch_decode_spectra_f32(const float* z, int64_t P, int k, const float* D, int n, float* out,
+                                     int sm_count, cudaStream_t s) {
+  const int64_t tiles = (P + kTP - 1) / kTP;
+  int64_t grid = tiles < (int64_t)sm_count * 8 ? tiles : (int64_t)sm_count * 8;
+  if (grid < 1) grid = 1;
+  const size_t smem = (size_t)(n * k + kTP * k) * sizeof(float);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(decode_spectra_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return set_error(HSC_ERR_CUDA, "smem attribute: %s", cudaGetErrorString(e));
+  }
+  decode_spectra_f32_kernel<<<(unsigned)grid, kDBlock, smem, s>>>(z, P, k, D, n, out);
+  return check_launch("decode_spectra_f32_kernel");
+}
+
+hsc_status launch_decode_spectra_tc(hsc_ctx* ctx, const void* latent, int dt, const float* scales, int64_t P, int k,
+                                    const float* D, int n, float* out, cudaStream_t s);
+
+}  // namespace hsc
+
+extern "C" {
+
+hsc_status hsc_decode_xyz(hsc_ctx* ctx, const void* latent, hsc_dtype dt, const float* scales, int64_t pixels, int k,
+                          const float* M_xyz, float* xyz_out, uint8_t* srgb8_out, void* stream) {
+  hsc::clear_error();
+  HSC_CHECK_CTX(ctx);
+  HSC_REQUIRE(k >= 1 && k <= HSC_MAX_K, "k=%d out of range", k);
+  HSC_REQUIRE(pixels >= 0, "negative pixel count");
+  HSC_REQUIRE(dt == HSC_F32 || dt == HSC_BF16 || dt == HSC_F16 || dt == HSC_FP8_E4M3, "bad latent dtype");
+  HSC_REQUIRE(latent && M_xyz && (xyz_out || srgb8_out), "null pointer");
+  HSC_REQUIRE(dt != HSC_FP8_E4M3 || scales, "fp8 latent needs scales");
+  HSC_REQUIRE(hsc::aligned(latent, dt == HSC_F32 ? 4 : (dt == HSC_FP8_E4M3 ? 1 : 2)) && hsc::aligned(xyz_out, 4) &&
+                  hsc::aligned(M_xyz, 4),
+              "misaligned pointer");
+  if (pixels == 0) return HSC_OK;
+  HSC_GUARD(ctx);
+  return hsc::launch_decode_xyz(latent, (int)dt, scales, pixels, k, M_xyz, xyz_out, srgb8_out, ctx->sm_count,
+                                hsc::as_stream(stream));
+}
+
+hsc_status hsc_decode_spectra(hsc_ctx* ctx, const void* latent, hsc_dtype dt, const float* scales, int64_t pixels,
+                              int k, const float* D, int n, float* spectra_out, void* stream) {
+  hsc::clear_error();
+  HSC_CHECK_CTX(ctx);
+  HSC_REQUIRE(k >= 1 && k <= HSC_MAX_K, "k=%d out of range", k);
+  HSC_REQUIRE(n >= 1 && n <= HSC_MAX_N, "n=%d out of range", n);
+  HSC_REQUIRE(pixels >= 0, "negative pixel count");
+  HSC_REQUIRE(latent && D && spectra_out, "null pointer");
+  HSC_REQUIRE(hsc::aligned(spectra_out, 16), "spectra_out must be 16-byte aligned");
+  if (pixels == 0) return HSC_OK;
+  HSC_GUARD(ctx);
+  cudaStream_t s = hsc::as_stream(stream);
+  if (dt == HSC_F32) {
+    HSC_REQUIRE(hsc::aligned(latent, 4), "misaligned latent");
+    return hsc::launch_decode_spectra_f32(reinterpret_cast<const float*>(latent), pixels, k, D, n, spectra_out,
+                                          ctx->sm_count, s);
+  }
+  HSC_REQUIRE(dt == HSC_BF16 || dt == HSC_FP8_E4M3, "spectral decode takes F32, BF16 or FP8_E4M3 latents");
+  HSC_REQUIRE(k <= 16, "tensor-core decode supports k <= 16 (got %d)", k);
+  HSC_REQUIRE(dt != HSC_FP8_E4M3 || scales, "fp8 latent needs scales");
+  return hsc::launch_decode_spectra_tc(ctx, latent, (int)dt, scales, pixels, k, D, n, spectra_out, s);
+}
+
+}  // extern "C"

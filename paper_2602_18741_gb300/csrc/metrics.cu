@@ -1,0 +1,274 @@
+// Colour-difference statistics of a test image against a reference image:
+// mean / nearest-rank p95 of CIEDE2000, means of CIE94 and Delta E 76.
+// The paper compares colours with CIE94 (codec selection, Sec. 3.5) and
+// Delta E 76 after the CIELAB transform (upsampler loss, Sec. 4.2).
+//
+// Pipeline, all on the caller's stream, no host round trip:
+//   1. max_p Y of the reference (unsigned max over float bits; Y >= 0).
+//   2. per pixel: both XYZ / Y_ref -> CIELAB (white = T @ 1) -> dE00, dE94,
+//      dE76; per-CTA FP64 partial sums written to scratch.
+//   3. one CTA folds the partials into the stats.
+//   4. p95 by exact radix select on the float bits of dE00 (non-negative):
+//      three passes over 11 / 11 / 10-bit digits, each a histogram kernel and a
+//      one-CTA scan that narrows the prefix and the rank.
+#include "common.cuh"
+
+namespace hsc {
+
+namespace {
+
+constexpr int kMBlock = 256;
+
+struct Scratch {
+  unsigned int ymax_bits;
+  unsigned int prefix;       // radix-select prefix (bits found so far)
+  unsigned long long rank;   // rank still to find inside the current prefix
+  float white[3];
+  unsigned int pad;
+  unsigned int hist[2048];
+  double partial[1];         // [grid][4]
+};
+
+__device__ __forceinline__ float lab_f(float t) {
+  const float d = 6.0f / 29.0f;
+  return (t > d * d * d) ? cbrtf(t) : t / (3.0f * d * d) + 4.0f / 29.0f;
+}
+
+__device__ __forceinline__ void to_lab(float X, float Y, float Z, const float* w, float& L, float& a, float& b) {
+  const float fx = lab_f(X / w[0]), fy = lab_f(Y / w[1]), fz = lab_f(Z / w[2]);
+  L = 116.0f * fy - 16.0f;
+  a = 500.0f * (fx - fy);
+  b = 200.0f * (fy - fz);
+}
+
+constexpr float kDeg = 57.29577951308232f;
+constexpr float kRad = 0.017453292519943295f;
+
+__device__ __forceinline__ float pow7(float x) {
+  const float x2 = x * x;
+  return x2 * x2 * x2 * x;
+}
+
+// CIEDE2000 (CIE 142-2001), kL = kC = kH = 1; colour 1 is the reference.
+__device__ float de2000(float L1, float a1, float b1, float L2, float a2, float b2) {
+  const float C1 = sqrtf(a1 * a1 + b1 * b1), C2 = sqrtf(a2 * a2 + b2 * b2);
+  const float Cm7 = pow7(0.5f * (C1 + C2));
+  const float G = 0.5f * (1.0f - sqrtf(Cm7 / (Cm7 + 6103515625.0f)));  // 25^7
+  const float ap1 = (1.0f + G) * a1, ap2 = (1.0f + G) * a2;
+  const float Cp1 = sqrtf(ap1 * ap1 + b1 * b1), Cp2 = sqrtf(ap2 * ap2 + b2 * b2);
+  float h1 = (ap1 == 0.0f && b1 == 0.0f) ? 0.0f : atan2f(b1, ap1) * kDeg;
+  float h2 = (ap2 == 0.0f && b2 == 0.0f) ? 0.0f : atan2f(b2, ap2) * kDeg;
+  if (h1 < 0.0f) h1 += 360.0f;
+  if (h2 < 0.0f) h2 += 360.0f;
+  const float dL = L2 - L1, dC = Cp2 - Cp1;
+  const float pc = Cp1 * Cp2;
+  float dh = h2 - h1;
+  if (pc == 0.0f) dh = 0.0f;
+  else if (dh > 180.0f) dh -= 360.0f;
+  else if (dh < -180.0f) dh += 360.0f;
+  const float dH = 2.0f * sqrtf(pc) * sinf(0.5f * dh * kRad);
+  const float Lm = 0.5f * (L1 + L2), Cm = 0.5f * (Cp1 + Cp2);
+  float hm = h1 + h2;
+  if (pc != 0.0f) {
+    if (fabsf(h1 - h2) <= 180.0f) hm *= 0.5f;
+    else if (hm < 360.0f) hm = 0.5f * (hm + 360.0f);
+    else hm = 0.5f * (hm - 360.0f);
+  }
+  const float T = 1.0f - 0.17f * cosf((hm - 30.0f) * kRad) + 0.24f * cosf(2.0f * hm * kRad) +
+                  0.32f * cosf((3.0f * hm + 6.0f) * kRad) - 0.20f * cosf((4.0f * hm - 63.0f) * kRad);
+  const float e = (hm - 275.0f) / 25.0f;
+  const float dtheta = 30.0f * expf(-e * e);
+  const float Cm7b = pow7(Cm);
+  const float RC = 2.0f * sqrtf(Cm7b / (Cm7b + 6103515625.0f));
+  const float l50 = (Lm - 50.0f) * (Lm - 50.0f);
+  const float SL = 1.0f + 0.015f * l50 / sqrtf(20.0f + l50);
+  const float SC = 1.0f + 0.045f * Cm;
+  const float SH = 1.0f + 0.015f * Cm * T;
+  const float RT = -sinf(2.0f * dtheta * kRad) * RC;
+  const float tL = dL / SL, tC = dC / SC, tH = dH / SH;
+  return sqrtf(fmaxf(tL * tL + tC * tC + tH * tH + RT * tC * tH, 0.0f));
+}
+
+// CIE94, graphic arts (kL = 1, K1 = 0.045, K2 = 0.015); colour 1 is the reference.
+__device__ float de94(float L1, float a1, float b1, float L2, float a2, float b2) {
+  const float C1 = sqrtf(a1 * a1 + b1 * b1), C2 = sqrtf(a2 * a2 + b2 * b2);
+  const float dL = L1 - L2, dC = C1 - C2, da = a1 - a2, db = b1 - b2;
+  const float dH2 = fmaxf(da * da + db * db - dC * dC, 0.0f);
+  const float SC = 1.0f + 0.045f * C1, SH = 1.0f + 0.015f * C1;
+  return sqrtf(dL * dL + (dC / SC) * (dC / SC) + dH2 / (SH * SH));
+}
+
+__global__ void ymax_kernel(const float* __restrict__ ref, int64_t P, const float* __restrict__ T, int n,
+                            Scratch* sc) {
+  __shared__ unsigned int s_m;
+  if (threadIdx.x == 0) s_m = 0u;
+  __syncthreads();
+  unsigned int m = 0u;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, __float_as_uint(fmaxf(__ldg(ref + 3 * p + 1), 0.0f)));
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0) atomicMax(&s_m, m);
+  __syncthreads();
+  if (threadIdx.x == 0) atomicMax(&sc->ymax_bits, s_m);
+  if (blockIdx.x == 0 && threadIdx.x < 3) {
+    double w = 0.0;
+    for (int i = 0; i < n; ++i) w += (double)T[threadIdx.x * n + i];
+    sc->white[threadIdx.x] = (float)w;
+  }
+}
+
+__global__ void __launch_bounds__(kMBlock) de_kernel(const float* __restrict__ test, const float* __restrict__ ref,
+                                                     int64_t P, Scratch* sc, float* __restrict__ de_out) {
+  __shared__ double s_red[kMBlock / 32][4];
+  float yr = __uint_as_float(sc->ymax_bits);
+  const float inv = (yr > 0.0f) ? 1.0f / yr : 1.0f;
+  const float w[3] = {sc->white[0], sc->white[1], sc->white[2]};
+  double s00 = 0.0, s94 = 0.0, s76 = 0.0, mx = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+    float L1, a1, b1, L2, a2, b2;
+    to_lab(__ldg(ref + 3 * p) * inv, __ldg(ref + 3 * p + 1) * inv, __ldg(ref + 3 * p + 2) * inv, w, L1, a1, b1);
+    to_lab(__ldg(test + 3 * p) * inv, __ldg(test + 3 * p + 1) * inv, __ldg(test + 3 * p + 2) * inv, w, L2, a2, b2);
+    const float d00 = de2000(L1, a1, b1, L2, a2, b2);
+    const float d94 = de94(L1, a1, b1, L2, a2, b2);
+    const float d76 = sqrtf((L1 - L2) * (L1 - L2) + (a1 - a2) * (a1 - a2) + (b1 - b2) * (b1 - b2));
+    de_out[p] = d00;
+    s00 += d00;
+    s94 += d94;
+    s76 += d76;
+    mx = fmax(mx, (double)d00);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s00 += __shfl_xor_sync(0xffffffffu, s00, o);
+    s94 += __shfl_xor_sync(0xffffffffu, s94, o);
+    s76 += __shfl_xor_sync(0xffffffffu, s76, o);
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  const int wid = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    s_red[wid][0] = s00;
+    s_red[wid][1] = s94;
+    s_red[wid][2] = s76;
+    s_red[wid][3] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[4] = {0, 0, 0, 0};
+    for (int i = 0; i < kMBlock / 32; ++i) {
+      t[0] += s_red[i][0];
+      t[1] += s_red[i][1];
+      t[2] += s_red[i][2];
+      t[3] = fmax(t[3], s_red[i][3]);
+    }
+    for (int j = 0; j < 4; ++j) sc->partial[4 * blockIdx.x + j] = t[j];
+  }
+}
+
+// One CTA: fold the per-CTA partials in a fixed order (deterministic) and set
+// up the radix select for rank ceil(0.95 P) - 1.
+__global__ void fold_kernel(Scratch* sc, int nblocks, int64_t P, double* stats) {
+  if (threadIdx.x != 0) return;
+  double t[4] = {0, 0, 0, 0};
+  for (int i = 0; i < nblocks; ++i) {
+    t[0] += sc->partial[4 * i];
+    t[1] += sc->partial[4 * i + 1];
+    t[2] += sc->partial[4 * i + 2];
+    t[3] = fmax(t[3], sc->partial[4 * i + 3]);
+  }
+  const double inv = P > 0 ? 1.0 / (double)P : 0.0;
+  stats[0] = t[0] * inv;
+  stats[2] = t[1] * inv;
+  stats[3] = t[2] * inv;
+  stats[4] = (double)__uint_as_float(sc->ymax_bits);
+  stats[5] = t[3];
+  stats[6] = (double)P;
+  stats[7] = 0.0;
+  long long r = (long long)ceil(0.95 * (double)P) - 1;
+  sc->rank = (unsigned long long)(r < 0 ? 0 : r);
+  sc->prefix = 0u;
+}
+
+// Histogram of the digit (bits [shift, shift+width)) of every value whose
+// higher bits equal the prefix found so far.
+__global__ void __launch_bounds__(kMBlock) radix_hist_kernel(const float* __restrict__ v, int64_t P, Scratch* sc,
+                                                             int shift, int width) {
+  __shared__ unsigned int s_h[2048];
+  const int bins = 1 << width;
+  for (int i = threadIdx.x; i < bins; i += blockDim.x) s_h[i] = 0u;
+  __syncthreads();
+  const unsigned int prefix = sc->prefix;
+  const int hi = shift + width;
+  const unsigned int hmask = (hi >= 32) ? 0u : (0xffffffffu << hi);
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned int u = __float_as_uint(fmaxf(__ldg(v + p), 0.0f));
+    if ((u & hmask) == (prefix & hmask)) atomicAdd(&s_h[(u >> shift) & (bins - 1)], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < bins; i += blockDim.x)
+    if (s_h[i]) atomicAdd(&sc->hist[i], s_h[i]);
+}
+
+// One thread: walk the histogram to the bin holding the rank, extend the
+// prefix, reduce the rank, clear the histogram for the next pass.
+__global__ void radix_select_kernel(Scratch* sc, int shift, int width, double* stats) {
+  if (threadIdx.x != 0) return;
+  const int bins = 1 << width;
+  unsigned long long r = sc->rank;
+  unsigned long long run = 0;
+  int sel = bins - 1;
+  for (int i = 0; i < bins; ++i) {
+    const unsigned long long c = sc->hist[i];
+    if (run + c > r) {
+      sel = i;
+      break;
+    }
+    run += c;
+  }
+  for (int i = 0; i < bins; ++i) sc->hist[i] = 0u;
+  sc->rank = r - run;
+  sc->prefix |= ((unsigned int)sel) << shift;
+  if (shift == 0) stats[1] = (double)__uint_as_float(sc->prefix);
+}
+
+}  // namespace
+
+}  // namespace hsc
+
+extern "C" hsc_status hsc_delta_e(hsc_ctx* ctx, const float* xyz_test, const float* xyz_ref, int64_t pixels,
+                                  const float* T, int n, float* de_out, double* stats_out, void* stream) {
+  hsc::clear_error();
+  HSC_CHECK_CTX(ctx);
+  HSC_REQUIRE(pixels >= 1, "need at least one pixel");
+  HSC_REQUIRE(n >= 1 && n <= HSC_MAX_N, "n=%d out of range", n);
+  HSC_REQUIRE(xyz_test && xyz_ref && T && stats_out, "null pointer");
+  HSC_REQUIRE(hsc::aligned(xyz_test, 4) && hsc::aligned(xyz_ref, 4) && hsc::aligned(T, 4) &&
+                  hsc::aligned(stats_out, 8) && (!de_out || hsc::aligned(de_out, 4)),
+              "misaligned pointer");
+  HSC_GUARD(ctx);
+  cudaStream_t s = hsc::as_stream(stream);
+  float* de = de_out;
+  if (!de) {
+    HSC_TRY(hsc::ensure_big(ctx, (size_t)pixels * sizeof(float), s));
+    de = reinterpret_cast<float*>(ctx->d_big);
+  }
+  int grid = ctx->sm_count * 4;
+  const int64_t need = (pixels + hsc::kMBlock - 1) / hsc::kMBlock;
+  if (grid > need) grid = (int)need;
+  if (grid < 1) grid = 1;
+  auto* sc = reinterpret_cast<hsc::Scratch*>(ctx->d_small + HSC_OFF_REDUCE);
+  HSC_CUDA(cudaMemsetAsync(sc, 0, sizeof(hsc::Scratch), s));
+  hsc::ymax_kernel<<<grid, hsc::kMBlock, 0, s>>>(xyz_ref, pixels, T, n, sc);
+  HSC_TRY(hsc::check_launch("ymax_kernel"));
+  hsc::de_kernel<<<grid, hsc::kMBlock, 0, s>>>(xyz_test, xyz_ref, pixels, sc, de);
+  HSC_TRY(hsc::check_launch("de_kernel"));
+  hsc::fold_kernel<<<1, 32, 0, s>>>(sc, grid, pixels, stats_out);
+  HSC_TRY(hsc::check_launch("fold_kernel"));
+  const int shifts[3] = {21, 10, 0};
+  const int widths[3] = {11, 11, 10};
+  for (int i = 0; i < 3; ++i) {
+    hsc::radix_hist_kernel<<<grid, hsc::kMBlock, 0, s>>>(de, pixels, sc, shifts[i], widths[i]);
+    HSC_TRY(hsc::check_launch("radix_hist_kernel"));
+    hsc::radix_select_kernel<<<1, 32, 0, s>>>(sc, shifts[i], widths[i], stats_out);
+    HSC_TRY(hsc::check_launch("radix_select_kernel"));
+  }
+  return HSC_OK;
+}

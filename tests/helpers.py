@@ -1,0 +1,68 @@
+"""Shared plumbing for the GPU tests: upload a seeded frame, run the library,
+and compute the oracle on the same inputs."""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+import hsc_inputs as hi
+
+
+def subset_frame(f: hi.Frame, idx: np.ndarray) -> hi.Frame:
+    """The frame restricted to pixels ``idx`` (for sampled oracle checks)."""
+    g1 = hi.GBuffer(f.g1.normal[idx], f.g1.pos[idx], f.g1.mat[idx])
+    g2 = None if f.g2 is None else hi.GBuffer(f.g2.normal[idx], f.g2.pos[idx], f.g2.mat[idx])
+    return hi.Frame(len(idx), 1, f.grid, f.mat_spectra, f.light_spd, f.light_pos, f.light_intensity, g1, g2)
+
+
+@dataclass
+class DevFrame:
+    g1: object
+    g2: Optional[object]
+    lights: object
+    mats: object
+    spd: object
+    T: object
+    P: int
+    n: int
+
+
+def upload(hsc, ctx, f: hi.Frame, dev):
+    import torch
+
+    def t(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    g1 = hsc.GBuffer(t(f.g1.normal), t(f.g1.pos), t(f.g1.mat))
+    g2 = None if f.g2 is None else hsc.GBuffer(t(f.g2.normal), t(f.g2.pos), t(f.g2.mat))
+    lights = hsc.Lights(t(f.light_pos), t(f.light_intensity))
+    T = torch.empty(3, f.n, device=dev)
+    hsc.hsc_cmf_weights(ctx, f.n, f.grid[0], f.grid[1], T)
+    return DevFrame(g1, g2, lights, t(f.mat_spectra), t(f.light_spd), T, f.pixels, f.n)
+
+
+def encode_all(hsc, ctx, df: DevFrame, E, dtype=None):
+    import torch
+    dtype = dtype or torch.float32
+    dev = df.mats.device
+    Ed = torch.from_numpy(np.ascontiguousarray(E, dtype=np.float32)).to(dev)
+    k = E.shape[0]
+    zm = torch.empty(df.mats.shape[0], k, device=dev, dtype=dtype)
+    zl = torch.empty(df.spd.shape[0], k, device=dev, dtype=dtype)
+    hsc.hsc_encode(ctx, Ed, df.mats, zm)
+    hsc.hsc_encode(ctx, Ed, df.spd, zl)
+    return zm, zl
+
+
+def rel_err_rows(got, ref, floor_frac=1e-3):
+    """max_p |got - ref|_inf / max(|ref(p)|_inf, floor * max|ref|) over rows."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    if ref.size == 0:
+        return 0.0
+    mag = np.abs(ref).max(axis=1)
+    den = np.maximum(mag, floor_frac * mag.max())
+    den = np.where(den > 0, den, 1.0)
+    return float((np.abs(got - ref).max(axis=1) / den).max())

@@ -1,0 +1,503 @@
+"""GPU parity of every libhsc entry point against the FP64 CPU oracle.
+
+Tolerances: the FP32 shading path must match the oracle to a relative XYZ
+error of 1e-5 (per pixel, floored at 1e-3 of the image maximum); the same
+bound is used for latent channels, spectra and decoded values.  Integer and
+byte outputs are compared exactly (or, where a float decides a rounding, the
+GPU value must be a valid rounding of the oracle value).  PASSES and FUSED
+latent images must agree bit for bit.
+"""
+import numpy as np
+import pytest
+
+import hsc_inputs as hi
+from oracle import cmf, codec, metrics, quant, shade
+
+from helpers import encode_all, rel_err_rows, subset_frame, upload
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import paper_2602_18741_gb300 as hsc
+    assert torch.cuda.is_available()
+    ctx = hsc.Context(0)
+    yield hsc, ctx, torch.device("cuda:0")
+    ctx.close()
+
+
+def _codec(k, n, seed=0):
+    try:
+        if k in (6, 9) and n in (31, 81):
+            return hi.load_codec(k, n)
+    except FileNotFoundError:
+        pass
+    rng = np.random.default_rng(seed + 17 * k + n)
+    return (rng.uniform(0, 2.0 / n, (k, n)).astype(np.float32), rng.uniform(0, 1.0, (n, k)).astype(np.float32))
+
+
+def _oracle_latent(f, E, D):
+    z = shade.shade_latent(f, E.astype(np.float64))
+    return z, shade.decode_xyz(z, D.astype(np.float64), cmf.cmf_weights(*f.grid))
+
+
+# ------------------------------------------------------------------ a1, a2
+
+@pytest.mark.parametrize("grid_spec", [hi.GRID_31, hi.GRID_81, (360.0, 2.5, 128), (500.0, 50.0, 1)])
+def test_cmf_weights(env, grid_spec):
+    hsc, ctx, dev = env
+    import torch
+    n = grid_spec[2]
+    T = torch.empty(3, n, device=dev)
+    hsc.hsc_cmf_weights(ctx, n, grid_spec[0], grid_spec[1], T)
+    ref = cmf.cmf_weights(*grid_spec)
+    got = T.cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-6 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("k,n", [(6, 31), (9, 81), (81, 81), (3, 5)])
+def test_fold_xyz(env, k, n):
+    hsc, ctx, dev = env
+    import torch
+    g = (380.0, 400.0 / max(n - 1, 1), n)
+    E, D = _codec(k, n)
+    T = torch.empty(3, n, device=dev)
+    hsc.hsc_cmf_weights(ctx, n, g[0], g[1], T)
+    M = torch.empty(3, k, device=dev)
+    hsc.hsc_fold_xyz(ctx, T, torch.from_numpy(D).to(dev), M)
+    ref = cmf.cmf_weights(*g) @ D.astype(np.float64)
+    assert np.max(np.abs(M.cpu().numpy() - ref)) <= TOL * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("k,n,m", [(6, 31, 16), (9, 81, 288), (15, 81, 1), (96, 128, 33)])
+def test_encode_f32(env, k, n, m):
+    hsc, ctx, dev = env
+    import torch
+    rng = np.random.default_rng(k * n + m)
+    E = rng.uniform(0, 1.0 / n, (k, n)).astype(np.float32)
+    S = rng.uniform(0, 1, (m, n)).astype(np.float32)
+    out = torch.empty(m, k, device=dev)
+    hsc.hsc_encode(ctx, torch.from_numpy(E).to(dev), torch.from_numpy(S).to(dev), out)
+    ref = codec.encode(E, S)
+    assert rel_err_rows(out.cpu().numpy(), ref) <= 1e-6
+
+
+@pytest.mark.parametrize("dtname", ["bfloat16", "float16"])
+def test_encode_reduced_precision_rounds_correctly(env, dtname):
+    hsc, ctx, dev = env
+    import torch
+    dt = getattr(torch, dtname)
+    rng = np.random.default_rng(3)
+    E = rng.uniform(0, 0.05, (9, 81)).astype(np.float32)
+    S = rng.uniform(0, 1, (500, 81)).astype(np.float32)
+    out = torch.empty(500, 9, device=dev, dtype=dt)
+    hsc.hsc_encode(ctx, torch.from_numpy(E).to(dev), torch.from_numpy(S).to(dev), out)
+    got = out.float().cpu().numpy().astype(np.float64)
+    ref = codec.encode(E, S)
+    ulp = 2.0 ** (np.floor(np.log2(np.abs(ref))) - (7 if dtname == "bfloat16" else 10))
+    # a valid round-to-nearest of the exact value, up to the FP32 sum's error
+    assert np.all(np.abs(got - ref) <= 0.5 * ulp * (1 + 1e-4) + 1e-6 * np.abs(ref))
+    exact = quant.round_bf16(ref.astype(np.float32)) if dtname == "bfloat16" else quant.round_f16(ref.astype(np.float32))
+    assert np.mean(got == exact) > 0.99
+
+
+# ------------------------------------------------------------ a3, a4, a5
+
+CASES = [
+    # (width, height, grid, lights, secondary, k)
+    (256, 256, hi.GRID_31, 4, False, 6),     # the 256x256 n=31 four-light frame
+    (7, 13, hi.GRID_81, 64, True, 6),
+    (1, 1, hi.GRID_81, 5, True, 9),
+    (333, 3, hi.GRID_31, 17, True, 3),        # ragged tail of the pixel tiles
+    (40, 25, hi.GRID_81, 300, True, 9),       # more lights than one shared-memory tile
+    (33, 31, hi.GRID_81, 11, False, 12),
+    (64, 17, hi.GRID_81, 7, True, 15),
+    (29, 11, hi.GRID_81, 6, True, 18),        # k > 15: fused launch in channel chunks
+]
+
+
+@pytest.mark.parametrize("w,h,grid_spec,L,sec,k", CASES)
+def test_shade_latent_fused_matches_oracle(env, w, h, grid_spec, L, sec, k):
+    hsc, ctx, dev = env
+    import torch
+    seed = w * 1000 + h + L
+    f = hi.make_frame(seed, w, h, grid_spec, n_smooth=20, n_saw=5, lights=L, secondary=sec)
+    if (w, h) == (256, 256):
+        f = hi.frame_config1()
+    E, D = _codec(k, f.n)
+    df = upload(hsc, ctx, f, dev)
+    zm, zl = encode_all(hsc, ctx, df, E)
+    M = torch.empty(3, k, device=dev)
+    hsc.hsc_fold_xyz(ctx, df.T, torch.from_numpy(D).to(dev), M)
+    lat = torch.empty(f.pixels, k, device=dev)
+    xyz = torch.empty(f.pixels, 3, device=dev)
+    hsc.hsc_shade_latent(ctx, df.g1, df.g2, zm, df.lights, zl, hsc.HSC_FUSED, lat, xyz_out=xyz, M_xyz=M)
+    hsc.hsc_sync(ctx)
+    z_ref, xyz_ref = _oracle_latent(f, E, D)
+    assert rel_err_rows(lat.cpu().numpy(), z_ref) <= TOL
+    assert metrics.rel_xyz_error(xyz.cpu().numpy(), xyz_ref) <= TOL
+
+
+@pytest.mark.parametrize("w,h,grid_spec,L,sec,k", [CASES[1], CASES[3], CASES[4], CASES[6], CASES[7]])
+def test_passes_bit_identical_to_fused(env, w, h, grid_spec, L, sec, k):
+    hsc, ctx, dev = env
+    import torch
+    f = hi.make_frame(w + h + L, w, h, grid_spec, n_smooth=20, n_saw=5, lights=L, secondary=sec)
+    E, D = _codec(k, f.n)
+    df = upload(hsc, ctx, f, dev)
+    zm, zl = encode_all(hsc, ctx, df, E)
+    M = torch.empty(3, k, device=dev)
+    hsc.hsc_fold_xyz(ctx, df.T, torch.from_numpy(D).to(dev), M)
+    fused = torch.empty(f.pixels, k, device=dev)
+    passes = torch.empty(f.pixels, k, device=dev)
+    xf = torch.empty(f.pixels, 3, device=dev)
+    xp = torch.empty(f.pixels, 3, device=dev)
+    hsc.hsc_shade_latent(ctx, df.g1, df.g2, zm, df.lights, zl, hsc.HSC_FUSED, fused, xyz_out=xf, M_xyz=M)
+    hsc.hsc_shade_latent(ctx, df.g1, df.g2, zm, df.lights, zl, hsc.HSC_PASSES, passes, xyz_out=xp, M_xyz=M)
+    # the explicit per-pass calls and the reassembly entry point
+    imgs = [torch.empty(f.pixels, 3, device=dev) for _ in range(k // 3)]
+    for b, img in enumerate(imgs):
+        hsc.hsc_shade_pass(ctx, df.g1, df.g2, zm, df.lights, zl, b, img)
+    re = torch.empty(f.pixels, k, device=dev)
+    hsc.hsc_reassemble(ctx, imgs, re)
+    hsc.hsc_sync(ctx)
+    assert torch.equal(fused, passes)
+    assert torch.equal(fused, re)
+    assert torch.equal(xf, xp)
+    for b, img in enumerate(imgs):
+        assert torch.equal(img, fused[:, 3 * b:3 * b + 3])
+
+
+@pytest.mark.parametrize("grid_spec,k,sec", [(hi.GRID_81, 81, False), (hi.GRID_81, 81, True), (hi.GRID_31, 33, False)])
+def test_identity_codec_latent_equals_spectral(env, grid_spec, k, sec):
+    # k = n with E = D = I (n = 31 padded to k = 33) is an exact codec; with
+    # direct light only the two kernels then run the same FP32 operations per
+    # channel, so their outputs agree bit for bit.
+    hsc, ctx, dev = env
+    import torch
+    f = hi.make_frame(91, 23, 19, grid_spec, n_smooth=9, n_saw=3, lights=13, secondary=sec)
+    n = f.n
+    E = np.zeros((k, n), np.float32)
+    E[:n, :n] = np.eye(n, dtype=np.float32)
+    D = np.ascontiguousarray(E.T)
+    df = upload(hsc, ctx, f, dev)
+    zm, zl = encode_all(hsc, ctx, df, E)
+    M = torch.empty(3, k, device=dev)
+    hsc.hsc_fold_xyz(ctx, df.T, torch.from_numpy(D).to(dev), M)
+    lat = torch.empty(f.pixels, k, device=dev)
+    xl = torch.empty(f.pixels, 3, device=dev)
+    hsc.hsc_shade_latent(ctx, df.g1, df.g2, zm, df.lights, zl, hsc.HSC_FUSED, lat, xyz_out=xl, M_xyz=M)
+    xs = torch.empty(f.pixels, 3, device=dev)
+    S = torch.empty(f.pixels, n, device=dev)
+    hsc.hsc_shade_spectral(ctx, df.g1, df.g2, df.mats, df.lights, df.spd, df.T, xs, S)
+    hsc.hsc_sync(ctx)
+    if sec:
+        assert rel_err_rows(lat[:, :n].cpu().numpy(), S.cpu().numpy()) <= 1e-6
+        assert metrics.rel_xyz_error(xl.cpu().numpy(), xs.cpu().numpy().astype(np.float64)) <= 1e-6
+    else:
+        assert torch.equal(lat[:, :n], S)
+        assert torch.equal(xl, xs)
+    _, ref = shade.shade_spectral(f)
+    assert metrics.rel_xyz_error(xl.cpu().numpy(), ref) <= TOL
+
+
+@pytest.mark.parametrize("dtname", ["bfloat16", "float16"])
+def test_shade_latent_reduced_precision_codes(env, dtname):
+    # codes stored in bf16 / fp16, FP32 accumulation: compared with the oracle
+    # run on the same rounded codes, so only FP32 arithmetic error remains
+    hsc, ctx, dev = env
+    import torch
+    dt = getattr(torch, dtname)
+    f = hi.make_frame(5, 61, 37, hi.GRID_81, n_smooth=30, n_saw=6, lights=64, secondary=True)
+    E, D = _codec(9, 81)
+    zm64 = shade.material_codes(E.astype(np.float64), f)
+    zl64 = shade.light_codes(E.astype(np.float64), f)
+    rnd = quant.round_bf16 if dtname == "bfloat16" else quant.round_f16
+    zm_r, zl_r = rnd(zm64.astype(np.float32)), rnd(zl64.astype(np.float32))
+    df = upload(hsc, ctx, f, dev)
+    zm = torch.from_numpy(zm_r.astype(np.float32)).to(dev).to(dt)
+    zl = torch.from_numpy(zl_r.astype(np.float32)).to(dev).to(dt)
+    M = torch.empty(3, 9, device=dev)
+    hsc.hsc_fold_xyz(ctx, df.T, torch.from_numpy(D).to(dev), M)
+    lat = torch.empty(f.pixels, 9, device=dev)
+    xyz = torch.empty(f.pixels, 3, device=dev)
+    hsc.hsc_shade_latent(ctx, df.g1, df.g2, zm, df.lights, zl, hsc.HSC_FUSED, lat, xyz_out=xyz, M_xyz=M)
+    hsc.hsc_sync(ctx)
+    z_ref = shade.shade_latent(f, E, zmat=zm_r, zlight=zl_r)
+    x_ref = shade.decode_xyz(z_ref, D.astype(np.float64), cmf.cmf_weights(*f.grid))
+    assert rel_err_rows(lat.cpu().numpy(), z_ref) <= TOL
+    assert metrics.rel_xyz_error(xyz.cpu().numpy(), x_ref) <= TOL
+
+
+@pytest.mark.parametrize("mode", ["FUSED", "PASSES"])
+def test_shade_latent_fp8_output(env, mode):
+    hsc, ctx, dev = env
+    import torch
+    f = hi.make_frame(8, 50, 41, hi.GRID_81, n_smooth=30, n_saw=6, lights=20, secondary=True)
+    E, D = _codec(6, 81)
+    df = upload(hsc, ctx, f, dev)
+    zm, zl = encode_all(hsc, ctx, df, E)
+    codes = torch.empty(f.pixels, 6, device=dev, dtype=torch.uint8)
+    scales = torch.empty(6, device=dev)
+    ref32 = torch.empty(f.pixels, 6, device=dev)
+    hsc.hsc_shade_latent(ctx, df.g1, df.g2, zm, df.lights, zl, getattr(hsc, "HSC_" + mode), codes, latent_scales=scales)
+    hsc.hsc_shade_latent(ctx, df.g1, df.g2, zm, df.lights, zl, hsc.HSC_FUSED, ref32)
+    hsc.hsc_sync(ctx)
+    z_ref, _ = _oracle_latent(f, E, D)
+    s_ref = z_ref.max(axis=0) / 448.0
+    assert np.max(np.abs(scales.cpu().numpy() - s_ref) / s_ref) <= TOL
+    # the codes are exactly the quantisation of the GPU's own FP32 latent ...
+    bits, _ = quant.quantize_fp8(ref32.cpu().numpy(), scales.cpu().numpy())
+    assert np.array_equal(codes.cpu().numpy(), bits)
+    # ... and dequantise to within fp8 rounding of the oracle's latent
+    vals = codes.cpu().view(torch.float8_e4m3fn).float().numpy() * scales.cpu().numpy()[None, :]
+    big = z_ref > 2 ** -6 * s_ref[None, :]
+    assert np.all(np.abs(vals[big] - z_ref[big]) <= (2 ** -4 + 1e-4) * z_ref[big])
+
+
+def test_quantize_fp8_bitwise(env):
+    hsc, ctx, dev = env
+    import torch
+    rng = np.random.default_rng(11)
+    z = (rng.gamma(1.0, 1.0, (4099, 9)) * rng.uniform(0.01, 10, 9)[None, :]).astype(np.float32)
+    z[:, 4] = 0.0
+    zd = torch.from_numpy(z).to(dev)
+    codes = torch.empty(4099, 9, device=dev, dtype=torch.uint8)
+    scales = torch.empty(9, device=dev)
+    hsc.hsc_quantize_fp8(ctx, zd, codes, scales)
+    hsc.hsc_sync(ctx)
+    s_ref = quant.fp8_channel_scales(z)
+    assert np.array_equal(scales.cpu().numpy(), s_ref)
+    bits, _ = quant.quantize_fp8(z, s_ref)
+    assert np.array_equal(codes.cpu().numpy(), bits)
+
+
+# --------------------------------------------------------------------- a8
+
+@pytest.mark.parametrize("w,h,grid_spec,L,sec", [
+    (256, 256, hi.GRID_31, 4, False), (7, 13, hi.GRID_81, 64, True), (1, 1, hi.GRID_81, 3, True),
+    (129, 5, hi.GRID_31, 70, True), (20, 20, (360.0, 2.5, 128), 9, True), (17, 9, (400.0, 20.0, 16), 5, False)])
+def test_shade_spectral_matches_oracle(env, w, h, grid_spec, L, sec):
+    hsc, ctx, dev = env
+    import torch
+    f = hi.make_frame(w * 7 + h + L, w, h, grid_spec, n_smooth=20, n_saw=5, lights=L, secondary=sec)
+    if (w, h) == (256, 256):
+        f = hi.frame_config1()
+    df = upload(hsc, ctx, f, dev)
+    xyz = torch.empty(f.pixels, 3, device=dev)
+    S = torch.empty(f.pixels, f.n, device=dev)
+    hsc.hsc_shade_spectral(ctx, df.g1, df.g2, df.mats, df.lights, df.spd, df.T, xyz, S)
+    hsc.hsc_sync(ctx)
+    S_ref, xyz_ref = shade.shade_spectral(f)
+    assert rel_err_rows(S.cpu().numpy(), S_ref) <= TOL
+    assert metrics.rel_xyz_error(xyz.cpu().numpy(), xyz_ref) <= TOL
+
+
+# --------------------------------------------------------------- a6, a7
+
+@pytest.mark.parametrize("k,P", [(6, 1000), (9, 4097), (3, 1), (18, 333)])
+def test_decode_xyz_and_srgb(env, k, P):
+    hsc, ctx, dev = env
+    import torch
+    rng = np.random.default_rng(k + P)
+    E, D = _codec(k, 81)
+    z = rng.gamma(1.0, 0.3, (P, k)).astype(np.float32)
+    T = torch.empty(3, 81, device=dev)
+    hsc.hsc_cmf_weights(ctx, 81, 380.0, 5.0, T)
+    M = torch.empty(3, k, device=dev)
+    hsc.hsc_fold_xyz(ctx, T, torch.from_numpy(D).to(dev), M)
+    xyz = torch.empty(P, 3, device=dev)
+    rgb = torch.empty(P, 3, device=dev, dtype=torch.uint8)
+    hsc.hsc_decode_xyz(ctx, torch.from_numpy(z).to(dev), M, xyz, srgb8_out=rgb)
+    hsc.hsc_sync(ctx)
+    ref = shade.decode_xyz(z, D.astype(np.float64), cmf.cmf_weights(*hi.GRID_81))
+    assert metrics.rel_xyz_error(xyz.cpu().numpy(), ref) <= TOL
+    u8 = cmf.srgb_to_u8(cmf.xyz_to_srgb(ref))
+    d = np.abs(rgb.cpu().numpy().astype(int) - u8.astype(int))
+    assert d.max() <= 1 and np.mean(d == 0) > 0.99
+
+
+def test_decode_xyz_from_reduced_latents(env):
+    hsc, ctx, dev = env
+    import torch
+    rng = np.random.default_rng(4)
+    E, D = _codec(9, 81)
+    z = rng.gamma(1.0, 0.3, (2000, 9)).astype(np.float32)
+    T = torch.empty(3, 81, device=dev)
+    hsc.hsc_cmf_weights(ctx, 81, 380.0, 5.0, T)
+    M = torch.empty(3, 9, device=dev)
+    hsc.hsc_fold_xyz(ctx, T, torch.from_numpy(D).to(dev), M)
+    Tr = cmf.cmf_weights(*hi.GRID_81)
+    for dt, rnd in ((torch.bfloat16, quant.round_bf16), (torch.float16, quant.round_f16)):
+        zr = rnd(z)
+        xyz = torch.empty(2000, 3, device=dev)
+        hsc.hsc_decode_xyz(ctx, torch.from_numpy(z).to(dev).to(dt), M, xyz)
+        hsc.hsc_sync(ctx)
+        assert metrics.rel_xyz_error(xyz.cpu().numpy(), shade.decode_xyz(zr, D.astype(np.float64), Tr)) <= TOL
+    s = quant.fp8_channel_scales(z)
+    bits, deq = quant.quantize_fp8(z, s)
+    xyz = torch.empty(2000, 3, device=dev)
+    hsc.hsc_decode_xyz(ctx, torch.from_numpy(bits).to(dev), M, xyz, scales=torch.from_numpy(s).to(dev))
+    hsc.hsc_sync(ctx)
+    assert metrics.rel_xyz_error(xyz.cpu().numpy(), shade.decode_xyz(deq, D.astype(np.float64), Tr)) <= TOL
+
+
+@pytest.mark.parametrize("k,n,P", [(6, 81, 1000), (9, 81, 4097), (6, 31, 63), (96, 128, 70), (3, 1, 5)])
+def test_decode_spectra_f32(env, k, n, P):
+    hsc, ctx, dev = env
+    import torch
+    rng = np.random.default_rng(k * n + P)
+    D = rng.uniform(0, 1, (n, k)).astype(np.float32)
+    z = rng.gamma(1.0, 0.3, (P, k)).astype(np.float32)
+    out = torch.empty(P, n, device=dev)
+    hsc.hsc_decode_spectra(ctx, torch.from_numpy(z).to(dev), torch.from_numpy(D).to(dev), out)
+    hsc.hsc_sync(ctx)
+    assert rel_err_rows(out.cpu().numpy(), codec.decode(D, z)) <= TOL
+
+
+# -------------------------------------------------------------------- a10
+
+def test_delta_e_on_shared_inputs(env):
+    # both sides take the same XYZ images: per-pixel dE00 agrees to FP32
+    # accuracy and the GPU p95 is the exact nearest rank of its own values
+    hsc, ctx, dev = env
+    import torch
+    f = hi.make_frame(21, 64, 48, hi.GRID_81, n_smooth=40, n_saw=8, lights=12, secondary=True)
+    E, D = _codec(6, 81)
+    _, xs = shade.shade_spectral(f)
+    _, xl = _oracle_latent(f, E, D)
+    xs32, xl32 = xs.astype(np.float32), xl.astype(np.float32)
+    T = torch.empty(3, 81, device=dev)
+    hsc.hsc_cmf_weights(ctx, 81, 380.0, 5.0, T)
+    st = torch.zeros(8, device=dev, dtype=torch.float64)
+    de = torch.empty(f.pixels, device=dev)
+    hsc.hsc_delta_e(ctx, torch.from_numpy(xl32).to(dev), torch.from_numpy(xs32).to(dev), T, st, de_out=de)
+    hsc.hsc_sync(ctx)
+    ref = metrics.delta_e_stats(xl32, xs32, cmf.cmf_weights(*hi.GRID_81))
+    got = st.cpu().numpy()
+    de_h = de.cpu().numpy()
+    assert np.max(np.abs(de_h - ref["per_pixel_de2000"])) < 2e-3
+    assert abs(got[0] - ref["de2000_mean"]) < 1e-3
+    assert got[1] == metrics.nearest_rank(de_h.astype(np.float64), 0.95)
+    assert abs(got[1] - ref["de2000_p95"]) < 1e-2
+    assert abs(got[2] - ref["de94_mean"]) < 1e-3
+    assert abs(got[3] - ref["de76_mean"]) < 1e-3
+    assert abs(got[4] - ref["y_ref"]) <= 1e-6 * ref["y_ref"]
+    assert got[6] == f.pixels
+
+
+def test_delta_e_latent_vs_spectral_end_to_end(env):
+    # GPU render + GPU metric vs oracle render + oracle metric, within 0.01
+    hsc, ctx, dev = env
+    import torch
+    f = hi.make_frame(23, 96, 80, hi.GRID_81, n_smooth=64, n_saw=8, lights=32, secondary=True)
+    E, D = _codec(6, 81)
+    df = upload(hsc, ctx, f, dev)
+    zm, zl = encode_all(hsc, ctx, df, E)
+    M = torch.empty(3, 6, device=dev)
+    hsc.hsc_fold_xyz(ctx, df.T, torch.from_numpy(D).to(dev), M)
+    lat = torch.empty(f.pixels, 6, device=dev)
+    xl = torch.empty(f.pixels, 3, device=dev)
+    xs = torch.empty(f.pixels, 3, device=dev)
+    hsc.hsc_shade_latent(ctx, df.g1, df.g2, zm, df.lights, zl, hsc.HSC_FUSED, lat, xyz_out=xl, M_xyz=M)
+    hsc.hsc_shade_spectral(ctx, df.g1, df.g2, df.mats, df.lights, df.spd, df.T, xs)
+    st = torch.zeros(8, device=dev, dtype=torch.float64)
+    hsc.hsc_delta_e(ctx, xl, xs, df.T, st)
+    hsc.hsc_sync(ctx)
+    _, xs_ref = shade.shade_spectral(f)
+    _, xl_ref = _oracle_latent(f, E, D)
+    ref = metrics.delta_e_stats(xl_ref, xs_ref, cmf.cmf_weights(*f.grid))
+    got = st.cpu().numpy()
+    assert abs(got[0] - ref["de2000_mean"]) <= 0.01
+    assert abs(got[1] - ref["de2000_p95"]) <= 0.01
+
+
+# ------------------------------------------------------------ edge cases
+
+def test_empty_inputs_are_noops(env):
+    hsc, ctx, dev = env
+    import torch
+    f = hi.make_frame(1, 2, 2, hi.GRID_31, n_smooth=3, n_saw=0, lights=2, secondary=True)
+    df = upload(hsc, ctx, f, dev)
+    E, D = _codec(6, 31)
+    zm, zl = encode_all(hsc, ctx, df, E)
+    e = torch.empty(0, 3, device=dev)
+    g0 = hsc.GBuffer(e, e.clone(), torch.empty(0, dtype=torch.int32, device=dev))
+    lat = torch.empty(0, 6, device=dev)
+    hsc.hsc_shade_latent(ctx, g0, g0, zm, df.lights, zl, hsc.HSC_PASSES, lat)
+    hsc.hsc_shade_spectral(ctx, g0, None, df.mats, df.lights, df.spd, df.T, e.clone())
+    hsc.hsc_decode_xyz(ctx, lat, torch.zeros(3, 6, device=dev), e.clone())
+    hsc.hsc_encode(ctx, torch.zeros(6, 31, device=dev), torch.empty(0, 31, device=dev), torch.empty(0, 6, device=dev))
+    hsc.hsc_sync(ctx)
+
+
+def test_bad_material_index_sets_device_error(env):
+    hsc, ctx, dev = env
+    import torch
+    f = hi.make_frame(2, 8, 8, hi.GRID_31, n_smooth=4, n_saw=0, lights=3, secondary=False)
+    f.g1.mat[5] = 99
+    df = upload(hsc, ctx, f, dev)
+    E, _ = _codec(6, 31)
+    zm, zl = encode_all(hsc, ctx, df, E)
+    lat = torch.empty(f.pixels, 6, device=dev)
+    hsc.hsc_shade_latent(ctx, df.g1, None, zm, df.lights, zl, hsc.HSC_FUSED, lat)
+    with pytest.raises(hsc.HscError) as ei:
+        hsc.hsc_sync(ctx)
+    assert ei.value.status == hsc.HSC_ERR_DEVICE_CHECK
+    assert float(lat[5].abs().max()) == 0.0
+    hsc.hsc_sync(ctx)  # the flag was cleared on read
+
+
+def test_invalid_arguments_are_rejected(env):
+    hsc, ctx, dev = env
+    import torch
+    f = hi.make_frame(2, 4, 4, hi.GRID_31, n_smooth=4, n_saw=0, lights=3, secondary=False)
+    df = upload(hsc, ctx, f, dev)
+    zm = torch.zeros(4, 7, device=dev)          # k not a multiple of 3
+    zl = torch.zeros(3, 7, device=dev)
+    with pytest.raises(hsc.HscError) as ei:
+        hsc.hsc_shade_latent(ctx, df.g1, None, zm, df.lights, zl, hsc.HSC_FUSED, torch.empty(16, 7, device=dev))
+    assert ei.value.status == hsc.HSC_ERR_INVALID_ARG
+    with pytest.raises(hsc.HscError):
+        hsc.hsc_cmf_weights(ctx, 0, 380.0, 5.0, torch.empty(3, 0, device=dev))
+    with pytest.raises(hsc.HscError):
+        hsc.hsc_decode_spectra(ctx, torch.zeros(4, 6, device=dev, dtype=torch.float16), torch.zeros(81, 6, device=dev),
+                               torch.empty(4, 81, device=dev))
+
+
+# ------------------------------------------- the 1920x1080 frame, sampled
+
+@pytest.mark.parametrize("k", [6, 9])
+def test_full_size_1080p_sampled(env, k):
+    # launch configuration of the benchmark: 1920x1080, n = 81, 64 lights,
+    # primary + secondary; the oracle checks 3000 sampled pixels (+ first/last)
+    hsc, ctx, dev = env
+    import torch
+    f = hi.frame_config2()
+    E, D = hi.load_codec(k, 81)
+    df = upload(hsc, ctx, f, dev)
+    zm, zl = encode_all(hsc, ctx, df, E)
+    M = torch.empty(3, k, device=dev)
+    hsc.hsc_fold_xyz(ctx, df.T, torch.from_numpy(D).to(dev), M)
+    lat = torch.empty(f.pixels, k, device=dev)
+    xl = torch.empty(f.pixels, 3, device=dev)
+    lat_p = torch.empty(f.pixels, k, device=dev)
+    xs = torch.empty(f.pixels, 3, device=dev)
+    hsc.hsc_shade_latent(ctx, df.g1, df.g2, zm, df.lights, zl, hsc.HSC_FUSED, lat, xyz_out=xl, M_xyz=M)
+    hsc.hsc_shade_latent(ctx, df.g1, df.g2, zm, df.lights, zl, hsc.HSC_PASSES, lat_p)
+    hsc.hsc_shade_spectral(ctx, df.g1, df.g2, df.mats, df.lights, df.spd, df.T, xs)
+    hsc.hsc_sync(ctx)
+    assert torch.equal(lat, lat_p)
+    rng = np.random.default_rng(k)
+    idx = np.unique(np.concatenate([[0, f.pixels - 1], rng.integers(0, f.pixels, 3000)]))
+    sf = subset_frame(f, idx)
+    z_ref, x_ref = _oracle_latent(sf, E, D)
+    assert rel_err_rows(lat[torch.from_numpy(idx).to(dev)].cpu().numpy(), z_ref) <= TOL
+    assert metrics.rel_xyz_error(xl[torch.from_numpy(idx).to(dev)].cpu().numpy(), x_ref) <= TOL
+    _, xs_ref = shade.shade_spectral(sf, want_spectra=False)
+    assert metrics.rel_xyz_error(xs[torch.from_numpy(idx).to(dev)].cpu().numpy(), xs_ref) <= TOL
+    # invariants at full size: non-negative latent, finite XYZ
+    assert float(lat.min()) >= 0.0 and bool(torch.isfinite(xs).all())

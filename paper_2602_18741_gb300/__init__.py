@@ -5,7 +5,7 @@ has the C entry point's name, takes torch CUDA tensors, checks shapes and
 dtypes, and passes raw device pointers and the current CUDA stream to the
 library.  All arithmetic runs in the library's CUDA kernels; there is no
 fallback.  Importing raises ``ImportError`` when ``libhsc.so`` has not been
-built (``python -m paper_2602_18741_gb300.build``).
+built (``python paper_2602_18741_gb300/build.py``).
 """
 from __future__ import annotations
 
@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhsc.so")
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"libhsc.so is not built at {LIB_PATH}; run `python -m paper_2602_18741_gb300.build`")
+    raise ImportError(f"libhsc.so is not built at {LIB_PATH}; run `python paper_2602_18741_gb300/build.py`")
 
 _lib = ctypes.CDLL(LIB_PATH)
 

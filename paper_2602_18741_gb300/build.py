@@ -1,11 +1,11 @@
 """Build libhsc.so in-tree for GB300 (sm_103a) with nvcc.
 
-    python -m paper_2602_18741_gb300.build [--jobs N] [--debug]
+    python paper_2602_18741_gb300/build.py [--jobs N] [--debug]
 
 Every ``csrc/*.cu`` is compiled to an object in parallel, then linked into
 ``paper_2602_18741_gb300/libhsc.so`` with the CUDA runtime linked statically
-(so the library depends only on the driver).  Objects go to ``_build/`` at the
-repository root.  A translation unit is rebuilt only when it or a header is
+(so the library depends only on the driver).  Objects go to ``_build/<machine>/`` at
+the repository root.  A translation unit is rebuilt only when it or a header is
 newer than its object.
 """
 from __future__ import annotations
@@ -13,6 +13,7 @@ from __future__ import annotations
 import argparse
 import glob
 import os
+import platform
 import subprocess
 import sys
 from concurrent.futures import ThreadPoolExecutor
@@ -20,7 +21,7 @@ from concurrent.futures import ThreadPoolExecutor
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
-BUILD = os.path.join(ROOT, "_build")
+BUILD = os.path.join(ROOT, "_build", platform.machine())
 LIB = os.path.join(PKG, "libhsc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -5,8 +5,9 @@
 
 namespace hsc {
 
-hsc_status validate_gbuffer(const hsc_gbuffer* g, const char* name) {
+hsc_status validate_gbuffer(const hsc_gbuffer* g, const char* name, int64_t pixels) {
   HSC_REQUIRE(g != nullptr, "%s is null", name);
+  if (pixels == 0) return HSC_OK;  // empty images may carry null arrays
   HSC_REQUIRE(g->normal && g->pos && g->mat, "%s has a null array", name);
   HSC_REQUIRE(aligned(g->normal, 4) && aligned(g->pos, 4) && aligned(g->mat, 4), "%s arrays must be 4-byte aligned",
               name);
@@ -31,8 +32,8 @@ static hsc_status validate_common(const hsc_gbuffer* g1, const hsc_gbuffer* g2, 
   HSC_REQUIRE(mat_codes && light_codes, "code arrays are null");
   HSC_REQUIRE(aligned(mat_codes, code_dt == HSC_F32 ? 4 : 2) && aligned(light_codes, code_dt == HSC_F32 ? 4 : 2),
               "code arrays misaligned");
-  HSC_TRY(validate_gbuffer(g1, "g1"));
-  if (g2) HSC_TRY(validate_gbuffer(g2, "g2"));
+  HSC_TRY(validate_gbuffer(g1, "g1", P));
+  if (g2) HSC_TRY(validate_gbuffer(g2, "g2", P));
   HSC_TRY(validate_lights(lights));
   return HSC_OK;
 }
@@ -117,7 +118,7 @@ hsc_status hsc_shade_latent(hsc_ctx* ctx, const hsc_gbuffer* g1, const hsc_gbuff
   HSC_TRY(hsc::validate_common(g1, g2, pixels, mat_codes, n_mat, lights, light_codes, k, code_dt));
   HSC_REQUIRE(mode == HSC_PASSES || mode == HSC_FUSED, "bad mode %d", (int)mode);
   HSC_REQUIRE(latent_dt == HSC_F32 || latent_dt == HSC_FP8_E4M3, "latent dtype must be F32 or FP8_E4M3");
-  HSC_REQUIRE(latent_out != nullptr, "latent_out is null");
+  HSC_REQUIRE(latent_out != nullptr || pixels == 0, "latent_out is null");
   HSC_REQUIRE(latent_dt != HSC_F32 || hsc::aligned(latent_out, 16), "F32 latent_out must be 16-byte aligned");
   HSC_REQUIRE(latent_dt != HSC_FP8_E4M3 || hsc::aligned(latent_out, 4), "fp8 latent_out must be 4-byte aligned");
   HSC_REQUIRE(latent_dt != HSC_FP8_E4M3 || (latent_scales && hsc::aligned(latent_scales, 4)),

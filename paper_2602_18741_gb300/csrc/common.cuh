@@ -32,6 +32,7 @@ struct hsc_ctx {
 
 // Device error flags.
 #define HSC_DEVERR_MATERIAL 1u
+#define HSC_DEVERR_TIMEOUT 2u
 
 namespace hsc {
 

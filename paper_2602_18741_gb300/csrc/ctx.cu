@@ -110,6 +110,8 @@ hsc_status hsc_sync(hsc_ctx* ctx, void* stream) {
   HSC_CUDA(cudaMemcpy(&err, ctx->d_err, sizeof(err), cudaMemcpyDeviceToHost));
   if (err) {
     HSC_CUDA(cudaMemset(ctx->d_err, 0, sizeof(unsigned int)));
+    if (err & HSC_DEVERR_TIMEOUT)
+      return hsc::set_error(HSC_ERR_TIMEOUT, "a bounded device wait expired (flags 0x%x)", err);
     return hsc::set_error(HSC_ERR_DEVICE_CHECK, "device check failed (flags 0x%x)%s", err,
                           (err & HSC_DEVERR_MATERIAL) ? ": material index out of range" : "");
   }

@@ -134,7 +134,7 @@ hsc_status hsc_decode_xyz(hsc_ctx* ctx, const void* latent, hsc_dtype dt, const 
   HSC_REQUIRE(k >= 1 && k <= HSC_MAX_K, "k=%d out of range", k);
   HSC_REQUIRE(pixels >= 0, "negative pixel count");
   HSC_REQUIRE(dt == HSC_F32 || dt == HSC_BF16 || dt == HSC_F16 || dt == HSC_FP8_E4M3, "bad latent dtype");
-  HSC_REQUIRE(latent && M_xyz && (xyz_out || srgb8_out), "null pointer");
+  HSC_REQUIRE(pixels == 0 || (latent && M_xyz && (xyz_out || srgb8_out)), "null pointer");
   HSC_REQUIRE(dt != HSC_FP8_E4M3 || scales, "fp8 latent needs scales");
   HSC_REQUIRE(hsc::aligned(latent, dt == HSC_F32 ? 4 : (dt == HSC_FP8_E4M3 ? 1 : 2)) && hsc::aligned(xyz_out, 4) &&
                   hsc::aligned(M_xyz, 4),
@@ -152,9 +152,9 @@ hsc_status hsc_decode_spectra(hsc_ctx* ctx, const void* latent, hsc_dtype dt, co
   HSC_REQUIRE(k >= 1 && k <= HSC_MAX_K, "k=%d out of range", k);
   HSC_REQUIRE(n >= 1 && n <= HSC_MAX_N, "n=%d out of range", n);
   HSC_REQUIRE(pixels >= 0, "negative pixel count");
+  if (pixels == 0) return HSC_OK;
   HSC_REQUIRE(latent && D && spectra_out, "null pointer");
   HSC_REQUIRE(hsc::aligned(spectra_out, 16), "spectra_out must be 16-byte aligned");
-  if (pixels == 0) return HSC_OK;
   HSC_GUARD(ctx);
   cudaStream_t s = hsc::as_stream(stream);
   if (dt == HSC_F32) {

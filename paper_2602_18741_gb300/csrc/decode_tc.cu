@@ -1,12 +1,274 @@
-// Tensor-core spectral decode (placeholder until the tcgen05 kernel lands).
+// Spectral decode s_hat = W_dec z (Eq. 4) on the 5th-generation tensor cores.
+//
+// Per tile of 128 pixels the decode is one [128 x 16] x [16 x N] BF16 MMA with
+// FP32 accumulation (k <= 16 code channels zero-padded to K = 16, n samples
+// padded to N = 16 * ceil(n / 16)).  The work is HBM-store bound (4n bytes
+// out per pixel against 2*16*N flops), so the kernel is shaped around the
+// output stream:
+//   * persistent CTAs (2 per SM), 128 threads; thread t owns pixel row t;
+//   * the A tile (latent rows, fp8 codes converted exactly to bf16) is written
+//     to shared memory in the no-swizzle K-major canonical layout (8-row x
+//     16-byte core matrices); B = bf16(D * diag(scale)) is staged once;
+//   * one elected thread issues tcgen05.mma into a 128-lane x N-column TMEM
+//     accumulator and commits to an mbarrier;
+//   * each warp reads its 32 TMEM lanes with tcgen05.ld, writes its rows to a
+//     double-buffered [128 x n] FP32 staging tile, and one thread streams the
+//     whole tile (128 * n * 4 contiguous bytes) to global memory with a bulk
+//     async copy (cp.async.bulk), overlapping the next tile's MMA.
+// Every mbarrier wait is bounded; on expiry the kernel sets an error bit,
+// drains its bulk copies, frees its TMEM and returns.
 #include "common.cuh"
 
 namespace hsc {
 
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr int kTcRows = 128;          // MMA M
+constexpr unsigned kTmemCols = 128;   // power of two >= N (N <= 128)
+constexpr unsigned kWaitLimit = 1u << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor (tcgen05 format): start address >> 4 in
+// bits 0-13, leading-dimension byte offset >> 4 in 16-29, stride-dimension
+// byte offset >> 4 in 32-45, the fixed value 0b001 in 46-48, base offset 0,
+// swizzle mode 0 (none) in 61-63.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9 and 10-12 = 1), both K-major, N >> 3 in bits 17-22, M >> 4 in 24-28.
+__host__ __device__ constexpr uint32_t instr_desc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of element (row r, k-element e) in the no-swizzle K-major
+// canonical layout with K = 16 bf16: core matrices of 8 rows x 16 bytes,
+// the two K-halves 128 bytes apart (LBO), 8-row groups 256 bytes apart (SBO).
+__device__ __forceinline__ uint32_t kmajor_off(int r, int e) {
+  return (uint32_t)((r >> 3) * 256 + (e >> 3) * 128 + (r & 7) * 16 + (e & 7) * 2);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+  for (unsigned it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+#define TC_LD16(taddr, v)                                                                                      \
+  asm volatile(                                                                                                \
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];" \
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),        \
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])    \
+      : "r"(taddr))
+
+struct TcArgs {
+  const void* latent;
+  int dt;  // HSC_BF16 or HSC_FP8_E4M3
+  const float* scales;
+  int64_t P;
+  int k;
+  const float* D;  // n x k
+  int n;
+  int npad;  // N of the MMA
+  float* out;
+  unsigned int* err;
+};
+
+template <int NPAD>
+__global__ void __launch_bounds__(kTcThreads) decode_spectra_tc_kernel(const TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* sA = base;                       // 128 x 16 bf16 = 4096 B
+  unsigned char* sB = base + 4096;                // NPAD x 16 bf16
+  float* sOut = reinterpret_cast<float*>(base + 4096 + NPAD * 32);  // 2 x [128 x n]
+  uint64_t* sBar = reinterpret_cast<uint64_t*>(sOut + 2 * kTcRows * a.n + 4);
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(sBar + 1);
+  int* sOk = reinterpret_cast<int*>(sTmem + 1);
+
+  const int t = threadIdx.x;
+  const int warp = t >> 5;
+  const int n = a.n;
+
+  // TMEM allocation (one warp), mbarrier init, B staging.
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(sTmem)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(sBar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *sOk = 1;
+  }
+  for (int idx = t; idx < NPAD * 16; idx += kTcThreads) {
+    const int r = idx >> 4, e = idx & 15;
+    float v = 0.0f;
+    if (r < n && e < a.k) {
+      v = __ldg(a.D + r * a.k + e);
+      if (a.dt == HSC_FP8_E4M3) v = __fmul_rn(v, __ldg(a.scales + e));
+    }
+    *reinterpret_cast<__nv_bfloat16*>(sB + kmajor_off(r, e)) = __float2bfloat16_rn(v);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *sTmem;
+  const uint32_t bar = smem_u32(sBar);
+  const uint64_t adesc = smem_desc(smem_u32(sA), 128, 256);
+  const uint64_t bdesc = smem_desc(smem_u32(sB), 128, 256);
+  constexpr uint32_t idesc = instr_desc_bf16(kTcRows, NPAD);
+
+  const int64_t tiles = (a.P + kTcRows - 1) / kTcRows;
+  uint32_t phase = 0;
+  int it = 0;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
+    const int64_t p0 = tile * kTcRows;
+    const int rows = (int)min((int64_t)kTcRows, a.P - p0);
+    // A tile: row t = pixel p0 + t, zero beyond P and beyond k.
+    {
+      const int64_t p = p0 + t;
+      uint32_t w[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) w[j] = 0u;
+      if (t < rows) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          if (e >= a.k) break;
+          float v;
+          if (a.dt == HSC_FP8_E4M3)
+            v = fp8_e4m3_to_float(__ldg(reinterpret_cast<const unsigned char*>(a.latent) + p * a.k + e));
+          else
+            v = __uint_as_float(((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(a.latent) + p * a.k + e)) << 16);
+          const uint32_t b = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v));
+          w[e >> 1] |= b << ((e & 1) * 16);
+        }
+      }
+      uint4* dst0 = reinterpret_cast<uint4*>(sA + kmajor_off(t, 0));
+      uint4* dst1 = reinterpret_cast<uint4*>(sA + kmajor_off(t, 8));
+      *dst0 = make_uint4(w[0], w[1], w[2], w[3]);
+      *dst1 = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (t == 0) {
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+          "l"(adesc), "l"(bdesc), "r"(idesc), "r"(0)
+          : "memory");
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+      if (!mbar_wait(bar, phase)) {
+        *sOk = 0;
+        atomicOr(a.err, HSC_DEVERR_TIMEOUT);
+      }
+      // the staging buffer of this iteration was last stored two tiles ago
+      asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+    }
+    __syncthreads();
+    if (!*sOk) break;
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    float* stage = sOut + (it & 1) * (kTcRows * n);
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    const bool full = rows == kTcRows;
+#pragma unroll
+    for (int c0 = 0; c0 < NPAD; c0 += 16) {
+      uint32_t v[16];
+      TC_LD16(trow + (uint32_t)c0, v);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int c = c0 + j;
+        if (c < n) {
+          const float x = __uint_as_float(v[j]);
+          if (full)
+            stage[t * n + c] = x;
+          else if (t < rows)
+            a.out[(p0 + t) * n + c] = x;
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    if (full) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (t == 0) {
+        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(a.out + p0 * n),
+                     "r"(smem_u32(stage)), "r"((uint32_t)(kTcRows * n * 4))
+                     : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      }
+    }
+  }
+  if (t == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+template <int NPAD>
+hsc_status launch_tc(const TcArgs& a, int sm_count, cudaStream_t s) {
+  const size_t smem = 1024 + 4096 + NPAD * 32 + (size_t)2 * kTcRows * a.n * 4 + 64;
+  auto kern = decode_spectra_tc_kernel<NPAD>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return set_error(HSC_ERR_CUDA, "smem attribute: %s", cudaGetErrorString(e));
+  const int64_t tiles = (a.P + kTcRows - 1) / kTcRows;
+  int per_sm = smem <= 100 * 1024 ? 2 : 1;   // at most 2 x 128 TMEM columns per SM
+  int64_t grid = (int64_t)sm_count * per_sm;
+  if (grid > tiles) grid = tiles;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, kTcThreads, smem, s>>>(a);
+  return check_launch("decode_spectra_tc_kernel");
+}
+
+}  // namespace
+
 hsc_status launch_decode_spectra_tc(hsc_ctx* ctx, const void* latent, int dt, const float* scales, int64_t P, int k,
                                     const float* D, int n, float* out, cudaStream_t s) {
-  (void)ctx; (void)latent; (void)dt; (void)scales; (void)P; (void)k; (void)D; (void)n; (void)out; (void)s;
-  return set_error(HSC_ERR_UNSUPPORTED, "tensor-core decode not built");
+  TcArgs a{};
+  a.latent = latent;
+  a.dt = dt;
+  a.scales = scales;
+  a.P = P;
+  a.k = k;
+  a.D = D;
+  a.n = n;
+  a.npad = (n + 15) / 16 * 16;
+  a.out = out;
+  a.err = ctx->d_err;
+  switch (a.npad) {
+    case 16: return launch_tc<16>(a, ctx->sm_count, s);
+    case 32: return launch_tc<32>(a, ctx->sm_count, s);
+    case 48: return launch_tc<48>(a, ctx->sm_count, s);
+    case 64: return launch_tc<64>(a, ctx->sm_count, s);
+    case 80: return launch_tc<80>(a, ctx->sm_count, s);
+    case 96: return launch_tc<96>(a, ctx->sm_count, s);
+    case 112: return launch_tc<112>(a, ctx->sm_count, s);
+    default: return launch_tc<128>(a, ctx->sm_count, s);
+  }
 }
 
 }  // namespace hsc

@@ -187,7 +187,7 @@ hsc_status launch_spec_sec(const SpecArgs& a, bool sec, int sm_count, cudaStream
 
 }  // namespace
 
-hsc_status validate_gbuffer(const hsc_gbuffer* g, const char* name);
+hsc_status validate_gbuffer(const hsc_gbuffer* g, const char* name, int64_t pixels);
 hsc_status validate_lights(const hsc_lights* l);
 
 }  // namespace hsc
@@ -201,12 +201,12 @@ extern "C" hsc_status hsc_shade_spectral(hsc_ctx* ctx, const hsc_gbuffer* g1, co
   HSC_REQUIRE(pixels >= 0, "negative pixel count");
   HSC_REQUIRE(n >= 1 && n <= HSC_MAX_N, "n=%d out of range [1, %d]", n, HSC_MAX_N);
   HSC_REQUIRE(n_mat >= 1 && n_mat <= HSC_MAX_MAT, "n_mat=%d out of range", n_mat);
-  HSC_REQUIRE(mat_spectra && light_spd && T && xyz_out, "null pointer");
+  HSC_REQUIRE(mat_spectra && light_spd && T && (xyz_out || pixels == 0), "null pointer");
   HSC_REQUIRE(hsc::aligned(mat_spectra, 4) && hsc::aligned(light_spd, 4) && hsc::aligned(T, 4) &&
                   hsc::aligned(xyz_out, 4) && (!spectra_out || hsc::aligned(spectra_out, 4)),
               "misaligned pointer");
-  HSC_TRY(hsc::validate_gbuffer(g1, "g1"));
-  if (g2) HSC_TRY(hsc::validate_gbuffer(g2, "g2"));
+  HSC_TRY(hsc::validate_gbuffer(g1, "g1", pixels));
+  if (g2) HSC_TRY(hsc::validate_gbuffer(g2, "g2", pixels));
   HSC_TRY(hsc::validate_lights(lights));
   if (pixels == 0) return HSC_OK;
   HSC_GUARD(ctx);

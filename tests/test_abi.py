@@ -18,8 +18,8 @@ def _declared():
 
 @pytest.fixture(scope="module")
 def lib_path():
-    from paper_2602_18741_gb300 import build
-    return build.build()
+    import __graft_entry__
+    return __graft_entry__._build_module().build()
 
 
 def test_header_declares_the_entry_points():

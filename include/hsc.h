@@ -63,6 +63,7 @@ extern "C" {
 #define HSC_MAX_K 96      /* code length limit (multiple of 3)            */
 #define HSC_MAX_N 128     /* spectral sample limit                        */
 #define HSC_MAX_MAT (1 << 24)
+#define HSC_NOALLOC_MAX_K 96  /* channel limit of hsc_quantize_fp8_noalloc   */
 
 typedef struct hsc_ctx hsc_ctx;
 
@@ -188,6 +189,27 @@ HSC_API hsc_status hsc_shade_latent(hsc_ctx* ctx, const hsc_gbuffer* g1, const h
  * Uses the context's reduction scratch.                                      */
 HSC_API hsc_status hsc_quantize_fp8(hsc_ctx* ctx, const float* latent, int64_t pixels, int k,
                             uint8_t* codes_out, float* scales_out, void* stream);
+
+/* Allocation-free fp8 quantiser.  The paper has no counterpart: this entry
+ * point exists for callers that may not allocate device memory at all -- for
+ * example a plugin inside a host renderer that owns the GPU's memory budget
+ * through its own allocator, or a frame loop with a hard deadline that cannot
+ * afford cudaMalloc's device-wide synchronisation.  Those callers cannot use
+ * hsc_create (it allocates), so this call needs no context.
+ * It computes exactly what hsc_quantize_fp8 computes.  Its only scratch, one
+ * max word per channel, is a static device array of HSC_NOALLOC_MAX_K words
+ * (384 bytes) that every GPU loading the library holds until process exit;
+ * k > HSC_NOALLOC_MAX_K is rejected with HSC_ERR_INVALID_ARG.
+ *   Runs on the calling thread's current device.  The first call on a device
+ *   looks up the array's device address (cudaGetSymbolAddress) and caches it;
+ *   make that first call before any stream capture.  Each call clears the
+ *   words it uses, but all calls share the one array: calls whose work
+ *   overlaps on the GPU (other streams, other threads) race on it and must be
+ *   serialised by the caller.  Allocates nothing: no cudaMalloc, no cudaFree.
+ *   latent: device P x k float32 (16-byte aligned);  codes_out: device P x k
+ *   bytes (4-byte aligned);  scales_out: device k float32.                    */
+HSC_API hsc_status hsc_quantize_fp8_noalloc(const float* latent, int64_t pixels, int k, uint8_t* codes_out,
+                                            float* scales_out, void* stream);
 
 /* ------------------------------------------------------------------ decode */
 

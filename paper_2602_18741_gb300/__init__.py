@@ -29,6 +29,7 @@ HSC_OK, HSC_ERR_INVALID_ARG, HSC_ERR_CUDA, HSC_ERR_OOM, HSC_ERR_UNSUPPORTED, HSC
 HSC_F32, HSC_BF16, HSC_F16, HSC_FP8_E4M3 = range(4)
 HSC_PASSES, HSC_FUSED = range(2)
 HSC_MAX_K = 96
+HSC_NOALLOC_MAX_K = 96
 HSC_MAX_N = 128
 
 STATUS_NAMES = {0: "HSC_OK", 1: "HSC_ERR_INVALID_ARG", 2: "HSC_ERR_CUDA", 3: "HSC_ERR_OOM",
@@ -74,6 +75,7 @@ _SIGS = {
     "hsc_shade_latent": ([_vp, _GB, _GB, _i64, _vp, _i32, _LI, _vp, _i32, _i32, _i32, _vp, _i32, _vp, _vp, _vp,
                           _vp], _i32),
     "hsc_quantize_fp8": ([_vp, _vp, _i64, _i32, _vp, _vp, _vp], _i32),
+    "hsc_quantize_fp8_noalloc": ([_vp, _i64, _i32, _vp, _vp, _vp], _i32),
     "hsc_decode_xyz": ([_vp, _vp, _i32, _vp, _i64, _i32, _vp, _vp, _vp, _vp], _i32),
     "hsc_decode_spectra": ([_vp, _vp, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _vp], _i32),
     "hsc_shade_spectral": ([_vp, _GB, _GB, _i64, _vp, _i32, _LI, _vp, _i32, _vp, _vp, _vp, _vp], _i32),
@@ -256,6 +258,14 @@ def hsc_quantize_fp8(ctx: Context, latent: torch.Tensor, codes_out: torch.Tensor
     P, k = latent.shape
     _check(_lib.hsc_quantize_fp8(ctx.handle, _ptr(latent), int(P), int(k), _ptr(codes_out), _ptr(scales_out),
                                  _stream(stream)))
+
+
+def hsc_quantize_fp8_noalloc(latent: torch.Tensor, codes_out: torch.Tensor, scales_out: torch.Tensor, stream=None):
+    """Same result as hsc_quantize_fp8, for callers that may not allocate:
+    needs no Context, runs on the current device, scratch in a static array."""
+    P, k = latent.shape
+    _check(_lib.hsc_quantize_fp8_noalloc(_ptr(latent), int(P), int(k), _ptr(codes_out), _ptr(scales_out),
+                                         _stream(stream)))
 
 
 def hsc_decode_xyz(ctx: Context, latent: torch.Tensor, M_xyz: torch.Tensor, xyz_out: torch.Tensor,

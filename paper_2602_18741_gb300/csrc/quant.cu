@@ -6,6 +6,8 @@
 #include "common.cuh"
 #include "shade_latent.cuh"
 
+#include <mutex>
+
 namespace hsc {
 
 namespace {
@@ -116,4 +118,73 @@ extern "C" hsc_status hsc_quantize_fp8(hsc_ctx* ctx, const float* latent, int64_
   HSC_CUDA(cudaMemsetAsync(chan_max, 0, sizeof(unsigned int) * k, s));
   if (pixels > 0) HSC_TRY(hsc::launch_channel_max(latent, pixels, k, chan_max, ctx->sm_count, s));
   return hsc::launch_quantize(latent, pixels, k, chan_max, codes_out, scales_out, ctx->sm_count, s);
+}
+
+namespace hsc {
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the quantiser.
+//
+// Some callers of this library may not allocate device memory at all: a
+// plugin that runs inside a host renderer which owns the GPU's whole memory
+// budget through its own allocator, or a frame loop with a hard deadline in
+// which cudaMalloc (which can synchronise the whole device) is not allowed.
+// Such callers cannot create an hsc_ctx either, because hsc_create allocates
+// the context's scratch.  hsc_quantize_fp8_noalloc serves them: its only
+// scratch, one max word per channel, is the file-scope array below.  The
+// array is part of the library's device code, so every GPU on which the
+// library is loaded holds its 384 bytes until the process exits.
+static __device__ __align__(256) unsigned int g_noalloc_chan_max[HSC_NOALLOC_MAX_K];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned int* g_noalloc_ptr[kMaxDevices];  // device address of g_noalloc_chan_max, per device
+int g_noalloc_sms[kMaxDevices];
+
+// One-time set-up per device, with that device current: the array's name in
+// host code is only a host-side stand-in, so its device address is fetched
+// with cudaGetSymbolAddress and cached.
+hsc_status noalloc_setup(int dev, unsigned int** ptr, int* sms) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_chan_max);
+    if (e != cudaSuccess) return set_error(HSC_ERR_CUDA, "cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    int sm = 0;
+    e = cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return set_error(HSC_ERR_CUDA, "cudaDeviceGetAttribute failed: %s", cudaGetErrorString(e));
+    g_noalloc_sms[dev] = sm > 0 ? sm : 1;
+    g_noalloc_ptr[dev] = reinterpret_cast<unsigned int*>(p);
+  }
+  *ptr = g_noalloc_ptr[dev];
+  *sms = g_noalloc_sms[dev];
+  return HSC_OK;
+}
+
+}  // namespace
+
+}  // namespace hsc
+
+extern "C" hsc_status hsc_quantize_fp8_noalloc(const float* latent, int64_t pixels, int k, uint8_t* codes_out,
+                                               float* scales_out, void* stream) {
+  hsc::clear_error();
+  HSC_REQUIRE(k >= 1 && k <= HSC_NOALLOC_MAX_K,
+              "k=%d exceeds the allocation-free quantiser's maximum of %d channels", k, HSC_NOALLOC_MAX_K);
+  HSC_REQUIRE(pixels >= 0, "negative pixel count");
+  HSC_REQUIRE(latent && codes_out && scales_out, "null pointer");
+  HSC_REQUIRE(hsc::aligned(latent, 16) && hsc::aligned(codes_out, 4) && hsc::aligned(scales_out, 4),
+              "latent must be 16-byte and codes 4-byte aligned");
+  int dev = 0;
+  HSC_CUDA(cudaGetDevice(&dev));
+  HSC_REQUIRE(dev >= 0 && dev < hsc::kMaxDevices, "device %d beyond the supported %d", dev, hsc::kMaxDevices);
+  unsigned int* chan_max = nullptr;
+  int sms = 1;
+  HSC_TRY(hsc::noalloc_setup(dev, &chan_max, &sms));
+  cudaStream_t s = hsc::as_stream(stream);
+  // the array keeps the previous call's maxima: clear the channels used here
+  HSC_CUDA(cudaMemsetAsync(chan_max, 0, sizeof(unsigned int) * k, s));
+  if (pixels > 0) HSC_TRY(hsc::launch_channel_max(latent, pixels, k, chan_max, sms, s));
+  return hsc::launch_quantize(latent, pixels, k, chan_max, codes_out, scales_out, sms, s);
 }

@@ -160,6 +160,7 @@ def run_hsc(args, rank: int, world: int):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     ctx = hsc.Context(dev.index)
+    hsc.hsc_set_autotune(ctx, True)   # tile shape / pixels per thread picked on the first (warm-up) call
     stream = torch.cuda.current_stream()
     k = args.k
 
@@ -269,6 +270,7 @@ def run_hsc(args, rank: int, world: int):
                     "kernel": "shade_codes_kernel<6,PPT,true> (fused latent shade + XYZ)",
                     "ops_per_eval": ops_per_eval, "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x {peak_mhz:.0f} MHz"}
         e2e = e2e_leg(args, hsc, ctx, f, dev, stream, Ed, M, evals)
+        tune = [ln for ln in hsc.hsc_tune_report(ctx).splitlines() if ln.strip()]
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             rate, nrows, secs = oracle_rate(args.cpu_seconds, k, threads=1)
@@ -284,7 +286,7 @@ def run_hsc(args, rank: int, world: int):
                        "parallelism": f"replicas x{world}"},
             "frame_ms": {"p50": _pct(per_step, 50), "p99": _pct(per_step, 99), "min": min(per_step)},
             "gpu_launches": gpu_launches_per_step * args.steps,
-            "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "rows": rows,
+            "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "rows": rows, "autotune": tune,
             "wall_s_timed_region": round(wall, 4),
         }
     ctx.close()
@@ -387,6 +389,34 @@ def secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T,
     rows["decode_spectra_f32"] = {"ms": dms, "GB_per_s": dbytes / (dms * 1e-3) / 1e9,
                                   "Mpx_per_s": P / (dms * 1e-3) / 1e6, "bytes": dbytes}
 
+    # tensor-core decode (tcgen05, BF16 operands, FP32 accumulation) from a
+    # bf16 latent and from an fp8 latent with per-channel scales, at 1920x1080
+    # and at 3840x2160 (four copies of the frame's latent image)
+    lat_bf = lat.to(torch.bfloat16)
+    codes = torch.empty(P, args.k, device=dev, dtype=torch.uint8)
+    scales = torch.empty(args.k, device=dev)
+    hsc.hsc_quantize_fp8(ctx, lat, codes, scales)
+    for tag, src, sc, esz in (("bf16", lat_bf, None, 2), ("fp8", codes, scales, 1)):
+        def dtc(src=src, sc=sc):
+            hsc.hsc_decode_spectra(ctx, src, Dd, spec_out, scales=sc)
+        ms, _ = timed(dtc, K, W)
+        m_ = statistics.mean(ms)
+        b_ = P * (args.k * esz + 81 * 4)
+        rows[f"decode_spectra_tc_{tag}_1080p"] = {"ms": m_, "GB_per_s": b_ / (m_ * 1e-3) / 1e9,
+                                                  "Mpx_per_s": P / (m_ * 1e-3) / 1e6, "bytes": b_}
+    del spec_out
+    P4 = 4 * P
+    out4 = torch.empty(P4, 81, device=dev)
+    for tag, src, sc, esz in (("bf16", lat_bf.repeat(4, 1), None, 2), ("fp8", codes.repeat(4, 1), scales, 1)):
+        def dtc4(src=src, sc=sc):
+            hsc.hsc_decode_spectra(ctx, src, Dd, out4, scales=sc)
+        ms, _ = timed(dtc4, K, W)
+        m_ = statistics.mean(ms)
+        b_ = P4 * (args.k * esz + 81 * 4)
+        rows[f"decode_spectra_tc_{tag}_4k"] = {"ms": m_, "GB_per_s": b_ / (m_ * 1e-3) / 1e9,
+                                               "Mpx_per_s": P4 / (m_ * 1e-3) / 1e6, "bytes": b_}
+    del out4
+
     xyz_only = torch.empty(P, 3, device=dev)
 
     def decx():
@@ -413,7 +443,61 @@ def secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T,
                                           "de2000_p95": float(s[1]), "de94_mean": float(s[2]),
                                           "de76_mean": float(s[3])}
     hsc.hsc_sync(ctx)
+    rows.update(batch_rows(args, hsc, ctx, dev, timed))
     return rows
+
+
+def batch_rows(args, hsc, ctx, dev, timed):
+    """64 frames of uneven size (W, H uniform in [256, 2048]), 4-256 lights,
+    k in {6, 9}, n in {31, 81}, each with its own jittered codec, shaded and
+    decoded to XYZ by one persistent launch replayed as a CUDA graph; codes in
+    FP32 and in BF16.  G-buffers are drawn on the device with the same recipe
+    as the host generator."""
+    import torch
+    specs = hi.batched_frame_specs()
+    gen = torch.Generator(device=dev)
+    keep = []
+    frames = {torch.float32: [], torch.bfloat16: []}
+    Ts = {}
+    for s in specs:
+        gen.manual_seed(s.seed)
+        (n1, x1, m1), _ = hi.torch_gbuffers(gen, s.pixels, 64, False, dev)
+        mats, spd, lpos, linten = hi.frame_assets(s)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        g1 = hsc.GBuffer(n1, x1, m1)
+        lights = hsc.Lights(t(lpos), t(linten))
+        if s.grid not in Ts:
+            T = torch.empty(3, s.grid[2], device=dev)
+            hsc.hsc_cmf_weights(ctx, s.grid[2], s.grid[0], s.grid[1], T)
+            Ts[s.grid] = T
+        Ed, Dd = t(s.E), t(s.D)
+        M = torch.empty(3, s.k, device=dev)
+        hsc.hsc_fold_xyz(ctx, Ts[s.grid], Dd, M)
+        xyz = torch.empty(s.pixels, 3, device=dev)
+        for dt in frames:
+            zm = torch.empty(mats.shape[0], s.k, device=dev, dtype=dt)
+            zl = torch.empty(s.lights, s.k, device=dev, dtype=dt)
+            hsc.hsc_encode(ctx, Ed, t(mats), zm)
+            hsc.hsc_encode(ctx, Ed, t(spd), zl)
+            frames[dt].append(hsc.BatchFrame(g1, None, zm, lights, zl, M, xyz))
+        keep.append((g1, lights, Ed, Dd, M, xyz))
+    px = sum(s.pixels for s in specs)
+    evals = sum(s.pixels * s.lights for s in specs)
+    out = {}
+    for dt, name in ((torch.float32, "f32"), (torch.bfloat16, "bf16")):
+        batch = hsc.hsc_batch_create(ctx, frames[dt])
+
+        def run(batch=batch):
+            hsc.hsc_batch_shade(ctx, batch)
+
+        ms, _ = timed(run, args.steps, args.warmup)
+        m_ = statistics.mean(ms)
+        out[f"batch64_{name}"] = {"ms": m_, "frames_per_s": len(specs) / (m_ * 1e-3), "Mpx_per_s": px / (m_ * 1e-3) / 1e6,
+                                  "evals_per_s": evals / (m_ * 1e-3), "pixels": px, "evals": evals,
+                                  "p50_ms": _pct(ms, 50), "p99_ms": _pct(ms, 99)}
+        batch.close()
+    hsc.hsc_sync(ctx)
+    return out
 
 
 def _M(hsc, ctx, T, Dd):

@@ -302,30 +302,109 @@ def load_codec(k: int, n: int):
 # Batched frames and request streams
 # ----------------------------------------------------------------------------
 
-def batched_frames(seed: int = MASTER_SEED + 4, count: int = 64, min_side: int = 256,
-                   max_side: int = 2048, min_lights: int = 4, max_lights: int = 256,
-                   ks=(6, 9), grids=(GRID_31, GRID_81), secondary: bool = False):
+@dataclass
+class FrameSpec:
+    """Parameters of one frame of a batch (materialised by make_frame or on
+    the device by torch_frame)."""
+    width: int
+    height: int
+    grid: tuple
+    lights: int
+    k: int
+    seed: int
+    E: np.ndarray
+    D: np.ndarray
+    secondary: bool = False
+
+    @property
+    def pixels(self) -> int:
+        return self.width * self.height
+
+
+def batched_frame_specs(seed: int = MASTER_SEED + 4, count: int = 64, min_side: int = 256,
+                        max_side: int = 2048, min_lights: int = 4, max_lights: int = 256,
+                        ks=(6, 9), grids=(GRID_31, GRID_81), secondary: bool = False):
     """Frames of uneven size for a batched launch: W, H independent uniform
     integers in [min_side, max_side], L uniform in [min_lights, max_lights],
     k and n uniform over the given choices; each frame carries its own codec,
-    a stored base codec times a seeded multiplicative jitter U[0.9, 1.1]."""
+    a stored base codec times a seeded multiplicative jitter U[0.9, 1.1]
+    (which keeps it non-negative)."""
     (r,) = streams(seed, 1)
     out = []
-    for i in range(count):
+    for _ in range(count):
         w = int(r.integers(min_side, max_side + 1))
         h = int(r.integers(min_side, max_side + 1))
         L = int(r.integers(min_lights, max_lights + 1))
         k = int(ks[r.integers(0, len(ks))])
         g = grids[r.integers(0, len(grids))]
         fseed = int(r.integers(0, 2**31 - 1))
-        f = make_frame(fseed, w, h, g, n_smooth=48, n_saw=16, lights=L, secondary=secondary)
         E, D = load_codec(k, g[2])
         jE = r.uniform(0.9, 1.1, size=E.shape).astype(np.float32)
         jD = r.uniform(0.9, 1.1, size=D.shape).astype(np.float32)
-        f.meta.update(k=k, E=(E * jE).astype(np.float32), D=(D * jD).astype(np.float32),
-                      name=f"batch[{i}] {w}x{h} L={L} k={k} n={g[2]}")
-        out.append(f)
+        out.append(FrameSpec(w, h, tuple(g), L, k, fseed, (E * jE).astype(np.float32),
+                             (D * jD).astype(np.float32), secondary))
     return out
+
+
+def frame_assets(spec: FrameSpec, n_smooth: int = 48, n_saw: int = 16):
+    """The spectral assets and lights of a batch frame (the same draws as
+    frame_from_spec, without the G-buffer): materials (m, n), light SPDs
+    (L, n), light positions (L, 3), intensities (L,)."""
+    _, r_mat, r_light, r_spd = streams(spec.seed, 4)
+    lam = grid(*spec.grid)
+    mats = np.concatenate([smooth_reflectances(r_mat, lam, n_smooth),
+                           sawtooth_reflectances(r_mat, lam, n_saw)], axis=0)
+    n_bb = spec.lights // 2
+    n_nb = spec.lights - n_bb
+    spd = np.concatenate([
+        blackbody(lam, r_spd.uniform(2000.0, 10000.0, size=n_bb)),
+        narrowband(lam, r_spd.uniform(400.0, 700.0, size=n_nb), r_spd.uniform(5.0, 20.0, size=n_nb))], axis=0)
+    lpos, linten = light_positions(r_light, spec.lights)
+    return mats.astype(np.float32), spd.astype(np.float32), lpos, linten
+
+
+def frame_from_spec(spec: FrameSpec, n_smooth: int = 48, n_saw: int = 16) -> Frame:
+    """Host (numpy) frame of a batch spec."""
+    f = make_frame(spec.seed, spec.width, spec.height, spec.grid, n_smooth=n_smooth, n_saw=n_saw,
+                   lights=spec.lights, secondary=spec.secondary)
+    f.meta.update(k=spec.k, E=spec.E, D=spec.D)
+    return f
+
+
+def torch_gbuffers(gen, pixels: int, n_mat: int, secondary: bool, device):
+    """The gbuffers() recipe drawn with a torch generator on a device (for
+    large benchmark batches, where drawing on the host would dominate).
+    Returns (normal, pos, mat) tuples for the primary and, optionally, the
+    secondary G-buffer, float32 / int32."""
+    import torch
+    kw = dict(generator=gen, device=device)
+
+    def hemi(count):
+        z = torch.rand(count, **kw)
+        phi = torch.rand(count, **kw) * (2.0 * math.pi)
+        r = torch.sqrt(torch.clamp(1.0 - z * z, min=0.0))
+        return torch.stack([r * torch.cos(phi), r * torch.sin(phi), z], dim=1)
+
+    def sphere(count):
+        z = torch.rand(count, **kw) * 2.0 - 1.0
+        phi = torch.rand(count, **kw) * (2.0 * math.pi)
+        r = torch.sqrt(torch.clamp(1.0 - z * z, min=0.0))
+        return torch.stack([r * torch.cos(phi), r * torch.sin(phi), z], dim=1)
+
+    def unit(v):
+        return (v / torch.linalg.norm(v, dim=1, keepdim=True)).float().contiguous()
+
+    n1 = unit(hemi(pixels))
+    x1 = torch.rand(pixels, 3, **kw).float().contiguous()
+    m1 = torch.randint(0, n_mat, (pixels,), **kw, dtype=torch.int32)
+    if not secondary:
+        return (n1, x1, m1), None
+    x2 = torch.rand(pixels, 3, **kw).float().contiguous()
+    back = x1 - x2
+    back = back / torch.clamp(torch.linalg.norm(back, dim=1, keepdim=True), min=1e-6)
+    n2 = unit(back + 0.8 * sphere(pixels))
+    m2 = torch.randint(0, n_mat, (pixels,), **kw, dtype=torch.int32)
+    return (n1, x1, m1), (n2, x2, m2)
 
 
 SERVE_SIZES = ((512, 512), (1024, 1024), (1920, 1080), (2048, 2048), (3840, 2160))

@@ -120,6 +120,26 @@ HSC_API hsc_status hsc_reserve(hsc_ctx* ctx, size_t bytes);
  * and `latent_dt`.                                                           */
 HSC_API size_t hsc_shade_latent_scratch_bytes(int64_t pixels, int k, hsc_mode mode, hsc_dtype latent_dt);
 
+/* Launch-configuration autotuning of the shading kernels.  The tile shape
+ * (threads per CTA, pixels per thread, persistent or one-CTA-per-tile grid)
+ * never changes what a channel computes, only how fast.  enable = 0 (the
+ * default): fixed defaults.  enable = 1: the first call of each shape class
+ * (kernel, channels, bounce on/off, light and pixel counts rounded up to
+ * powers of two) times every candidate on its own inputs -- synchronising
+ * the stream once -- and caches the fastest; calls made while a stream is
+ * captured never tune.                                                      */
+HSC_API hsc_status hsc_set_autotune(hsc_ctx* ctx, int enable);
+/* Text table of the tuned shape classes and candidate timings (valid until
+ * the next tuning call on this context).                                   */
+HSC_API const char* hsc_tune_report(hsc_ctx* ctx);
+/* Force one launch configuration for every shading launch (testing and
+ * benchmarking): ppt in {1, 2, 4} (spectral kernel: 1 or 2 shading points per
+ * thread), block in {128, 256}, waves >= 0 (0 = one CTA per pixel tile),
+ * vec = 1 (scalar FP32) or 2 (packed f32x2 pairs: pairs of shading points in
+ * the latent kernels, pairs of wavelengths in the spectral kernel).  ppt <= 0
+ * removes the override.                                                     */
+HSC_API hsc_status hsc_force_launch_config(hsc_ctx* ctx, int ppt, int block, int waves, int vec);
+
 /* ----------------------------------------------------- colour projection */
 
 /* Integration weights of the CIE 1931 2-degree observer on the grid
@@ -141,8 +161,9 @@ HSC_API hsc_status hsc_fold_xyz(hsc_ctx* ctx, const float* T, const float* D, in
 /* ------------------------------------------------------------------ encode */
 
 /* Encode m spectra (Eq. 4, z = W_enc s); the paper encodes every spectral
- * asset a single time per scene (Fig. 2b): codes[j][c] = sum_i E[c][i] spectra[j][i], FP32 sums in
- * order of i, stored as `out_dt` (F32, BF16 or F16, round-to-nearest-even).
+ * asset a single time per scene (Fig. 2b): codes[j][c] = sum_i E[c][i] spectra[j][i], FP32
+ * (per-lane partial sums, then a fixed butterfly), stored as `out_dt` (F32, BF16 or F16,
+ * round-to-nearest-even).
  *   E: device k x n float32;  spectra: device m x n float32;
  *   codes_out: device m x k of out_dt.  1 <= n <= HSC_MAX_N, 1 <= k <= HSC_MAX_K. */
 HSC_API hsc_status hsc_encode(hsc_ctx* ctx, const float* E, int k, int n, const float* spectra, int m,
@@ -247,6 +268,45 @@ HSC_API hsc_status hsc_shade_spectral(hsc_ctx* ctx, const hsc_gbuffer* g1, const
                               const float* mat_spectra, int n_mat, const hsc_lights* lights,
                               const float* light_spd, int n, const float* T,
                               float* xyz_out, float* spectra_out, void* stream);
+
+/* ------------------------------------------------------------ batched frames */
+
+/* One frame of a batched launch: its own G-buffer(s), codes (from its own
+ * codec), lights, code length and folded decode matrix.  Pointers are
+ * device pointers, as in hsc_shade_latent.                                  */
+typedef struct {
+  hsc_gbuffer g1;
+  hsc_gbuffer g2;          /* used when has_g2 != 0                          */
+  int32_t has_g2;
+  int64_t pixels;
+  const void* mat_codes;   /* n_mat x k of code_dt                           */
+  int32_t n_mat;
+  hsc_lights lights;
+  const void* light_codes; /* L x k of code_dt                               */
+  int32_t k;               /* 6 or 9                                         */
+  hsc_dtype code_dt;       /* F32, BF16 or F16                               */
+  const float* M_xyz;      /* 3 x k                                          */
+  float* xyz_out;          /* P x 3 float32                                  */
+  float* latent_out;       /* P x k float32, or NULL                         */
+} hsc_frame;
+
+typedef struct hsc_batch hsc_batch;
+
+/* Prepare a batch of frames of uneven size, light count, k and codec for
+ * one persistent latent-shading launch with the XYZ decode fused (the
+ * batched-serving extension; the paper renders one frame at a time).  Copies
+ * the frame descriptors to the device, picks the tile shape (pixels per
+ * thread, threads per CTA, scalar or f32x2) by timing every candidate on the
+ * batch when autotuning is on (hsc_set_autotune), and records a CUDA graph of
+ * the launch.  Synchronous; allocates the batch's own descriptors.  Every
+ * frame's result is bit-identical to shading that frame alone with
+ * hsc_shade_latent.  The frames' buffers must stay valid while the batch
+ * exists.                                                                    */
+HSC_API hsc_status hsc_batch_create(hsc_ctx* ctx, const hsc_frame* frames, int count, hsc_batch** out);
+/* Replay the batch's graph on `stream` (queue reset + one kernel).          */
+HSC_API hsc_status hsc_batch_shade(hsc_ctx* ctx, hsc_batch* batch, void* stream);
+/* Synchronise the device and free the batch.                                */
+HSC_API void hsc_batch_destroy(hsc_batch* batch);
 
 /* ----------------------------------------------------------------- metrics */
 

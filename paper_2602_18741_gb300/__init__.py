@@ -53,6 +53,13 @@ class _Lights(ctypes.Structure):
     _fields_ = [("pos", ctypes.c_void_p), ("intensity", ctypes.c_void_p), ("count", ctypes.c_int32)]
 
 
+class _Frame(ctypes.Structure):
+    _fields_ = [("g1", _GBuffer), ("g2", _GBuffer), ("has_g2", ctypes.c_int32), ("pixels", ctypes.c_int64),
+                ("mat_codes", ctypes.c_void_p), ("n_mat", ctypes.c_int32), ("lights", _Lights),
+                ("light_codes", ctypes.c_void_p), ("k", ctypes.c_int32), ("code_dt", ctypes.c_int),
+                ("M_xyz", ctypes.c_void_p), ("xyz_out", ctypes.c_void_p), ("latent_out", ctypes.c_void_p)]
+
+
 _vp = ctypes.c_void_p
 _i32 = ctypes.c_int
 _i64 = ctypes.c_int64
@@ -67,6 +74,9 @@ _SIGS = {
     "hsc_sync": ([_vp, _vp], _i32),
     "hsc_reserve": ([_vp, ctypes.c_size_t], _i32),
     "hsc_shade_latent_scratch_bytes": ([_i64, _i32, _i32, _i32], ctypes.c_size_t),
+    "hsc_set_autotune": ([_vp, _i32], _i32),
+    "hsc_tune_report": ([_vp], ctypes.c_char_p),
+    "hsc_force_launch_config": ([_vp, _i32, _i32, _i32, _i32], _i32),
     "hsc_cmf_weights": ([_vp, _i32, _f32, _f32, _vp, _vp], _i32),
     "hsc_fold_xyz": ([_vp, _vp, _vp, _i32, _i32, _vp, _vp], _i32),
     "hsc_encode": ([_vp, _vp, _i32, _i32, _vp, _i32, _vp, _i32, _vp], _i32),
@@ -80,6 +90,9 @@ _SIGS = {
     "hsc_decode_spectra": ([_vp, _vp, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _vp], _i32),
     "hsc_shade_spectral": ([_vp, _GB, _GB, _i64, _vp, _i32, _LI, _vp, _i32, _vp, _vp, _vp, _vp], _i32),
     "hsc_delta_e": ([_vp, _vp, _vp, _i64, _vp, _i32, _vp, _vp, _vp], _i32),
+    "hsc_batch_create": ([_vp, ctypes.POINTER(_Frame), _i32, ctypes.POINTER(_vp)], _i32),
+    "hsc_batch_shade": ([_vp, _vp, _vp], _i32),
+    "hsc_batch_destroy": ([_vp], None),
 }
 
 for _name, (_args, _res) in _SIGS.items():
@@ -191,6 +204,18 @@ def hsc_sync(ctx: Context, stream=None):
 
 def hsc_reserve(ctx: Context, nbytes: int):
     _check(_lib.hsc_reserve(ctx.handle, int(nbytes)))
+
+
+def hsc_set_autotune(ctx: Context, enable: bool = True):
+    _check(_lib.hsc_set_autotune(ctx.handle, 1 if enable else 0))
+
+
+def hsc_tune_report(ctx: Context) -> str:
+    return _lib.hsc_tune_report(ctx.handle).decode(errors="replace")
+
+
+def hsc_force_launch_config(ctx: Context, ppt: int = 0, block: int = 128, waves: int = 1, vec: int = 1):
+    _check(_lib.hsc_force_launch_config(ctx.handle, int(ppt), int(block), int(waves), int(vec)))
 
 
 def hsc_shade_latent_scratch_bytes(pixels: int, k: int, mode: int, latent_dt: int) -> int:
@@ -305,3 +330,69 @@ def hsc_delta_e(ctx: Context, xyz_test: torch.Tensor, xyz_ref: torch.Tensor, T: 
         raise ValueError("stats_out must hold 8 float64")
     _check(_lib.hsc_delta_e(ctx.handle, _ptr(xyz_test), _ptr(xyz_ref), int(P), _ptr(T), int(T.shape[1]),
                             _ptr(de_out), _ptr(stats_out), _stream(stream)))
+
+
+# ------------------------------------------------------------------- batches
+
+class BatchFrame:
+    """One frame of a batched launch (see hsc_frame in include/hsc.h).  Keeps
+    references to its tensors so they outlive the batch."""
+
+    def __init__(self, g1: GBuffer, g2: Optional[GBuffer], mat_codes: torch.Tensor, lights: Lights,
+                 light_codes: torch.Tensor, M_xyz: torch.Tensor, xyz_out: torch.Tensor,
+                 latent_out: Optional[torch.Tensor] = None):
+        k = int(mat_codes.shape[1])
+        if light_codes.shape != (lights.count, k) or light_codes.dtype != mat_codes.dtype:
+            raise ValueError("light_codes must be (L,k) with the material codes' dtype")
+        if M_xyz.shape != (3, k) or xyz_out.shape != (g1.pixels, 3):
+            raise ValueError("shapes: M_xyz (3,k), xyz_out (P,3)")
+        if latent_out is not None and latent_out.shape != (g1.pixels, k):
+            raise ValueError("latent_out must be (P,k)")
+        self.keep = (g1, g2, mat_codes, lights, light_codes, M_xyz, xyz_out, latent_out)
+        self.s = _Frame()
+        self.s.g1 = g1._s
+        if g2 is not None:
+            self.s.g2 = g2._s
+        self.s.has_g2 = 1 if g2 is not None else 0
+        self.s.pixels = g1.pixels
+        self.s.mat_codes = _ptr(mat_codes)
+        self.s.n_mat = int(mat_codes.shape[0])
+        self.s.lights = lights._s
+        self.s.light_codes = _ptr(light_codes)
+        self.s.k = k
+        self.s.code_dt = _dt(mat_codes)
+        self.s.M_xyz = _ptr(M_xyz)
+        self.s.xyz_out = _ptr(xyz_out)
+        self.s.latent_out = _ptr(latent_out)
+
+
+class Batch:
+    def __init__(self, ctx: Context, frames: Sequence[BatchFrame]):
+        self.ctx = ctx
+        self.frames = list(frames)
+        arr = (_Frame * len(self.frames))(*[f.s for f in self.frames])
+        self._h = _vp()
+        _check(_lib.hsc_batch_create(ctx.handle, arr, len(self.frames), ctypes.byref(self._h)))
+
+    def close(self):
+        if self._h:
+            _lib.hsc_batch_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hsc_batch_create(ctx: Context, frames: Sequence[BatchFrame]) -> Batch:
+    return Batch(ctx, frames)
+
+
+def hsc_batch_shade(ctx: Context, batch: Batch, stream=None):
+    _check(_lib.hsc_batch_shade(ctx.handle, batch._h, _stream(stream)))
+
+
+def hsc_batch_destroy(batch: Batch):
+    batch.close()

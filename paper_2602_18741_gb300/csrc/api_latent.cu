@@ -2,6 +2,7 @@
 // whole-frame call in PASSES or FUSED mode (Fig. 2b of the paper).
 #include "common.cuh"
 #include "shade_latent.cuh"
+#include "tune.cuh"
 
 namespace hsc {
 
@@ -63,6 +64,15 @@ static ShadeArgs base_args(hsc_ctx* ctx, const hsc_gbuffer* g1, const hsc_gbuffe
   return a;
 }
 
+// One shading launch of `kc` channels in the tuned (or default) configuration.
+static hsc_status shade_launch(hsc_ctx* ctx, const ShadeArgs& a, int kc, bool sec, cudaStream_t s) {
+  const TuneKey key = make_tune_key(kTuneLatent, kc, sec, a.L, a.P, a.code_dt);
+  auto launch = [&](const LaunchCfg& c) { return launch_shade_codes(a, kc, sec, c, s); };
+  LaunchCfg cfg;
+  HSC_TRY(tuned_cfg(ctx, key, latent_candidates(ctx), launch, s, &cfg));
+  return launch(cfg);
+}
+
 }  // namespace hsc
 
 using hsc::ShadeArgs;
@@ -93,7 +103,7 @@ hsc_status hsc_shade_pass(hsc_ctx* ctx, const hsc_gbuffer* g1, const hsc_gbuffer
   a.out = rgb_out;
   a.out_stride = 3;
   a.out_c0 = 0;
-  return hsc::launch_shade_codes(a, 3, g2 != nullptr, hsc::default_cfg(ctx), hsc::as_stream(stream));
+  return hsc::shade_launch(ctx, a, 3, g2 != nullptr, hsc::as_stream(stream));
 }
 
 hsc_status hsc_reassemble(hsc_ctx* ctx, const float* const* passes, int B, int64_t pixels, float* latent_out,
@@ -136,7 +146,6 @@ hsc_status hsc_shade_latent(hsc_ctx* ctx, const hsc_gbuffer* g1, const hsc_gbuff
   float* lat32 = (latent_dt == HSC_F32) ? reinterpret_cast<float*>(latent_out) : reinterpret_cast<float*>(scratch);
   if (latent_dt != HSC_F32) scratch += img;
   unsigned int* chan_max = reinterpret_cast<unsigned int*>(ctx->d_small + HSC_OFF_CHANMAX);
-  const hsc::LaunchCfg cfg = hsc::default_cfg(ctx);
   ShadeArgs a = hsc::base_args(ctx, g1, g2, pixels, mat_codes, n_mat, lights, light_codes, k, code_dt);
 
   if (mode == HSC_PASSES) {
@@ -149,7 +158,7 @@ hsc_status hsc_shade_latent(hsc_ctx* ctx, const hsc_gbuffer* g1, const hsc_gbuff
       pa.out = img_b;
       pa.out_stride = 3;
       pa.out_c0 = 0;
-      HSC_TRY(hsc::launch_shade_codes(pa, 3, sec, cfg, s));
+      HSC_TRY(hsc::shade_launch(ctx, pa, 3, sec, s));
     }
     HSC_TRY(hsc::launch_reassemble(passes, B, pixels, lat32, ctx->sm_count, s));
     if (latent_dt == HSC_FP8_E4M3) {
@@ -168,7 +177,7 @@ hsc_status hsc_shade_latent(hsc_ctx* ctx, const hsc_gbuffer* g1, const hsc_gbuff
       fa.xyz = (k <= 15) ? xyz_out : nullptr;
       fa.M = M_xyz;
       fa.chan_max = (latent_dt == HSC_FP8_E4M3) ? chan_max : nullptr;
-      HSC_TRY(hsc::launch_shade_codes(fa, kc, sec, cfg, s));
+      HSC_TRY(hsc::shade_launch(ctx, fa, kc, sec, s));
     }
   }
   if (latent_dt == HSC_FP8_E4M3)

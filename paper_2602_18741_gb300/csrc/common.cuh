@@ -8,7 +8,9 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <map>
 #include <string>
+#include <tuple>
 
 #include "../../include/hsc.h"
 
@@ -20,6 +22,24 @@
 #define HSC_OFF_CHANMAX 0u          // HSC_MAX_K uint32 (fp8 per-channel max)
 #define HSC_OFF_REDUCE 4096u        // reduction workspace for hsc_delta_e
 
+namespace hsc {
+// Shape class of a tuned kernel launch (see tune.cuh).
+struct TuneKey {
+  int kind = 0, channels = 0, sec = 0, lbucket = 0, pbucket = 0, dtype = 0;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(kind, channels, sec, lbucket, pbucket, dtype) <
+           std::tie(o.kind, o.channels, o.sec, o.lbucket, o.pbucket, o.dtype);
+  }
+};
+struct LaunchCfg {
+  int sm_count = 0;
+  int ppt = 2;      // pixels (or shading points) per thread
+  int block = 128;  // threads per CTA
+  int waves = 1;    // persistent grid of waves x resident CTAs x SMs; 0 = one CTA per pixel tile
+  int vec = 1;      // 1: scalar FP32; 2: shading points in f32x2 pairs
+};
+}  // namespace hsc
+
 struct hsc_ctx {
   int device = 0;
   int sm_count = 0;
@@ -28,6 +48,10 @@ struct hsc_ctx {
   unsigned char* d_small = nullptr;
   unsigned char* d_big = nullptr;  // growable scratch (PASSES images, fp32 latent)
   size_t big_bytes = 0;
+  int autotune = 0;                               // hsc_set_autotune
+  std::map<hsc::TuneKey, hsc::LaunchCfg> tuned;   // chosen launch configurations
+  std::string tune_report;                        // candidate timings, one line per shape class
+  hsc::LaunchCfg forced{0, 0, 128, 1, 1};         // hsc_force_launch_config (ppt 0 = not forced)
 };
 
 // Device error flags.
@@ -119,6 +143,51 @@ __device__ __forceinline__ float geometry_term(float x, float y, float z, float 
   c = fmaxf(c, 0.0f);
   const float ri = rsqrt_mufu(r2);
   return __fmul_rn(__fmul_rn(c, ri), __fmul_rn(ri, ri));
+}
+
+// Packed FP32 pairs (sm_100+ f32x2 arithmetic): each half is rounded exactly
+// like the scalar instruction, so a pair op equals two scalar ops bit for bit
+// while taking one issue slot.
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(f2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+  f2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// geometry_term for two shading points at once: the same operations in the
+// same order per half, so each half equals geometry_term bit for bit.
+__device__ __forceinline__ f2 geometry_term_x2(f2 x, f2 y, f2 z, f2 nx, f2 ny, f2 nz, f2 px, f2 py, f2 pz) {
+  const f2 dx = f2_sub(px, x);
+  const f2 dy = f2_sub(py, y);
+  const f2 dz = f2_sub(pz, z);
+  const f2 r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
+  const f2 c = f2_fma(nz, dz, f2_fma(ny, dy, f2_mul(nx, dx)));
+  float c0, c1, r0, r1;
+  f2_unpack(c, c0, c1);
+  f2_unpack(r2, r0, r1);
+  const f2 cm = f2_pack(fmaxf(c0, 0.0f), fmaxf(c1, 0.0f));
+  const f2 ri = f2_pack(rsqrt_mufu(r0), rsqrt_mufu(r1));
+  return f2_mul(f2_mul(cm, ri), f2_mul(ri, ri));
 }
 
 // Virtual-point-light transfer from the secondary point to the primary,

@@ -14,22 +14,38 @@ constexpr int kDBlock = 256;
 // IEC 61966-2-1 XYZ -> linear sRGB.
 __constant__ float c_srgb[9] = {3.2406f, -1.5372f, -0.4986f, -0.9689f, 1.8758f, 0.0415f, 0.0557f, -0.2040f, 1.0570f};
 
+// sRGB transfer function.  The 8-bit output quantises it, so the power uses
+// the fast exp2/log2 hardware intrinsics.
 __device__ __forceinline__ float srgb_encode(float v) {
   v = fminf(fmaxf(v, 0.0f), 1.0f);
-  return (v <= 0.0031308f) ? 12.92f * v : 1.055f * powf(v, 1.0f / 2.4f) - 0.055f;
+  return (v <= 0.0031308f) ? 12.92f * v : 1.055f * __powf(v, 1.0f / 2.4f) - 0.055f;
 }
 
-__global__ void __launch_bounds__(kDBlock) decode_xyz_kernel(const void* __restrict__ latent, int dt,
+template <int DT>
+__device__ __forceinline__ float load_lat(const void* base, int64_t i, const float* s_scale, int c) {
+  if (DT == HSC_F32) return __ldg(reinterpret_cast<const float*>(base) + i);
+  if (DT == HSC_BF16)
+    return __uint_as_float(((unsigned int)__ldg(reinterpret_cast<const unsigned short*>(base) + i)) << 16);
+  if (DT == HSC_F16) return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(base) + i)));
+  return __fmul_rn(fp8_e4m3_to_float(__ldg(reinterpret_cast<const unsigned char*>(base) + i)), s_scale[c]);
+}
+
+// One thread per pixel: XYZ = M z with the sums over c in order, then sRGB.
+template <int DT>
+__global__ void __launch_bounds__(kDBlock) decode_xyz_kernel(const void* __restrict__ latent,
                                                              const float* __restrict__ scales, int64_t P, int k,
                                                              const float* __restrict__ M, float* __restrict__ xyz,
                                                              uint8_t* __restrict__ srgb8) {
   __shared__ float s_M[3 * HSC_MAX_K];
+  __shared__ float s_scale[HSC_MAX_K];
   for (int i = threadIdx.x; i < 3 * k; i += blockDim.x) s_M[i] = M[i];
+  if (DT == HSC_FP8_E4M3)
+    for (int i = threadIdx.x; i < k; i += blockDim.x) s_scale[i] = scales[i];
   __syncthreads();
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
     float X = 0.0f, Y = 0.0f, Z = 0.0f;
     for (int c = 0; c < k; ++c) {
-      const float z = load_latent(latent, dt, p * k + c, scales, c);
+      const float z = load_lat<DT>(latent, p * k + c, s_scale, c);
       X = __fmaf_rn(s_M[c], z, X);
       Y = __fmaf_rn(s_M[k + c], z, Y);
       Z = __fmaf_rn(s_M[2 * k + c], z, Z);
@@ -49,44 +65,65 @@ __global__ void __launch_bounds__(kDBlock) decode_xyz_kernel(const void* __restr
   }
 }
 
-// Spectral decode on CUDA cores (FP32 latent).  A CTA owns a tile of TP
-// pixels: z (TP x k) and D (n x k) sit in shared memory and the TP*n outputs of
-// the tile are written in flat order, so consecutive threads store
-// consecutive addresses.
-constexpr int kTP = 64;
+// Spectral decode on CUDA cores (FP32 latent).  Thread (i, r) of an n x R
+// CTA owns wavelength i -- its row of D stays in registers for the whole
+// kernel -- and pixel rows r, r + R, ... of each tile.  A tile's latent rows
+// are staged in shared memory (row stride padded to a multiple of 4 floats)
+// and read as broadcast float4s; the 32 lanes of a warp then store 32
+// consecutive floats of one output row, so every store is a full 128-byte
+// line.  Sums over c run in order.
+constexpr int kTP = 64;        // pixels per tile
+constexpr int kDecThreads = 256;
 
-__global__ void __launch_bounds__(kDBlock) decode_spectra_f32_kernel(const float* __restrict__ z, int64_t P, int k,
-                                                                     const float* __restrict__ D, int n,
-                                                                     float* __restrict__ out) {
-  extern __shared__ float s_mem[];
-  float* s_D = s_mem;             // n x k
-  float* s_z = s_mem + n * k;     // kTP x k
-  for (int i = threadIdx.x; i < n * k; i += blockDim.x) s_D[i] = __ldg(D + i);
+template <int KP>  // k rounded up to a multiple of 4 (<= 16)
+__global__ void __launch_bounds__(kDecThreads) decode_spectra_f32_kernel(const float* __restrict__ z, int64_t P,
+                                                                         int k, const float* __restrict__ D, int n,
+                                                                         int R, float* __restrict__ out) {
+  __shared__ __align__(16) float s_z[kTP * KP];
+  const int t = threadIdx.x;
+  const int i = t % n, r = t / n;
+  const bool active = r < R;
+  float d[KP];
+#pragma unroll
+  for (int c = 0; c < KP; ++c) d[c] = (active && c < k) ? __ldg(D + i * k + c) : 0.0f;
   const int64_t tiles = (P + kTP - 1) / kTP;
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t p0 = tile * kTP;
     const int tp = (int)min((int64_t)kTP, P - p0);
     __syncthreads();
-    for (int i = threadIdx.x; i < tp * k; i += blockDim.x) s_z[i] = __ldg(z + p0 * k + i);
-    __syncthreads();
-    const int total = tp * n;
-    int f = threadIdx.x;
-    int pl = f / n, i = f - pl * n;
-    const int dp = kDBlock / n, di = kDBlock - dp * n;
-    float* o = out + p0 * n;
-    for (; f < total; f += kDBlock) {
-      const float* zz = s_z + pl * k;
-      const float* dd = s_D + i * k;
-      float s = 0.0f;
-      for (int c = 0; c < k; ++c) s = __fmaf_rn(dd[c], zz[c], s);
-      o[f] = s;
-      pl += dp;
-      i += di;
-      if (i >= n) {
-        i -= n;
-        ++pl;
-      }
+    for (int e = t; e < kTP * KP; e += blockDim.x) {
+      const int pl = e / KP, c = e - pl * KP;
+      s_z[e] = (pl < tp && c < k) ? __ldg(z + (p0 + pl) * k + c) : 0.0f;
     }
+    __syncthreads();
+    if (!active) continue;
+    for (int pl = r; pl < tp; pl += R) {
+      const float4* zr = reinterpret_cast<const float4*>(s_z + pl * KP);
+      float s = 0.0f;
+#pragma unroll
+      for (int q = 0; q < KP / 4; ++q) {
+        const float4 v = zr[q];
+        s = __fmaf_rn(d[4 * q + 0], v.x, s);
+        s = __fmaf_rn(d[4 * q + 1], v.y, s);
+        s = __fmaf_rn(d[4 * q + 2], v.z, s);
+        s = __fmaf_rn(d[4 * q + 3], v.w, s);
+      }
+      out[(p0 + pl) * n + i] = s;
+    }
+  }
+}
+
+// Generic FP32 decode for k > 16: one thread per output, sums over c in order.
+__global__ void __launch_bounds__(256) decode_spectra_f32_generic(const float* __restrict__ z, int64_t P, int k,
+                                                                  const float* __restrict__ D, int n,
+                                                                  float* __restrict__ out) {
+  const int64_t total = P * n;
+  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total; f += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = f / n;
+    const int i = (int)(f - p * n);
+    float s = 0.0f;
+    for (int c = 0; c < k; ++c) s = __fmaf_rn(__ldg(D + i * k + c), __ldg(z + p * k + c), s);
+    out[f] = s;
   }
 }
 
@@ -102,21 +139,33 @@ int64_t stream_grid(int64_t work, int block, int sm_count, int per_sm) {
 hsc_status launch_decode_xyz(const void* latent, int dt, const float* scales, int64_t P, int k, const float* M,
                              float* xyz, uint8_t* srgb8, int sm_count, cudaStream_t s) {
   const int64_t grid = stream_grid(P, kDBlock, sm_count, 8);
-  decode_xyz_kernel<<<(unsigned)grid, kDBlock, 0, s>>>(latent, dt, scales, P, k, M, xyz, srgb8);
+  switch (dt) {
+    case HSC_F32: decode_xyz_kernel<HSC_F32><<<(unsigned)grid, kDBlock, 0, s>>>(latent, scales, P, k, M, xyz, srgb8); break;
+    case HSC_BF16: decode_xyz_kernel<HSC_BF16><<<(unsigned)grid, kDBlock, 0, s>>>(latent, scales, P, k, M, xyz, srgb8); break;
+    case HSC_F16: decode_xyz_kernel<HSC_F16><<<(unsigned)grid, kDBlock, 0, s>>>(latent, scales, P, k, M, xyz, srgb8); break;
+    default: decode_xyz_kernel<HSC_FP8_E4M3><<<(unsigned)grid, kDBlock, 0, s>>>(latent, scales, P, k, M, xyz, srgb8); break;
+  }
   return check_launch("decode_xyz_kernel");
 }
 
 hsc_status launch_decode_spectra_f32(const float* z, int64_t P, int k, const float* D, int n, float* out,
                                      int sm_count, cudaStream_t s) {
+  if (k > 16) {
+    const int64_t grid = stream_grid(P * n, 256, sm_count, 8);
+    decode_spectra_f32_generic<<<(unsigned)grid, 256, 0, s>>>(z, P, k, D, n, out);
+    return check_launch("decode_spectra_f32_generic");
+  }
+  const int R = kDecThreads / n > 0 ? kDecThreads / n : 1;   // pixel rows per CTA (n <= 128)
   const int64_t tiles = (P + kTP - 1) / kTP;
   int64_t grid = tiles < (int64_t)sm_count * 8 ? tiles : (int64_t)sm_count * 8;
   if (grid < 1) grid = 1;
-  const size_t smem = (size_t)(n * k + kTP * k) * sizeof(float);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(decode_spectra_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return set_error(HSC_ERR_CUDA, "smem attribute: %s", cudaGetErrorString(e));
+  const int kp = (k + 3) / 4 * 4;
+  switch (kp) {
+    case 4: decode_spectra_f32_kernel<4><<<(unsigned)grid, kDecThreads, 0, s>>>(z, P, k, D, n, R, out); break;
+    case 8: decode_spectra_f32_kernel<8><<<(unsigned)grid, kDecThreads, 0, s>>>(z, P, k, D, n, R, out); break;
+    case 12: decode_spectra_f32_kernel<12><<<(unsigned)grid, kDecThreads, 0, s>>>(z, P, k, D, n, R, out); break;
+    default: decode_spectra_f32_kernel<16><<<(unsigned)grid, kDecThreads, 0, s>>>(z, P, k, D, n, R, out); break;
   }
-  decode_spectra_f32_kernel<<<(unsigned)grid, kDBlock, smem, s>>>(z, P, k, D, n, out);
   return check_launch("decode_spectra_f32_kernel");
 }
 

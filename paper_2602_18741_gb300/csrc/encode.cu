@@ -1,25 +1,34 @@
 // Asset encoding z = W_enc s (Eq. 4), done once per scene for every material
 // reflectance and light SPD (Fig. 2b).  m*k outputs of n FMAs each: a few
-// hundred thousand flops per scene, so one thread per code value is enough.
+// hundred thousand flops per scene; latency bound, so each output gets a
+// whole warp.
 #include "common.cuh"
 
 namespace {
 
-__global__ void encode_kernel(const float* __restrict__ E, int k, int n, const float* __restrict__ S, int m,
-                              void* __restrict__ out, int out_dt) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)m * k) return;
-  const int j = (int)(idx / k), c = (int)(idx % k);
+// One warp per code value: lane i sums E[c][i'] s[j][i'] over i' = i, i+32,
+// ..., then a butterfly reduction adds the 32 partial sums.
+__global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ E, int k, int n,
+                                                     const float* __restrict__ S, int m, void* __restrict__ out,
+                                                     int out_dt) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (int64_t)m * k) return;  // whole warps exit together
+  const int j = (int)(w / k), c = (int)(w % k);
   const float* e = E + (int64_t)c * n;
   const float* s = S + (int64_t)j * n;
   float acc = 0.0f;
-  for (int i = 0; i < n; ++i) acc = __fmaf_rn(__ldg(e + i), __ldg(s + i), acc);
-  if (out_dt == HSC_F32)
-    reinterpret_cast<float*>(out)[idx] = acc;
-  else if (out_dt == HSC_BF16)
-    reinterpret_cast<unsigned short*>(out)[idx] = hsc::float_to_bf16_bits(acc);
-  else
-    reinterpret_cast<unsigned short*>(out)[idx] = hsc::float_to_f16_bits(acc);
+  for (int i = lane; i < n; i += 32) acc = __fmaf_rn(__ldg(e + i), __ldg(s + i), acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+  if (lane == 0) {
+    if (out_dt == HSC_F32)
+      reinterpret_cast<float*>(out)[w] = acc;
+    else if (out_dt == HSC_BF16)
+      reinterpret_cast<unsigned short*>(out)[w] = hsc::float_to_bf16_bits(acc);
+    else
+      reinterpret_cast<unsigned short*>(out)[w] = hsc::float_to_f16_bits(acc);
+  }
 }
 
 }  // namespace
@@ -37,8 +46,8 @@ extern "C" hsc_status hsc_encode(hsc_ctx* ctx, const float* E, int k, int n, con
   HSC_REQUIRE(hsc::aligned(E, 4) && hsc::aligned(spectra, 4) && hsc::aligned(codes_out, out_dt == HSC_F32 ? 4 : 2),
               "misaligned pointer");
   HSC_GUARD(ctx);
-  const int64_t total = (int64_t)m * k;
-  encode_kernel<<<hsc::ceil_div_i(total, 256), 256, 0, hsc::as_stream(stream)>>>(E, k, n, spectra, m, codes_out,
-                                                                                  (int)out_dt);
+  const int64_t warps = (int64_t)m * k;
+  encode_kernel<<<hsc::ceil_div_i(warps * 32, 256), 256, 0, hsc::as_stream(stream)>>>(E, k, n, spectra, m, codes_out,
+                                                                                       (int)out_dt);
   return hsc::check_launch("encode_kernel");
 }

@@ -163,28 +163,46 @@ __global__ void __launch_bounds__(kMBlock) de_kernel(const float* __restrict__ t
   }
 }
 
-// One CTA: fold the per-CTA partials in a fixed order (deterministic) and set
-// up the radix select for rank ceil(0.95 P) - 1.
-__global__ void fold_kernel(Scratch* sc, int nblocks, int64_t P, double* stats) {
-  if (threadIdx.x != 0) return;
-  double t[4] = {0, 0, 0, 0};
-  for (int i = 0; i < nblocks; ++i) {
-    t[0] += sc->partial[4 * i];
-    t[1] += sc->partial[4 * i + 1];
-    t[2] += sc->partial[4 * i + 2];
-    t[3] = fmax(t[3], sc->partial[4 * i + 3]);
+// One CTA of 256 threads: fold the per-CTA partials (thread t takes partials
+// t, t+256, ..., then a fixed-shape tree), so the result is deterministic, and
+// set up the radix select for rank ceil(0.95 P) - 1.
+__global__ void __launch_bounds__(256) fold_kernel(Scratch* sc, int nblocks, int64_t P, double* stats) {
+  __shared__ double s_r[4][256];
+  const int t = threadIdx.x;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  for (int i = t; i < nblocks; i += 256) {
+    a0 += sc->partial[4 * i];
+    a1 += sc->partial[4 * i + 1];
+    a2 += sc->partial[4 * i + 2];
+    a3 = fmax(a3, sc->partial[4 * i + 3]);
   }
-  const double inv = P > 0 ? 1.0 / (double)P : 0.0;
-  stats[0] = t[0] * inv;
-  stats[2] = t[1] * inv;
-  stats[3] = t[2] * inv;
-  stats[4] = (double)__uint_as_float(sc->ymax_bits);
-  stats[5] = t[3];
-  stats[6] = (double)P;
-  stats[7] = 0.0;
-  long long r = (long long)ceil(0.95 * (double)P) - 1;
-  sc->rank = (unsigned long long)(r < 0 ? 0 : r);
-  sc->prefix = 0u;
+  s_r[0][t] = a0;
+  s_r[1][t] = a1;
+  s_r[2][t] = a2;
+  s_r[3][t] = a3;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (t < w) {
+      s_r[0][t] += s_r[0][t + w];
+      s_r[1][t] += s_r[1][t + w];
+      s_r[2][t] += s_r[2][t + w];
+      s_r[3][t] = fmax(s_r[3][t], s_r[3][t + w]);
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    const double inv = P > 0 ? 1.0 / (double)P : 0.0;
+    stats[0] = s_r[0][0] * inv;
+    stats[2] = s_r[1][0] * inv;
+    stats[3] = s_r[2][0] * inv;
+    stats[4] = (double)__uint_as_float(sc->ymax_bits);
+    stats[5] = s_r[3][0];
+    stats[6] = (double)P;
+    stats[7] = 0.0;
+    long long r = (long long)ceil(0.95 * (double)P) - 1;
+    sc->rank = (unsigned long long)(r < 0 ? 0 : r);
+    sc->prefix = 0u;
+  }
 }
 
 // Histogram of the digit (bits [shift, shift+width)) of every value whose
@@ -207,26 +225,55 @@ __global__ void __launch_bounds__(kMBlock) radix_hist_kernel(const float* __rest
     if (s_h[i]) atomicAdd(&sc->hist[i], s_h[i]);
 }
 
-// One thread: walk the histogram to the bin holding the rank, extend the
-// prefix, reduce the rank, clear the histogram for the next pass.
-__global__ void radix_select_kernel(Scratch* sc, int shift, int width, double* stats) {
-  if (threadIdx.x != 0) return;
+// One CTA of 1024 threads: exclusive prefix sum over the (up to 2048) bins,
+// the bin whose range holds the rank extends the prefix and reduces the rank;
+// the histogram is cleared for the next pass.
+__global__ void __launch_bounds__(1024) radix_select_kernel(Scratch* sc, int shift, int width, double* stats) {
+  __shared__ unsigned long long s_warp[32];
+  __shared__ int s_sel;
+  __shared__ unsigned long long s_before;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int bins = 1 << width;
-  unsigned long long r = sc->rank;
-  unsigned long long run = 0;
-  int sel = bins - 1;
-  for (int i = 0; i < bins; ++i) {
-    const unsigned long long c = sc->hist[i];
-    if (run + c > r) {
-      sel = i;
-      break;
-    }
-    run += c;
+  const unsigned long long r = sc->rank;
+  // thread t owns bins 2t and 2t+1
+  const unsigned long long c0 = (2 * t < bins) ? sc->hist[2 * t] : 0ull;
+  const unsigned long long c1 = (2 * t + 1 < bins) ? sc->hist[2 * t + 1] : 0ull;
+  unsigned long long incl = c0 + c1;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
   }
-  for (int i = 0; i < bins; ++i) sc->hist[i] = 0u;
-  sc->rank = r - run;
-  sc->prefix |= ((unsigned int)sel) << shift;
-  if (shift == 0) stats[1] = (double)__uint_as_float(sc->prefix);
+  if (lane == 31) s_warp[wid] = incl;
+  if (t == 0) {
+    s_sel = bins - 1;
+    s_before = 0ull;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    unsigned long long w = s_warp[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long v = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += v;
+    }
+    s_warp[lane] = w;  // inclusive warp totals
+  }
+  __syncthreads();
+  const unsigned long long before = incl - (c0 + c1) + (wid > 0 ? s_warp[wid - 1] : 0ull);
+  if (before <= r && r < before + c0) {
+    s_sel = 2 * t;
+    s_before = before;
+  } else if (before + c0 <= r && r < before + c0 + c1) {
+    s_sel = 2 * t + 1;
+    s_before = before + c0;
+  }
+  __syncthreads();
+  if (2 * t < bins) sc->hist[2 * t] = 0u;
+  if (2 * t + 1 < bins) sc->hist[2 * t + 1] = 0u;
+  if (t == 0) {
+    sc->rank = r - s_before;
+    sc->prefix |= ((unsigned int)s_sel) << shift;
+    if (shift == 0) stats[1] = (double)__uint_as_float(sc->prefix);
+  }
 }
 
 }  // namespace
@@ -260,14 +307,14 @@ extern "C" hsc_status hsc_delta_e(hsc_ctx* ctx, const float* xyz_test, const flo
   HSC_TRY(hsc::check_launch("ymax_kernel"));
   hsc::de_kernel<<<grid, hsc::kMBlock, 0, s>>>(xyz_test, xyz_ref, pixels, sc, de);
   HSC_TRY(hsc::check_launch("de_kernel"));
-  hsc::fold_kernel<<<1, 32, 0, s>>>(sc, grid, pixels, stats_out);
+  hsc::fold_kernel<<<1, 256, 0, s>>>(sc, grid, pixels, stats_out);
   HSC_TRY(hsc::check_launch("fold_kernel"));
   const int shifts[3] = {21, 10, 0};
   const int widths[3] = {11, 11, 10};
   for (int i = 0; i < 3; ++i) {
     hsc::radix_hist_kernel<<<grid, hsc::kMBlock, 0, s>>>(de, pixels, sc, shifts[i], widths[i]);
     HSC_TRY(hsc::check_launch("radix_hist_kernel"));
-    hsc::radix_select_kernel<<<1, 32, 0, s>>>(sc, shifts[i], widths[i], stats_out);
+    hsc::radix_select_kernel<<<1, 1024, 0, s>>>(sc, shifts[i], widths[i], stats_out);
     HSC_TRY(hsc::check_launch("radix_select_kernel"));
   }
   return HSC_OK;

@@ -6,7 +6,6 @@
 namespace hsc {
 
 constexpr int kLightTile = 256;   // lights staged per shared-memory tile
-constexpr int kShadeBlock = 128;  // threads per CTA
 
 struct ShadeArgs {
   const float* n1;
@@ -35,13 +34,16 @@ struct ShadeArgs {
   int64_t tiles;
 };
 
-struct LaunchCfg {
-  int sm_count = 0;
-  int ppt = 2;    // pixels per thread: 1, 2 or 4
-  int waves = 1;  // resident-CTA multiples of the SM count in the persistent grid
-};
-
 LaunchCfg default_cfg(const hsc_ctx* ctx);
+
+// Defined in shade_latent_kernel.cuh, instantiated per KC in shade_latent_k*.cu.
+template <int KC>
+hsc_status launch_kc(const ShadeArgs& a, bool sec, const LaunchCfg& cfg, cudaStream_t s);
+extern template hsc_status launch_kc<3>(const ShadeArgs&, bool, const LaunchCfg&, cudaStream_t);
+extern template hsc_status launch_kc<6>(const ShadeArgs&, bool, const LaunchCfg&, cudaStream_t);
+extern template hsc_status launch_kc<9>(const ShadeArgs&, bool, const LaunchCfg&, cudaStream_t);
+extern template hsc_status launch_kc<12>(const ShadeArgs&, bool, const LaunchCfg&, cudaStream_t);
+extern template hsc_status launch_kc<15>(const ShadeArgs&, bool, const LaunchCfg&, cudaStream_t);
 hsc_status launch_shade_codes(const ShadeArgs& a, int kc, bool sec, const LaunchCfg& cfg, cudaStream_t s);
 hsc_status launch_reassemble(const float* const* passes, int B, int64_t P, float* out, int sm_count, cudaStream_t s);
 

@@ -1,0 +1,303 @@
+// Latent (k-code) deferred shading: the k/3 RGB passes of Fig. 2b, their
+// reassembly, and the fused single-launch k-channel form.
+//
+// Per pixel and per light the work is one geometry term g (13 FP32 ops + one
+// MUFU rsqrt) and KC FMAs acc[c] += g * v_l[c], where v_l = (I_l / pi) * E(spd_l)
+// is the light's scaled code.  After the light loop the blockwise Hadamard
+// product with the material codes (Eq. 5, element-wise on R^k) and the
+// indirect bounce give
+//     z[c] = zR1[c] * (A1[c] + h * (zR2[c] * A2[c])).
+// A pass (KC = 3) and the fused launch (KC = k) run the same template: each
+// channel sees the same operations in the same order (same light order, same
+// geometry_term instruction sequence, no reductions across channels), so the
+// fused latent image is bit-identical to the reassembled passes.
+//
+// GB300 mapping: FP32 issue bound (~20 lane-ops per pixel-light for k = 6 vs
+// 56 bytes of G-buffer per pixel amortised over 2L evaluations).  Lights and
+// their pre-scaled codes are staged once per CTA in shared memory and read as
+// broadcast float4s; each thread owns PPT pixels (x2 shading points with the
+// secondary G-buffer) so one light load feeds 2*PPT geometry evaluations; the
+// grid is either persistent (a multiple of the SM count striding over pixel
+// tiles) or one CTA per tile.  The thread mapping never changes what a
+// channel computes, so every configuration gives bit-identical results; the
+// autotuner picks among them by timing.  VEC = 2 processes the shading
+// points in pairs with the packed f32x2 instructions of sm_100+: half the
+// FP32 issue slots for the same FP32 work.
+#pragma once
+
+#include "common.cuh"
+#include "shade_latent.cuh"
+
+namespace hsc {
+
+namespace {
+
+// Float4s per staged light.  VEC = 1: px py pz v0 .. v{KC-1} (padded);
+// VEC = 2: every value duplicated (px px py py pz pz v0 v0 ...) so that a
+// float4 load yields two ready-made f32x2 broadcast operands.
+template <int KC, int VEC>
+struct LightStage {
+  static constexpr int F4 = VEC == 1 ? (3 + KC + 3) / 4 : (3 + KC + 1) / 2;
+};
+
+// Stages lights l0 .. l0+nl-1 of one launch: positions and the code channels
+// c0 .. c0+KC-1 pre-multiplied by I/pi, laid out as LightStage describes.
+template <int KC, int VEC, int BLOCK>
+__device__ __forceinline__ void stage_light_codes(const ShadeArgs& a, float4* s_light, int l0, int nl) {
+  constexpr int F4 = LightStage<KC, VEC>::F4;
+  float* s = reinterpret_cast<float*>(s_light);
+  constexpr int per = F4 * 4;
+  for (int idx = threadIdx.x; idx < nl * per; idx += BLOCK) {
+    const int l = idx / per, j0 = idx - l * per;
+    const int j = VEC == 1 ? j0 : (j0 >> 1);
+    const int lg = l0 + l;
+    float v = 0.0f;
+    if (j < 3) {
+      v = __ldg(a.lpos + 3 * lg + j);
+    } else if (j < 3 + KC) {
+      const float sc = __fmul_rn(__ldg(a.linten + lg), kInvPi);
+      v = __fmul_rn(load_code(a.light_codes, a.code_dt, (int64_t)lg * a.k + a.c0 + (j - 3)), sc);
+    }
+    s[idx] = v;
+  }
+}
+
+// Shades one tile of BLOCK * PPT pixels: loads the shading points, sums every
+// light into KC accumulators per point, applies the blockwise product with the
+// material codes and the bounce, writes the latent channels (and XYZ, and
+// the fp8 channel maxima when asked).  When the lights fit one shared-memory
+// tile the caller has staged them already (`staged`); otherwise the light
+// tiles are staged here.  Must be called by every thread of the CTA.
+template <int KC, int PPT, bool SEC, int BLOCK, int VEC>
+__device__ __forceinline__ void shade_tile(const ShadeArgs& a, int64_t tile, float4* s_light, bool staged) {
+  constexpr int F4 = LightStage<KC, VEC>::F4;
+  constexpr int NPT = PPT * (SEC ? 2 : 1);
+  static_assert(VEC == 1 || NPT % 2 == 0, "paired points need an even point count");
+  const int tid = threadIdx.x;
+  const bool multi_tile = !staged;
+  auto stage = [&](int l0, int nl) { stage_light_codes<KC, VEC, BLOCK>(a, s_light, l0, nl); };
+  {
+    float px[NPT], py[NPT], pz[NPT], nx[NPT], ny[NPT], nz[NPT];
+    int64_t pix[PPT];
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+      const int64_t p = tile * (BLOCK * PPT) + (int64_t)j * BLOCK + tid;
+      pix[j] = p;
+      const int64_t pc = p < a.P ? p : a.P - 1;
+      px[j] = __ldg(a.x1 + 3 * pc + 0);
+      py[j] = __ldg(a.x1 + 3 * pc + 1);
+      pz[j] = __ldg(a.x1 + 3 * pc + 2);
+      nx[j] = __ldg(a.n1 + 3 * pc + 0);
+      ny[j] = __ldg(a.n1 + 3 * pc + 1);
+      nz[j] = __ldg(a.n1 + 3 * pc + 2);
+      if (SEC) {
+        px[PPT + j] = __ldg(a.x2 + 3 * pc + 0);
+        py[PPT + j] = __ldg(a.x2 + 3 * pc + 1);
+        pz[PPT + j] = __ldg(a.x2 + 3 * pc + 2);
+        nx[PPT + j] = __ldg(a.n2 + 3 * pc + 0);
+        ny[PPT + j] = __ldg(a.n2 + 3 * pc + 1);
+        nz[PPT + j] = __ldg(a.n2 + 3 * pc + 2);
+      }
+    }
+    float acc[NPT][KC];
+#pragma unroll
+    for (int q = 0; q < NPT; ++q)
+#pragma unroll
+      for (int c = 0; c < KC; ++c) acc[q][c] = 0.0f;
+
+    if constexpr (VEC == 1) {
+      for (int l0 = 0; l0 < a.L; l0 += kLightTile) {
+        const int nl = min(kLightTile, a.L - l0);
+        if (multi_tile) {
+          __syncthreads();
+          stage(l0, nl);
+          __syncthreads();
+        }
+#pragma unroll 2
+        for (int l = 0; l < nl; ++l) {
+          float v[F4 * 4];
+#pragma unroll
+          for (int f = 0; f < F4; ++f) {
+            const float4 t = s_light[l * F4 + f];
+            v[4 * f + 0] = t.x;
+            v[4 * f + 1] = t.y;
+            v[4 * f + 2] = t.z;
+            v[4 * f + 3] = t.w;
+          }
+#pragma unroll
+          for (int q = 0; q < NPT; ++q) {
+            const float g = geometry_term(px[q], py[q], pz[q], nx[q], ny[q], nz[q], v[0], v[1], v[2]);
+#pragma unroll
+            for (int c = 0; c < KC; ++c) acc[q][c] = __fmaf_rn(g, v[3 + c], acc[q][c]);
+          }
+        }
+      }
+    } else {
+      // Pairs of shading points in f32x2 registers: with the secondary
+      // G-buffer pair j is (primary j, secondary j), otherwise (pixel 2m,
+      // pixel 2m + 1).
+      constexpr int NPR = NPT / 2 > 0 ? NPT / 2 : 1;
+      f2 X[NPR], Y[NPR], Z[NPR], NX[NPR], NY[NPR], NZ[NPR], A[NPR][KC];
+#pragma unroll
+      for (int q = 0; q < NPR; ++q) {
+        const int qa = SEC ? q : 2 * q, qb = SEC ? PPT + q : 2 * q + 1;
+        X[q] = f2_pack(px[qa], px[qb]);
+        Y[q] = f2_pack(py[qa], py[qb]);
+        Z[q] = f2_pack(pz[qa], pz[qb]);
+        NX[q] = f2_pack(nx[qa], nx[qb]);
+        NY[q] = f2_pack(ny[qa], ny[qb]);
+        NZ[q] = f2_pack(nz[qa], nz[qb]);
+#pragma unroll
+        for (int c = 0; c < KC; ++c) A[q][c] = 0ull;  // +0.0f in both halves
+      }
+      for (int l0 = 0; l0 < a.L; l0 += kLightTile) {
+        const int nl = min(kLightTile, a.L - l0);
+        if (multi_tile) {
+          __syncthreads();
+          stage(l0, nl);
+          __syncthreads();
+        }
+        const ulonglong2* sl = reinterpret_cast<const ulonglong2*>(s_light);
+#pragma unroll 2
+        for (int l = 0; l < nl; ++l) {
+          f2 v[F4 * 2];
+#pragma unroll
+          for (int f = 0; f < F4; ++f) {
+            const ulonglong2 t = sl[l * F4 + f];
+            v[2 * f + 0] = t.x;
+            v[2 * f + 1] = t.y;
+          }
+#pragma unroll
+          for (int q = 0; q < NPR; ++q) {
+            const f2 g = geometry_term_x2(X[q], Y[q], Z[q], NX[q], NY[q], NZ[q], v[0], v[1], v[2]);
+#pragma unroll
+            for (int c = 0; c < KC; ++c) A[q][c] = f2_fma(g, v[3 + c], A[q][c]);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NPR; ++q) {
+        const int qa = SEC ? q : 2 * q, qb = SEC ? PPT + q : 2 * q + 1;
+#pragma unroll
+        for (int c = 0; c < KC; ++c) f2_unpack(A[q][c], acc[qa][c], acc[qb][c]);
+      }
+    }
+
+    // Epilogue: blockwise Hadamard product with the material codes + bounce.
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+      const int64_t p = pix[j];
+      const bool valid = p < a.P;
+      const int64_t pc = valid ? p : a.P - 1;
+      int m1 = __ldg(a.m1 + pc);
+      bool bad = (m1 < 0 || m1 >= a.n_mat);
+      float zr1[KC], out[KC];
+#pragma unroll
+      for (int c = 0; c < KC; ++c) zr1[c] = bad ? 0.0f : load_code(a.mat_codes, a.code_dt, (int64_t)m1 * a.k + a.c0 + c);
+      if (SEC) {
+        const int m2 = __ldg(a.m2 + pc);
+        const bool bad2 = (m2 < 0 || m2 >= a.n_mat);
+        bad = bad || bad2;
+        const float h = bounce_term(px[j], py[j], pz[j], nx[j], ny[j], nz[j], px[PPT + j], py[PPT + j],
+                                    pz[PPT + j], nx[PPT + j], ny[PPT + j], nz[PPT + j]);
+#pragma unroll
+        for (int c = 0; c < KC; ++c) {
+          const float zr2 = bad2 ? 0.0f : load_code(a.mat_codes, a.code_dt, (int64_t)m2 * a.k + a.c0 + c);
+          out[c] = __fmul_rn(zr1[c], __fmaf_rn(h, __fmul_rn(zr2, acc[PPT + j][c]), acc[j][c]));
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < KC; ++c) out[c] = __fmul_rn(zr1[c], acc[j][c]);
+      }
+      if (valid && bad) atomicOr(a.err, HSC_DEVERR_MATERIAL);
+      if (valid) {
+        if (a.out) {  // the batched launch may ask for XYZ only
+          float* o = a.out + p * a.out_stride + a.out_c0;
+#pragma unroll
+          for (int c = 0; c < KC; ++c) o[c] = out[c];
+        }
+        if (a.xyz) {
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            float s = 0.0f;
+#pragma unroll
+            for (int c = 0; c < KC; ++c) s = __fmaf_rn(__ldg(a.M + r * a.k + c), out[c], s);
+            a.xyz[3 * p + r] = s;
+          }
+        }
+      }
+      if (a.chan_max) {
+        // non-negative floats order like their bit patterns
+#pragma unroll
+        for (int c = 0; c < KC; ++c) {
+          const unsigned int bits = valid ? __float_as_uint(fmaxf(out[c], 0.0f)) : 0u;
+          const unsigned int mx = __reduce_max_sync(0xffffffffu, bits);
+          if ((tid & 31) == 0 && mx) atomicMax(a.chan_max + a.c0 + c, mx);
+        }
+      }
+    }
+  }
+}
+
+template <int KC, int PPT, bool SEC, int BLOCK, int VEC>
+__global__ void __launch_bounds__(BLOCK) shade_codes_kernel(const ShadeArgs a) {
+  extern __shared__ float4 s_light[];
+  const bool staged = a.L <= kLightTile;
+  if (staged) {
+    stage_light_codes<KC, VEC, BLOCK>(a, s_light, 0, a.L);
+    __syncthreads();
+  }
+  for (int64_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x) shade_tile<KC, PPT, SEC, BLOCK, VEC>(a, tile, s_light, staged);
+}
+
+template <int KC, int PPT, bool SEC, int BLOCK, int VEC>
+hsc_status launch_one(const ShadeArgs& a0, const LaunchCfg& cfg, cudaStream_t stream) {
+  constexpr int F4 = LightStage<KC, VEC>::F4;
+  ShadeArgs a = a0;
+  a.tiles = (a.P + (int64_t)BLOCK * PPT - 1) / ((int64_t)BLOCK * PPT);
+  const size_t smem = (size_t)min(a.L, kLightTile) * F4 * sizeof(float4);
+  auto kern = shade_codes_kernel<KC, PPT, SEC, BLOCK, VEC>;
+  static int occ = -1;
+  if (occ < 0) {
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, BLOCK, kLightTile * F4 * sizeof(float4)) != cudaSuccess)
+      o = 1;
+    occ = o > 0 ? o : 1;
+  }
+  // waves > 0: persistent grid of waves x (resident CTAs per SM) x SMs striding
+  // over the pixel tiles; waves == 0: one CTA per tile.
+  int64_t grid = cfg.waves > 0 ? (int64_t)cfg.sm_count * occ * cfg.waves : a.tiles;
+  if (grid > a.tiles) grid = a.tiles;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, BLOCK, smem, stream>>>(a);
+  return check_launch("shade_codes_kernel");
+}
+
+template <int KC, int BLOCK>
+hsc_status launch_kc_block(const ShadeArgs& a, bool sec, const LaunchCfg& cfg, cudaStream_t s) {
+  if (cfg.vec == 2) {
+    // paired points: with the bounce every PPT pairs up; without it PPT must be even
+    switch (cfg.ppt) {
+      case 1: return sec ? launch_one<KC, 1, true, BLOCK, 2>(a, cfg, s) : launch_one<KC, 2, false, BLOCK, 2>(a, cfg, s);
+      case 4: return sec ? launch_one<KC, 4, true, BLOCK, 2>(a, cfg, s) : launch_one<KC, 4, false, BLOCK, 2>(a, cfg, s);
+      default: return sec ? launch_one<KC, 2, true, BLOCK, 2>(a, cfg, s) : launch_one<KC, 2, false, BLOCK, 2>(a, cfg, s);
+    }
+  }
+  switch (cfg.ppt) {
+    case 1: return sec ? launch_one<KC, 1, true, BLOCK, 1>(a, cfg, s) : launch_one<KC, 1, false, BLOCK, 1>(a, cfg, s);
+    case 4: return sec ? launch_one<KC, 4, true, BLOCK, 1>(a, cfg, s) : launch_one<KC, 4, false, BLOCK, 1>(a, cfg, s);
+    default: return sec ? launch_one<KC, 2, true, BLOCK, 1>(a, cfg, s) : launch_one<KC, 2, false, BLOCK, 1>(a, cfg, s);
+  }
+}
+
+}  // namespace
+
+// Launches the KC-channel shading kernel in the configuration `cfg`
+// (pixels per thread 1/2/4, 128 or 256 threads, persistent or one CTA per
+// tile, scalar or f32x2-paired points).
+template <int KC>
+hsc_status launch_kc(const ShadeArgs& a, bool sec, const LaunchCfg& cfg, cudaStream_t s) {
+  return cfg.block == 256 ? launch_kc_block<KC, 256>(a, sec, cfg, s) : launch_kc_block<KC, 128>(a, sec, cfg, s);
+}
+
+}  // namespace hsc

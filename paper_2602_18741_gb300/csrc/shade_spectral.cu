@@ -4,19 +4,24 @@
 // kernels; per (pixel, light) it does the geometry term plus n FMAs instead
 // of k.
 //
-// Mapping: one thread per pixel holds NCH >= n FP32 accumulators.  Lights and
-// their (I/pi)-scaled SPDs are staged in shared memory and read as broadcast
-// float4s.  With a secondary G-buffer the thread first sums the light at the
-// secondary point, turns it into h * (R2 (.) A2), then adds the direct light
-// of the primary point on top and multiplies by R1; XYZ = T S is fused.
+// Mapping: a thread owns PTS shading points (PTS = 2: the primary and the
+// secondary point of one pixel, or two pixels when there is no secondary
+// G-buffer) with NCH >= n FP32 accumulators each.  Lights and their
+// (I/pi)-scaled SPDs are staged in shared memory; every broadcast float4 load
+// of a light's spectrum feeds 4 * PTS FMAs, which keeps the shared-memory pipe
+// below the FP32 pipe (with one point per thread the loads, one per four FMAs,
+// saturate it).  VEC = 2 keeps the accumulators in f32x2 pairs along
+// wavelength (one packed FMA per two samples).  With the secondary point the
+// radiance is
+//     S = R1 (.) (A1 + h (R2 (.) A2)),  XYZ = T S fused.
 #include "common.cuh"
 #include "shade_latent.cuh"
+#include "tune.cuh"
 
 namespace hsc {
 
 namespace {
 
-constexpr int kSpecBlock = 128;
 constexpr int kSpecLightTile = 64;
 
 struct SpecArgs {
@@ -65,53 +70,180 @@ __device__ __forceinline__ void stage_lights(const SpecArgs& a, float4* s_light,
   }
 }
 
-template <int NCH>
-__device__ __forceinline__ void sweep(const float4* s_light, int nl, float x, float y, float z, float nx, float ny,
-                                      float nz, float (&acc)[NCH]) {
+struct Pt {
+  float x, y, z, nx, ny, nz;
+};
+
+__device__ __forceinline__ Pt load_pt(const float* pos, const float* nrm, int64_t p) {
+  Pt q;
+  q.x = __ldg(pos + 3 * p);
+  q.y = __ldg(pos + 3 * p + 1);
+  q.z = __ldg(pos + 3 * p + 2);
+  q.nx = __ldg(nrm + 3 * p);
+  q.ny = __ldg(nrm + 3 * p + 1);
+  q.nz = __ldg(nrm + 3 * p + 2);
+  return q;
+}
+
+// acc[q][i] += g(q, l) * V_l[i] for PTS points over nl staged lights.
+template <int NCH, int PTS>
+__device__ __forceinline__ void sweep(const float4* s_light, int nl, const Pt (&pt)[PTS], float (&acc)[PTS][NCH]) {
   constexpr int F4 = SpecLayout<NCH>::F4;
   constexpr int V4 = SpecLayout<NCH>::V4;
 #pragma unroll 1
   for (int l = 0; l < nl; ++l) {
     const float4 pl = s_light[l * F4];
-    const float g = geometry_term(x, y, z, nx, ny, nz, pl.x, pl.y, pl.z);
+    float g[PTS];
+#pragma unroll
+    for (int q = 0; q < PTS; ++q)
+      g[q] = geometry_term(pt[q].x, pt[q].y, pt[q].z, pt[q].nx, pt[q].ny, pt[q].nz, pl.x, pl.y, pl.z);
 #pragma unroll
     for (int f = 0; f < V4; ++f) {
       const float4 v = s_light[l * F4 + 1 + f];
-      if (4 * f + 0 < NCH) acc[4 * f + 0] = __fmaf_rn(g, v.x, acc[4 * f + 0]);
-      if (4 * f + 1 < NCH) acc[4 * f + 1] = __fmaf_rn(g, v.y, acc[4 * f + 1]);
-      if (4 * f + 2 < NCH) acc[4 * f + 2] = __fmaf_rn(g, v.z, acc[4 * f + 2]);
-      if (4 * f + 3 < NCH) acc[4 * f + 3] = __fmaf_rn(g, v.w, acc[4 * f + 3]);
+#pragma unroll
+      for (int q = 0; q < PTS; ++q) {
+        if (4 * f + 0 < NCH) acc[q][4 * f + 0] = __fmaf_rn(g[q], v.x, acc[q][4 * f + 0]);
+        if (4 * f + 1 < NCH) acc[q][4 * f + 1] = __fmaf_rn(g[q], v.y, acc[q][4 * f + 1]);
+        if (4 * f + 2 < NCH) acc[q][4 * f + 2] = __fmaf_rn(g[q], v.z, acc[q][4 * f + 2]);
+        if (4 * f + 3 < NCH) acc[q][4 * f + 3] = __fmaf_rn(g[q], v.w, acc[q][4 * f + 3]);
+      }
     }
   }
 }
 
-template <int NCH, bool SEC>
-__global__ void __launch_bounds__(kSpecBlock) shade_spectral_kernel(const SpecArgs a) {
+// The same sweep with the accumulators in f32x2 pairs along wavelength: one
+// packed FMA per two samples, the light's float4 splitting into two pairs.
+// Each half performs exactly the scalar FMA, so the results are identical.
+template <int NCH, int PTS>
+__device__ __forceinline__ void sweep_x2(const float4* s_light, int nl, const Pt (&pt)[PTS],
+                                         f2 (&acc)[PTS][NCH / 2]) {
+  constexpr int F4 = SpecLayout<NCH>::F4;
+  constexpr int V4 = SpecLayout<NCH>::V4;
+  static_assert(NCH % 4 == 0, "paired sweep needs NCH divisible by 4");
+  const ulonglong2* sl = reinterpret_cast<const ulonglong2*>(s_light);
+#pragma unroll 1
+  for (int l = 0; l < nl; ++l) {
+    const float4 pl = s_light[l * F4];
+    f2 g[PTS];
+#pragma unroll
+    for (int q = 0; q < PTS; ++q) {
+      const float gs = geometry_term(pt[q].x, pt[q].y, pt[q].z, pt[q].nx, pt[q].ny, pt[q].nz, pl.x, pl.y, pl.z);
+      g[q] = f2_pack(gs, gs);
+    }
+#pragma unroll
+    for (int f = 0; f < V4; ++f) {
+      const ulonglong2 v = sl[l * F4 + 1 + f];
+#pragma unroll
+      for (int q = 0; q < PTS; ++q) {
+        acc[q][2 * f + 0] = f2_fma(g[q], v.x, acc[q][2 * f + 0]);
+        acc[q][2 * f + 1] = f2_fma(g[q], v.y, acc[q][2 * f + 1]);
+      }
+    }
+  }
+}
+
+// Reflectance R_m1, XYZ and optional spectrum output of one pixel given the
+// radiance before the primary reflectance, acc[i] = A1 + h (R2 (.) A2).
+template <int NCH>
+__device__ __forceinline__ void finish_pixel(const SpecArgs& a, int64_t p, bool valid, int m1, bool bad,
+                                             const float (&acc)[NCH]) {
+  const float* r1 = a.mats + (int64_t)(bad ? 0 : m1) * a.n;
+  float X = 0.0f, Y = 0.0f, Z = 0.0f;
+#pragma unroll
+  for (int i = 0; i < NCH; ++i) {
+    if (i < a.n) {
+      const float S = bad ? 0.0f : __fmul_rn(__ldg(r1 + i), acc[i]);
+      X = __fmaf_rn(__ldg(a.T + i), S, X);
+      Y = __fmaf_rn(__ldg(a.T + a.n + i), S, Y);
+      Z = __fmaf_rn(__ldg(a.T + 2 * a.n + i), S, Z);
+      if (a.spectra && valid) a.spectra[p * a.n + i] = S;
+    }
+  }
+  if (valid) {
+    a.xyz[3 * p] = X;
+    a.xyz[3 * p + 1] = Y;
+    a.xyz[3 * p + 2] = Z;
+    if (bad) atomicOr(a.err, HSC_DEVERR_MATERIAL);
+  }
+}
+
+// PTS = 1: one point per thread; with the secondary G-buffer the thread runs
+// the secondary sweep first and folds h (R2 (.) A2) into the accumulators
+// before adding the primary sweep.
+// PTS = 2: both points (or two pixels) share every light load.
+template <int NCH, bool SEC, int PTS, int BLOCK, int VEC>
+__global__ void __launch_bounds__(BLOCK) shade_spectral_kernel(const SpecArgs a) {
   extern __shared__ float4 s_light[];
   const bool multi_tile = a.L > kSpecLightTile;
   if (!multi_tile) {
     stage_lights<NCH>(a, s_light, 0, a.L);
     __syncthreads();
   }
-  const int64_t tiles = (a.P + kSpecBlock - 1) / kSpecBlock;
+  // pixels per thread: 2 only for PTS = 2 without a secondary G-buffer
+  constexpr int PXT = (PTS == 2 && !SEC) ? 2 : 1;
+  const int64_t tiles = (a.P + (int64_t)BLOCK * PXT - 1) / ((int64_t)BLOCK * PXT);
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const int64_t p = tile * kSpecBlock + threadIdx.x;
-    const bool valid = p < a.P;
-    const int64_t pc = valid ? p : a.P - 1;
-    const float x1 = __ldg(a.x1 + 3 * pc), y1 = __ldg(a.x1 + 3 * pc + 1), z1 = __ldg(a.x1 + 3 * pc + 2);
-    const float nx1 = __ldg(a.n1 + 3 * pc), ny1 = __ldg(a.n1 + 3 * pc + 1), nz1 = __ldg(a.n1 + 3 * pc + 2);
-    const int m1 = __ldg(a.m1 + pc);
-    bool bad = (m1 < 0 || m1 >= a.n_mat);
-    float acc[NCH];
+    int64_t pix[PXT];
+    bool valid[PXT];
+    int m1[PXT];
+    bool bad[PXT];
+    Pt pt[PTS];
 #pragma unroll
-    for (int i = 0; i < NCH; ++i) acc[i] = 0.0f;
+    for (int j = 0; j < PXT; ++j) {
+      pix[j] = tile * (BLOCK * PXT) + (int64_t)j * BLOCK + threadIdx.x;
+      valid[j] = pix[j] < a.P;
+      const int64_t pc = valid[j] ? pix[j] : a.P - 1;
+      m1[j] = __ldg(a.m1 + pc);
+      bad[j] = (m1[j] < 0 || m1[j] >= a.n_mat);
+      pt[j] = load_pt(a.x1, a.n1, pc);
+    }
+    float acc[PTS][NCH];
+#pragma unroll
+    for (int q = 0; q < PTS; ++q)
+#pragma unroll
+      for (int i = 0; i < NCH; ++i) acc[q][i] = 0.0f;
 
+    int m2 = 0;
+    bool bad2 = false;
+    float h = 0.0f;
     if (SEC) {
-      const float x2 = __ldg(a.x2 + 3 * pc), y2 = __ldg(a.x2 + 3 * pc + 1), z2 = __ldg(a.x2 + 3 * pc + 2);
-      const float nx2 = __ldg(a.n2 + 3 * pc), ny2 = __ldg(a.n2 + 3 * pc + 1), nz2 = __ldg(a.n2 + 3 * pc + 2);
-      const int m2 = __ldg(a.m2 + pc);
-      const bool bad2 = (m2 < 0 || m2 >= a.n_mat);
-      bad = bad || bad2;
+      const int64_t pc = valid[0] ? pix[0] : a.P - 1;
+      const Pt s2 = load_pt(a.x2, a.n2, pc);
+      m2 = __ldg(a.m2 + pc);
+      bad2 = (m2 < 0 || m2 >= a.n_mat);
+      bad[0] = bad[0] || bad2;
+      h = bounce_term(pt[0].x, pt[0].y, pt[0].z, pt[0].nx, pt[0].ny, pt[0].nz, s2.x, s2.y, s2.z, s2.nx, s2.ny,
+                      s2.nz);
+      if (PTS == 2) pt[PTS - 1] = s2;
+      if (PTS == 1) {
+        // secondary sweep first, then acc = h (R2 (.) A2)
+        Pt one[1] = {s2};
+        float a2[1][NCH];
+#pragma unroll
+        for (int i = 0; i < NCH; ++i) a2[0][i] = 0.0f;
+        for (int l0 = 0; l0 < a.L; l0 += kSpecLightTile) {
+          const int nl = min(kSpecLightTile, a.L - l0);
+          if (multi_tile) {
+            __syncthreads();
+            stage_lights<NCH>(a, s_light, l0, nl);
+            __syncthreads();
+          }
+          sweep<NCH, 1>(s_light, nl, one, a2);
+        }
+        const float* r2 = a.mats + (int64_t)(bad2 ? 0 : m2) * a.n;
+#pragma unroll
+        for (int i = 0; i < NCH; ++i) {
+          const float r = (i < a.n && !bad2) ? __ldg(r2 + i) : 0.0f;
+          acc[0][i] = __fmul_rn(h, __fmul_rn(r, a2[0][i]));
+        }
+      }
+    }
+    if constexpr (VEC == 2) {
+      f2 acc2[PTS][NCH / 2];
+#pragma unroll
+      for (int q = 0; q < PTS; ++q)
+#pragma unroll
+        for (int i = 0; i < NCH / 2; ++i) acc2[q][i] = f2_pack(acc[q][2 * i], acc[q][2 * i + 1]);
       for (int l0 = 0; l0 < a.L; l0 += kSpecLightTile) {
         const int nl = min(kSpecLightTile, a.L - l0);
         if (multi_tile) {
@@ -119,70 +251,81 @@ __global__ void __launch_bounds__(kSpecBlock) shade_spectral_kernel(const SpecAr
           stage_lights<NCH>(a, s_light, l0, nl);
           __syncthreads();
         }
-        sweep<NCH>(s_light + 0, nl, x2, y2, z2, nx2, ny2, nz2, acc);
+        sweep_x2<NCH, PTS>(s_light, nl, pt, acc2);
       }
-      const float h = bounce_term(x1, y1, z1, nx1, ny1, nz1, x2, y2, z2, nx2, ny2, nz2);
+#pragma unroll
+      for (int q = 0; q < PTS; ++q)
+#pragma unroll
+        for (int i = 0; i < NCH / 2; ++i) f2_unpack(acc2[q][i], acc[q][2 * i], acc[q][2 * i + 1]);
+    } else {
+      for (int l0 = 0; l0 < a.L; l0 += kSpecLightTile) {
+        const int nl = min(kSpecLightTile, a.L - l0);
+        if (multi_tile) {
+          __syncthreads();
+          stage_lights<NCH>(a, s_light, l0, nl);
+          __syncthreads();
+        }
+        sweep<NCH, PTS>(s_light, nl, pt, acc);
+      }
+    }
+    if (SEC && PTS == 2) {
+      // A1 + h (R2 (.) A2)
       const float* r2 = a.mats + (int64_t)(bad2 ? 0 : m2) * a.n;
 #pragma unroll
       for (int i = 0; i < NCH; ++i) {
         const float r = (i < a.n && !bad2) ? __ldg(r2 + i) : 0.0f;
-        acc[i] = __fmul_rn(h, __fmul_rn(r, acc[i]));
+        acc[0][i] = __fmaf_rn(h, __fmul_rn(r, acc[PTS - 1][i]), acc[0][i]);
       }
     }
-    for (int l0 = 0; l0 < a.L; l0 += kSpecLightTile) {
-      const int nl = min(kSpecLightTile, a.L - l0);
-      if (multi_tile) {
-        __syncthreads();
-        stage_lights<NCH>(a, s_light, l0, nl);
-        __syncthreads();
-      }
-      sweep<NCH>(s_light, nl, x1, y1, z1, nx1, ny1, nz1, acc);
-    }
-    const float* r1 = a.mats + (int64_t)(bad ? 0 : m1) * a.n;
-    float X = 0.0f, Y = 0.0f, Z = 0.0f;
-#pragma unroll
-    for (int i = 0; i < NCH; ++i) {
-      if (i < a.n) {
-        const float S = bad ? 0.0f : __fmul_rn(__ldg(r1 + i), acc[i]);
-        X = __fmaf_rn(__ldg(a.T + i), S, X);
-        Y = __fmaf_rn(__ldg(a.T + a.n + i), S, Y);
-        Z = __fmaf_rn(__ldg(a.T + 2 * a.n + i), S, Z);
-        if (a.spectra && valid) a.spectra[p * a.n + i] = S;
-      }
-    }
-    if (valid) {
-      a.xyz[3 * p] = X;
-      a.xyz[3 * p + 1] = Y;
-      a.xyz[3 * p + 2] = Z;
-      if (bad) atomicOr(a.err, HSC_DEVERR_MATERIAL);
-    }
+    finish_pixel<NCH>(a, pix[0], valid[0], m1[0], bad[0], acc[0]);
+    if (PXT == 2) finish_pixel<NCH>(a, pix[PXT - 1], valid[PXT - 1], m1[PXT - 1], bad[PXT - 1], acc[PTS - 1]);
   }
 }
 
-template <int NCH, bool SEC>
-hsc_status launch_spec(const SpecArgs& a, int sm_count, cudaStream_t s) {
+template <int NCH, bool SEC, int PTS, int BLOCK, int VEC>
+hsc_status launch_spec(const SpecArgs& a, const LaunchCfg& cfg, cudaStream_t s) {
   constexpr int F4 = SpecLayout<NCH>::F4;
-  auto kern = shade_spectral_kernel<NCH, SEC>;
+  auto kern = shade_spectral_kernel<NCH, SEC, PTS, BLOCK, VEC>;
   const size_t smem_max = (size_t)kSpecLightTile * F4 * sizeof(float4);
   const size_t smem = (size_t)min(a.L, kSpecLightTile) * F4 * sizeof(float4);
   static int occ = -1;
   if (occ < 0) {
     if (smem_max > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
     int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kSpecBlock, smem_max) != cudaSuccess) o = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, BLOCK, smem_max) != cudaSuccess) o = 1;
     occ = o > 0 ? o : 1;
   }
-  const int64_t tiles = (a.P + kSpecBlock - 1) / kSpecBlock;
-  int64_t grid = (int64_t)sm_count * occ;
+  constexpr int PXT = (PTS == 2 && !SEC) ? 2 : 1;
+  const int64_t tiles = (a.P + (int64_t)BLOCK * PXT - 1) / ((int64_t)BLOCK * PXT);
+  int64_t grid = cfg.waves > 0 ? (int64_t)cfg.sm_count * occ * cfg.waves : tiles;
   if (grid > tiles) grid = tiles;
   if (grid < 1) grid = 1;
-  kern<<<(unsigned)grid, kSpecBlock, smem, s>>>(a);
+  kern<<<(unsigned)grid, BLOCK, smem, s>>>(a);
   return check_launch("shade_spectral_kernel");
 }
 
+template <int NCH, int VEC>
+hsc_status launch_spec_vec(const SpecArgs& a, bool sec, const LaunchCfg& cfg, cudaStream_t s) {
+  if (cfg.ppt == 2)
+    return sec ? launch_spec<NCH, true, 2, 128, VEC>(a, cfg, s) : launch_spec<NCH, false, 2, 128, VEC>(a, cfg, s);
+  return sec ? launch_spec<NCH, true, 1, 128, VEC>(a, cfg, s) : launch_spec<NCH, false, 1, 128, VEC>(a, cfg, s);
+}
+
 template <int NCH>
-hsc_status launch_spec_sec(const SpecArgs& a, bool sec, int sm_count, cudaStream_t s) {
-  return sec ? launch_spec<NCH, true>(a, sm_count, s) : launch_spec<NCH, false>(a, sm_count, s);
+hsc_status launch_spec_cfg(const SpecArgs& a, bool sec, const LaunchCfg& cfg, cudaStream_t s) {
+  return cfg.vec == 2 ? launch_spec_vec<NCH, 2>(a, sec, cfg, s) : launch_spec_vec<NCH, 1>(a, sec, cfg, s);
+}
+
+hsc_status launch_spectral(const SpecArgs& a, bool sec, const LaunchCfg& cfg, cudaStream_t s) {
+  const int n = a.n;
+  if (n <= 8) return launch_spec_cfg<8>(a, sec, cfg, s);
+  if (n <= 16) return launch_spec_cfg<16>(a, sec, cfg, s);
+  if (n <= 32) return launch_spec_cfg<32>(a, sec, cfg, s);
+  if (n <= 48) return launch_spec_cfg<48>(a, sec, cfg, s);
+  if (n <= 64) return launch_spec_cfg<64>(a, sec, cfg, s);
+  if (n <= 84) return launch_spec_cfg<84>(a, sec, cfg, s);
+  if (n <= 96) return launch_spec_cfg<96>(a, sec, cfg, s);
+  return launch_spec_cfg<128>(a, sec, cfg, s);
 }
 
 }  // namespace
@@ -233,13 +376,9 @@ extern "C" hsc_status hsc_shade_spectral(hsc_ctx* ctx, const hsc_gbuffer* g1, co
   a.err = ctx->d_err;
   const bool sec = g2 != nullptr;
   cudaStream_t s = hsc::as_stream(stream);
-  const int sm = ctx->sm_count;
-  if (n <= 8) return hsc::launch_spec_sec<8>(a, sec, sm, s);
-  if (n <= 16) return hsc::launch_spec_sec<16>(a, sec, sm, s);
-  if (n <= 32) return hsc::launch_spec_sec<32>(a, sec, sm, s);
-  if (n <= 48) return hsc::launch_spec_sec<48>(a, sec, sm, s);
-  if (n <= 64) return hsc::launch_spec_sec<64>(a, sec, sm, s);
-  if (n <= 84) return hsc::launch_spec_sec<84>(a, sec, sm, s);
-  if (n <= 96) return hsc::launch_spec_sec<96>(a, sec, sm, s);
-  return hsc::launch_spec_sec<128>(a, sec, sm, s);
+  const hsc::TuneKey key = hsc::make_tune_key(hsc::kTuneSpectral, n, sec, lights->count, pixels, 0);
+  auto launch = [&](const hsc::LaunchCfg& c) { return hsc::launch_spectral(a, sec, c, s); };
+  hsc::LaunchCfg cfg;
+  HSC_TRY(hsc::tuned_cfg(ctx, key, hsc::spectral_candidates(ctx), launch, s, &cfg));
+  return launch(cfg);
 }

@@ -1,0 +1,155 @@
+// Launch-configuration autotuner (see tune.cuh).
+#include "tune.cuh"
+
+#include <stdio.h>
+
+namespace hsc {
+
+static int ceil_log2(int64_t v) {
+  int b = 0;
+  while (((int64_t)1 << b) < v && b < 62) ++b;
+  return b;
+}
+
+TuneKey make_tune_key(int kind, int channels, bool sec, int lights, int64_t pixels, int dtype) {
+  TuneKey k;
+  k.kind = kind;
+  k.channels = channels;
+  k.sec = sec ? 1 : 0;
+  k.lbucket = ceil_log2(lights);
+  k.pbucket = ceil_log2(pixels);
+  k.dtype = dtype;
+  return k;
+}
+
+std::vector<LaunchCfg> latent_candidates(const hsc_ctx* ctx) {
+  std::vector<LaunchCfg> v;
+  LaunchCfg d = default_cfg(ctx);
+  v.push_back(d);
+  for (int vec : {1, 2})
+    for (int ppt : {1, 2, 4})
+      for (int block : {128, 256})
+        for (int waves : {1, 0}) {
+          LaunchCfg c = d;
+          c.ppt = ppt;
+          c.block = block;
+          c.waves = waves;
+          c.vec = vec;
+          if (c.ppt == d.ppt && c.block == d.block && c.waves == d.waves && c.vec == d.vec) continue;
+          v.push_back(c);
+        }
+  return v;
+}
+
+std::vector<LaunchCfg> spectral_candidates(const hsc_ctx* ctx) {
+  std::vector<LaunchCfg> v;
+  LaunchCfg d;
+  d.sm_count = ctx->sm_count;
+  d.block = 128;
+  d.ppt = 2;
+  d.waves = 1;
+  v.push_back(d);
+  for (int vec : {1, 2})
+    for (int ppt : {1, 2})
+      for (int waves : {1, 0}) {
+        LaunchCfg c = d;
+        c.ppt = ppt;
+        c.waves = waves;
+        c.vec = vec;
+        if (c.ppt == d.ppt && c.waves == d.waves && c.vec == d.vec) continue;
+        v.push_back(c);
+      }
+  return v;
+}
+
+hsc_status tuned_cfg(hsc_ctx* ctx, const TuneKey& key, const std::vector<LaunchCfg>& cands,
+                     const std::function<hsc_status(const LaunchCfg&)>& launch, cudaStream_t s, LaunchCfg* out) {
+  *out = cands[0];
+  if (ctx->forced.ppt > 0) {
+    *out = ctx->forced;
+    out->sm_count = ctx->sm_count;
+    return HSC_OK;
+  }
+  if (!ctx->autotune || cands.size() < 2) return HSC_OK;
+  auto it = ctx->tuned.find(key);
+  if (it != ctx->tuned.end()) {
+    *out = it->second;
+    return HSC_OK;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return HSC_OK;
+  cudaEvent_t e0, e1;
+  HSC_CUDA(cudaEventCreate(&e0));
+  HSC_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  LaunchCfg best_cfg = cands[0];
+  char line[256];
+  snprintf(line, sizeof(line), "%s ch=%d sec=%d L<=2^%d P<=2^%d dt=%d:", key.kind == kTuneLatent ? "latent" : "spectral",
+           key.channels, key.sec, key.lbucket, key.pbucket, key.dtype);
+  std::string rep = line;
+  hsc_status st = HSC_OK;
+  for (const LaunchCfg& c : cands) {
+    if ((st = launch(c)) != HSC_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 3 && st == HSC_OK; ++r) st = launch(c);
+    if (st != HSC_OK) break;
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      st = set_error(HSC_ERR_CUDA, "autotune event wait failed");
+      break;
+    }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= 3.0f;
+    snprintf(line, sizeof(line), " [ppt=%d block=%d waves=%d vec=%d %.4f ms]", c.ppt, c.block, c.waves, c.vec, ms);
+    rep += line;
+    if (ms < best) {
+      best = ms;
+      best_cfg = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != HSC_OK) return st;
+  snprintf(line, sizeof(line), " -> ppt=%d block=%d waves=%d vec=%d\n", best_cfg.ppt, best_cfg.block, best_cfg.waves,
+           best_cfg.vec);
+  rep += line;
+  ctx->tune_report += rep;
+  ctx->tuned[key] = best_cfg;
+  *out = best_cfg;
+  return HSC_OK;
+}
+
+}  // namespace hsc
+
+extern "C" {
+
+hsc_status hsc_set_autotune(hsc_ctx* ctx, int enable) {
+  hsc::clear_error();
+  HSC_CHECK_CTX(ctx);
+  ctx->autotune = enable ? 1 : 0;
+  return HSC_OK;
+}
+
+const char* hsc_tune_report(hsc_ctx* ctx) { return ctx ? ctx->tune_report.c_str() : ""; }
+
+hsc_status hsc_force_launch_config(hsc_ctx* ctx, int ppt, int block, int waves, int vec) {
+  hsc::clear_error();
+  HSC_CHECK_CTX(ctx);
+  if (ppt <= 0) {
+    ctx->forced = hsc::LaunchCfg();
+    ctx->forced.ppt = 0;
+    return HSC_OK;
+  }
+  HSC_REQUIRE(ppt == 1 || ppt == 2 || ppt == 4, "ppt must be 1, 2 or 4");
+  HSC_REQUIRE(block == 128 || block == 256, "block must be 128 or 256");
+  HSC_REQUIRE(waves >= 0 && waves <= 64, "waves out of range");
+  HSC_REQUIRE(vec == 1 || vec == 2, "vec must be 1 or 2");
+  ctx->forced.vec = vec;
+  ctx->forced.ppt = ppt;
+  ctx->forced.block = block;
+  ctx->forced.waves = waves;
+  return HSC_OK;
+}
+
+}  // extern "C"

@@ -501,3 +501,79 @@ def test_full_size_1080p_sampled(env, k):
     assert metrics.rel_xyz_error(xs[torch.from_numpy(idx).to(dev)].cpu().numpy(), xs_ref) <= TOL
     # invariants at full size: non-negative latent, finite XYZ
     assert float(lat.min()) >= 0.0 and bool(torch.isfinite(xs).all())
+
+
+# ------------------------------------------------ launch configurations
+
+def test_every_latent_launch_config_is_bit_identical(env):
+    # pixels per thread, CTA size and grid shape change only the thread
+    # mapping, never a channel's arithmetic: every configuration must give the
+    # same bits (the autotuner relies on it)
+    hsc, ctx, dev = env
+    import torch
+    f = hi.make_frame(31, 97, 61, hi.GRID_81, n_smooth=20, n_saw=5, lights=37, secondary=True)
+    E, D = _codec(9, 81)
+    df = upload(hsc, ctx, f, dev)
+    zm, zl = encode_all(hsc, ctx, df, E)
+    M = torch.empty(3, 9, device=dev)
+    hsc.hsc_fold_xyz(ctx, df.T, torch.from_numpy(D).to(dev), M)
+    outs = []
+    configs = [(p_, b_, w_, v_) for p_ in (1, 2, 4) for b_ in (128, 256) for w_ in (1, 0, 3) for v_ in (1, 2)]
+    for ppt, block, waves, vec in configs:
+        hsc.hsc_force_launch_config(ctx, ppt, block, waves, vec)
+        lat = torch.empty(f.pixels, 9, device=dev)
+        xyz = torch.empty(f.pixels, 3, device=dev)
+        hsc.hsc_shade_latent(ctx, df.g1, df.g2, zm, df.lights, zl, hsc.HSC_FUSED, lat, xyz_out=xyz, M_xyz=M)
+        p3 = torch.empty(f.pixels, 3, device=dev)
+        hsc.hsc_shade_pass(ctx, df.g1, None, zm, df.lights, zl, 1, p3)
+        outs.append((lat, xyz, p3))
+    hsc.hsc_force_launch_config(ctx, 0)
+    hsc.hsc_sync(ctx)
+    for lat, xyz, p3 in outs[1:]:
+        assert torch.equal(lat, outs[0][0]) and torch.equal(xyz, outs[0][1]) and torch.equal(p3, outs[0][2])
+    z_ref, _ = _oracle_latent(f, E, D)
+    assert rel_err_rows(outs[0][0].cpu().numpy(), z_ref) <= TOL
+
+
+@pytest.mark.parametrize("sec", [False, True])
+def test_spectral_launch_configs_match_oracle(env, sec):
+    hsc, ctx, dev = env
+    import torch
+    f = hi.make_frame(32, 83, 41, hi.GRID_81, n_smooth=20, n_saw=5, lights=70, secondary=sec)
+    df = upload(hsc, ctx, f, dev)
+    S_ref, xyz_ref = shade.shade_spectral(f)
+    for ppt, waves, vec in [(p_, w_, v_) for p_ in (1, 2) for w_ in (1, 0) for v_ in (1, 2)]:
+        hsc.hsc_force_launch_config(ctx, ppt, 128, waves, vec)
+        xyz = torch.empty(f.pixels, 3, device=dev)
+        S = torch.empty(f.pixels, f.n, device=dev)
+        hsc.hsc_shade_spectral(ctx, df.g1, df.g2, df.mats, df.lights, df.spd, df.T, xyz, S)
+        hsc.hsc_sync(ctx)
+        assert rel_err_rows(S.cpu().numpy(), S_ref) <= TOL, (ppt, waves, vec)
+        assert metrics.rel_xyz_error(xyz.cpu().numpy(), xyz_ref) <= TOL, (ppt, waves, vec)
+    hsc.hsc_force_launch_config(ctx, 0)
+
+
+def test_autotune_picks_a_config_without_changing_results(env):
+    hsc, ctx, dev = env
+    import torch
+    f = hi.make_frame(33, 160, 90, hi.GRID_81, n_smooth=20, n_saw=5, lights=24, secondary=True)
+    E, D = _codec(6, 81)
+    df = upload(hsc, ctx, f, dev)
+    zm, zl = encode_all(hsc, ctx, df, E)
+    ref = torch.empty(f.pixels, 6, device=dev)
+    hsc.hsc_shade_latent(ctx, df.g1, df.g2, zm, df.lights, zl, hsc.HSC_FUSED, ref)
+    tctx = hsc.Context(0)
+    hsc.hsc_set_autotune(tctx, True)
+    got = torch.empty(f.pixels, 6, device=dev)
+    hsc.hsc_shade_latent(tctx, df.g1, df.g2, zm, df.lights, zl, hsc.HSC_FUSED, got)
+    xs = torch.empty(f.pixels, 3, device=dev)
+    hsc.hsc_shade_spectral(tctx, df.g1, df.g2, df.mats, df.lights, df.spd, df.T, xs)
+    hsc.hsc_sync(tctx)
+    rep = hsc.hsc_tune_report(tctx)
+    assert "latent ch=6" in rep and "spectral ch=81" in rep and "->" in rep
+    assert torch.equal(got, ref)
+    # a second call of the same shape class reuses the cached choice
+    hsc.hsc_shade_latent(tctx, df.g1, df.g2, zm, df.lights, zl, hsc.HSC_FUSED, got)
+    hsc.hsc_sync(tctx)
+    assert hsc.hsc_tune_report(tctx) == rep
+    tctx.close()

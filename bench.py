@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the secondary rows (spectral, passes, decodes)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--serve-seconds", type=float, default=8.0,
+                    help="length of the Poisson request stream served (0 = skip); the first quarter is warm-up")
     return ap.parse_args()
 
 
@@ -260,7 +262,7 @@ def run_hsc(args, rank: int, world: int):
         # roofline of the dominant kernel: the fused shading launch
         sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
         peak_mhz = _peak_sm_mhz()
-        ops_per_eval = 14 + k          # 13 FP32 geometry ops + 1 MUFU + k FMAs
+        ops_per_eval = 13 + k          # 12 FP32 geometry ops + 1 MUFU rsqrt + k FMAs
         ops = evals * ops_per_eval
         shade_avg_s = statistics.mean(shade_ms) * 1e-3
         achieved = ops / shade_avg_s / 1e12
@@ -332,7 +334,7 @@ def secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T,
     ms, _ = timed(spectral, K, W)
     spec_ms = statistics.mean(ms)
     rows["spectral_n81"] = {"ms": spec_ms, "evals_per_s": evals / (spec_ms * 1e-3),
-                            "ops_per_eval": 14 + 81}
+                            "ops_per_eval": 13 + 81}
 
     Mk = _M(hsc, ctx, T, Dd)
 
@@ -342,7 +344,7 @@ def secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T,
     ms, _ = timed(fused, K, W)
     fused_ms = statistics.mean(ms)
     rows[f"latent_fused_k{args.k}_xyz"] = {"ms": fused_ms, "evals_per_s": evals / (fused_ms * 1e-3),
-                                            "ops_per_eval": 14 + args.k}
+                                            "ops_per_eval": 13 + args.k}
     rows["speedup_latent_fused_vs_spectral"] = spec_ms / fused_ms
 
     lat_p = torch.empty_like(lat)
@@ -374,7 +376,7 @@ def secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T,
 
     ms, _ = timed(fused9, K, W)
     f9 = statistics.mean(ms)
-    rows["latent_fused_k9_xyz"] = {"ms": f9, "evals_per_s": evals / (f9 * 1e-3), "ops_per_eval": 23}
+    rows["latent_fused_k9_xyz"] = {"ms": f9, "evals_per_s": evals / (f9 * 1e-3), "ops_per_eval": 22}
     rows["speedup_latent_fused_k9_vs_spectral"] = spec_ms / f9
 
     # decode to spectra (FP32 CUDA cores): P x 81 float32 out
@@ -444,7 +446,35 @@ def secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T,
                                           "de76_mean": float(s[3])}
     hsc.hsc_sync(ctx)
     rows.update(batch_rows(args, hsc, ctx, dev, timed))
+    if args.serve_seconds > 0:
+        rows.update(serve_rows(args, hsc, ctx, dev))
     return rows
+
+
+def serve_rows(args, hsc, ctx, dev):
+    """Poisson arrivals (200 requests/s) of render-plus-decode requests over 8
+    resident scenes (256 materials, 128-light pools), sizes from 512x512 to
+    3840x2160, k in {6, 9}, n in {31, 81}, 16-128 lights, BF16 codes, 40 GB
+    admission budget; served with continuous batching by the latent path and,
+    on the same stream, by naive n-sample shading.  Latency: arrival to GPU
+    completion; the first quarter of the stream is warm-up."""
+    from paper_2602_18741_gb300 import serve
+    scenes = serve.ResidentScenes(hsc, ctx, dev)
+    reqs = hi.request_stream(duration_s=args.serve_seconds)
+    warm = args.serve_seconds / 4.0
+    arrivals = [r.arrival_s for r in sorted(reqs, key=lambda r: r.arrival_s)]
+    out = {}
+    for mode in ("latent", "spectral"):
+        stats, _ = serve.serve(hsc, ctx, scenes, reqs, mode=mode)
+        sm = stats.summary(warmup_s=warm, arrivals=arrivals)
+        sm["offered_per_s"] = len(reqs) / args.serve_seconds
+        out[f"serve_{mode}"] = sm
+    lat, spe = out["serve_latent"], out["serve_spectral"]
+    if lat.get("p50_ms") and spe.get("p50_ms"):
+        out["serve_latency_ratio_spectral_over_latent"] = {"p50": spe["p50_ms"] / lat["p50_ms"],
+                                                           "p99": spe["p99_ms"] / lat["p99_ms"]}
+    del scenes
+    return out
 
 
 def batch_rows(args, hsc, ctx, dev, timed):

@@ -64,6 +64,7 @@ extern "C" {
 #define HSC_MAX_N 128     /* spectral sample limit                        */
 #define HSC_MAX_MAT (1 << 24)
 #define HSC_NOALLOC_MAX_K 96  /* channel limit of hsc_quantize_fp8_noalloc   */
+#define HSC_MAX_FRAMES_PER_CALL 512  /* frames per hsc_shade_frames call    */
 
 typedef struct hsc_ctx hsc_ctx;
 
@@ -136,9 +137,10 @@ HSC_API const char* hsc_tune_report(hsc_ctx* ctx);
  * benchmarking): ppt in {1, 2, 4} (spectral kernel: 1 or 2 shading points per
  * thread), block in {128, 256}, waves >= 0 (0 = one CTA per pixel tile),
  * vec = 1 (scalar FP32) or 2 (packed f32x2 pairs: pairs of shading points in
- * the latent kernels, pairs of wavelengths in the spectral kernel).  ppt <= 0
+ * the latent kernels, pairs of wavelengths in the spectral kernel), chunk =
+ * spectral channels per sweep (0 = default, 16, 28, 32, 44 or 84).  ppt <= 0
  * removes the override.                                                     */
-HSC_API hsc_status hsc_force_launch_config(hsc_ctx* ctx, int ppt, int block, int waves, int vec);
+HSC_API hsc_status hsc_force_launch_config(hsc_ctx* ctx, int ppt, int block, int waves, int vec, int chunk);
 
 /* ----------------------------------------------------- colour projection */
 
@@ -307,6 +309,15 @@ HSC_API hsc_status hsc_batch_create(hsc_ctx* ctx, const hsc_frame* frames, int c
 HSC_API hsc_status hsc_batch_shade(hsc_ctx* ctx, hsc_batch* batch, void* stream);
 /* Synchronise the device and free the batch.                                */
 HSC_API void hsc_batch_destroy(hsc_batch* batch);
+
+/* One-shot batched launch for continuous batching: shades and decodes to XYZ
+ * up to HSC_MAX_FRAMES_PER_CALL frames in one persistent launch on `stream`,
+ * asynchronously (descriptors go through a ring of 8 pinned host buffers in
+ * the context; a slot is reused once its previous launch has started, which
+ * may block the host briefly).  Same results as hsc_batch_shade and as
+ * shading each frame alone.  Tile shape: 2 pixels per thread, 128 threads,
+ * unless hsc_force_launch_config overrides it.                              */
+HSC_API hsc_status hsc_shade_frames(hsc_ctx* ctx, const hsc_frame* frames, int count, void* stream);
 
 /* ----------------------------------------------------------------- metrics */
 

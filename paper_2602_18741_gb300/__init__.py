@@ -30,6 +30,7 @@ HSC_F32, HSC_BF16, HSC_F16, HSC_FP8_E4M3 = range(4)
 HSC_PASSES, HSC_FUSED = range(2)
 HSC_MAX_K = 96
 HSC_NOALLOC_MAX_K = 96
+HSC_MAX_FRAMES_PER_CALL = 512
 HSC_MAX_N = 128
 
 STATUS_NAMES = {0: "HSC_OK", 1: "HSC_ERR_INVALID_ARG", 2: "HSC_ERR_CUDA", 3: "HSC_ERR_OOM",
@@ -76,7 +77,7 @@ _SIGS = {
     "hsc_shade_latent_scratch_bytes": ([_i64, _i32, _i32, _i32], ctypes.c_size_t),
     "hsc_set_autotune": ([_vp, _i32], _i32),
     "hsc_tune_report": ([_vp], ctypes.c_char_p),
-    "hsc_force_launch_config": ([_vp, _i32, _i32, _i32, _i32], _i32),
+    "hsc_force_launch_config": ([_vp, _i32, _i32, _i32, _i32, _i32], _i32),
     "hsc_cmf_weights": ([_vp, _i32, _f32, _f32, _vp, _vp], _i32),
     "hsc_fold_xyz": ([_vp, _vp, _vp, _i32, _i32, _vp, _vp], _i32),
     "hsc_encode": ([_vp, _vp, _i32, _i32, _vp, _i32, _vp, _i32, _vp], _i32),
@@ -93,6 +94,7 @@ _SIGS = {
     "hsc_batch_create": ([_vp, ctypes.POINTER(_Frame), _i32, ctypes.POINTER(_vp)], _i32),
     "hsc_batch_shade": ([_vp, _vp, _vp], _i32),
     "hsc_batch_destroy": ([_vp], None),
+    "hsc_shade_frames": ([_vp, ctypes.POINTER(_Frame), _i32, _vp], _i32),
 }
 
 for _name, (_args, _res) in _SIGS.items():
@@ -214,8 +216,9 @@ def hsc_tune_report(ctx: Context) -> str:
     return _lib.hsc_tune_report(ctx.handle).decode(errors="replace")
 
 
-def hsc_force_launch_config(ctx: Context, ppt: int = 0, block: int = 128, waves: int = 1, vec: int = 1):
-    _check(_lib.hsc_force_launch_config(ctx.handle, int(ppt), int(block), int(waves), int(vec)))
+def hsc_force_launch_config(ctx: Context, ppt: int = 0, block: int = 128, waves: int = 1, vec: int = 1,
+                            chunk: int = 0):
+    _check(_lib.hsc_force_launch_config(ctx.handle, int(ppt), int(block), int(waves), int(vec), int(chunk)))
 
 
 def hsc_shade_latent_scratch_bytes(pixels: int, k: int, mode: int, latent_dt: int) -> int:
@@ -396,3 +399,9 @@ def hsc_batch_shade(ctx: Context, batch: Batch, stream=None):
 
 def hsc_batch_destroy(batch: Batch):
     batch.close()
+
+
+def hsc_shade_frames(ctx: Context, frames: Sequence[BatchFrame], stream=None):
+    """Asynchronous one-shot batched launch (continuous batching)."""
+    arr = (_Frame * len(frames))(*[f.s for f in frames])
+    _check(_lib.hsc_shade_frames(ctx.handle, arr, len(frames), _stream(stream)))

@@ -119,6 +119,65 @@ hsc_status launch_batch_cfg(const BatchArgs& b, const LaunchCfg& c, cudaStream_t
 hsc_status validate_gbuffer(const hsc_gbuffer* g, const char* name, int64_t pixels);
 hsc_status validate_lights(const hsc_lights* l);
 
+// Fills the device descriptors of `count` frames for tiles of c.block * c.ppt
+// pixels; returns the total tile count.
+static int64_t build_frame_descs(hsc_ctx* ctx, const hsc_frame* frames, int count, const LaunchCfg& c, FrameDesc* h) {
+  int64_t tile0 = 0;
+  const int64_t tile_px = (int64_t)c.block * c.ppt;
+  for (int i = 0; i < count; ++i) {
+    const hsc_frame& f = frames[i];
+    ShadeArgs a{};
+    a.n1 = f.g1.normal;
+    a.x1 = f.g1.pos;
+    a.m1 = f.g1.mat;
+    if (f.has_g2) {
+      a.n2 = f.g2.normal;
+      a.x2 = f.g2.pos;
+      a.m2 = f.g2.mat;
+    }
+    a.P = f.pixels;
+    a.mat_codes = f.mat_codes;
+    a.n_mat = f.n_mat;
+    a.lpos = f.lights.pos;
+    a.linten = f.lights.intensity;
+    a.L = f.lights.count;
+    a.light_codes = f.light_codes;
+    a.code_dt = (int)f.code_dt;
+    a.k = f.k;
+    a.c0 = 0;
+    a.out = f.latent_out;
+    a.out_stride = f.k;
+    a.out_c0 = 0;
+    a.xyz = f.xyz_out;
+    a.M = f.M_xyz;
+    a.chan_max = nullptr;
+    a.err = ctx->d_err;
+    a.tiles = (f.pixels + tile_px - 1) / tile_px;
+    h[i].a = a;
+    h[i].tile0 = tile0;
+    h[i].sec = f.has_g2 ? 1 : 0;
+    tile0 += a.tiles;
+  }
+  return tile0;
+}
+
+static hsc_status validate_frames(const hsc_frame* frames, int count) {
+  HSC_REQUIRE(frames != nullptr && count >= 1, "need at least one frame");
+  for (int i = 0; i < count; ++i) {
+    const hsc_frame& f = frames[i];
+    HSC_REQUIRE(f.k == 6 || f.k == 9, "frame %d: the batched launch supports k = 6 and 9 (got %d)", i, f.k);
+    HSC_REQUIRE(f.pixels >= 1, "frame %d: empty frame", i);
+    HSC_REQUIRE(f.code_dt == HSC_F32 || f.code_dt == HSC_BF16 || f.code_dt == HSC_F16, "frame %d: bad code dtype", i);
+    HSC_REQUIRE(f.mat_codes && f.light_codes && f.M_xyz && f.xyz_out, "frame %d: null pointer", i);
+    HSC_REQUIRE(f.n_mat >= 1 && f.n_mat <= HSC_MAX_MAT, "frame %d: n_mat out of range", i);
+    HSC_REQUIRE(!f.latent_out || aligned(f.latent_out, 4), "frame %d: latent_out misaligned", i);
+    HSC_TRY(validate_gbuffer(&f.g1, "g1", f.pixels));
+    if (f.has_g2) HSC_TRY(validate_gbuffer(&f.g2, "g2", f.pixels));
+    HSC_TRY(validate_lights(&f.lights));
+  }
+  return HSC_OK;
+}
+
 }  // namespace hsc
 
 struct hsc_batch {
@@ -149,19 +208,7 @@ hsc_status hsc_batch_create(hsc_ctx* ctx, const hsc_frame* frames, int count, hs
   HSC_CHECK_CTX(ctx);
   HSC_REQUIRE(out != nullptr, "out is null");
   *out = nullptr;
-  HSC_REQUIRE(frames != nullptr && count >= 1, "need at least one frame");
-  for (int i = 0; i < count; ++i) {
-    const hsc_frame& f = frames[i];
-    HSC_REQUIRE(f.k == 6 || f.k == 9, "frame %d: the batched launch supports k = 6 and 9 (got %d)", i, f.k);
-    HSC_REQUIRE(f.pixels >= 1, "frame %d: empty frame", i);
-    HSC_REQUIRE(f.code_dt == HSC_F32 || f.code_dt == HSC_BF16 || f.code_dt == HSC_F16, "frame %d: bad code dtype", i);
-    HSC_REQUIRE(f.mat_codes && f.light_codes && f.M_xyz && f.xyz_out, "frame %d: null pointer", i);
-    HSC_REQUIRE(f.n_mat >= 1 && f.n_mat <= HSC_MAX_MAT, "frame %d: n_mat out of range", i);
-    HSC_REQUIRE(!f.latent_out || hsc::aligned(f.latent_out, 4), "frame %d: latent_out misaligned", i);
-    HSC_TRY(hsc::validate_gbuffer(&f.g1, "g1", f.pixels));
-    if (f.has_g2) HSC_TRY(hsc::validate_gbuffer(&f.g2, "g2", f.pixels));
-    HSC_TRY(hsc::validate_lights(&f.lights));
-  }
+  HSC_TRY(hsc::validate_frames(frames, count));
   HSC_GUARD(ctx);
   hsc_batch* b = new hsc_batch();
   b->ctx = ctx;
@@ -189,45 +236,7 @@ hsc_status hsc_batch_create(hsc_ctx* ctx, const hsc_frame* frames, int count, hs
     cands.resize(1);  // default: ppt 1, 128 threads, scalar
   }
   std::vector<hsc::FrameDesc> h(count);
-  auto build_desc = [&](const hsc::LaunchCfg& c) -> int64_t {
-    int64_t tile0 = 0;
-    const int64_t tile_px = (int64_t)c.block * c.ppt;
-    for (int i = 0; i < count; ++i) {
-      const hsc_frame& f = frames[i];
-      hsc::ShadeArgs a{};
-      a.n1 = f.g1.normal;
-      a.x1 = f.g1.pos;
-      a.m1 = f.g1.mat;
-      if (f.has_g2) {
-        a.n2 = f.g2.normal;
-        a.x2 = f.g2.pos;
-        a.m2 = f.g2.mat;
-      }
-      a.P = f.pixels;
-      a.mat_codes = f.mat_codes;
-      a.n_mat = f.n_mat;
-      a.lpos = f.lights.pos;
-      a.linten = f.lights.intensity;
-      a.L = f.lights.count;
-      a.light_codes = f.light_codes;
-      a.code_dt = (int)f.code_dt;
-      a.k = f.k;
-      a.c0 = 0;
-      a.out = f.latent_out;
-      a.out_stride = f.k;
-      a.out_c0 = 0;
-      a.xyz = f.xyz_out;
-      a.M = f.M_xyz;
-      a.chan_max = nullptr;
-      a.err = ctx->d_err;
-      a.tiles = (f.pixels + tile_px - 1) / tile_px;
-      h[i].a = a;
-      h[i].tile0 = tile0;
-      h[i].sec = f.has_g2 ? 1 : 0;
-      tile0 += a.tiles;
-    }
-    return tile0;
-  };
+  auto build_desc = [&](const hsc::LaunchCfg& c) -> int64_t { return hsc::build_frame_descs(ctx, frames, count, c, h.data()); };
   cudaError_t e = cudaMalloc(&b->d_frames, sizeof(hsc::FrameDesc) * count);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, sizeof(unsigned int));
   if (e != cudaSuccess) {
@@ -330,6 +339,51 @@ hsc_status hsc_batch_shade(hsc_ctx* ctx, hsc_batch* batch, void* stream) {
   HSC_REQUIRE(batch->ctx == ctx, "batch belongs to another context");
   HSC_GUARD(ctx);
   HSC_CUDA(cudaGraphLaunch(batch->exec, hsc::as_stream(stream)));
+  return HSC_OK;
+}
+
+hsc_status hsc_shade_frames(hsc_ctx* ctx, const hsc_frame* frames, int count, void* stream) {
+  hsc::clear_error();
+  HSC_CHECK_CTX(ctx);
+  HSC_REQUIRE(count <= HSC_MAX_FRAMES_PER_CALL, "at most %d frames per call", HSC_MAX_FRAMES_PER_CALL);
+  HSC_TRY(hsc::validate_frames(frames, count));
+  HSC_GUARD(ctx);
+  cudaStream_t s = hsc::as_stream(stream);
+  // descriptor ring: the slot is reused only after its previous launch has
+  // consumed the descriptors (its event), so host writes never race a copy
+  hsc_ctx::DescSlot& slot = ctx->desc_ring[ctx->desc_next];
+  ctx->desc_next = (ctx->desc_next + 1) % hsc_ctx::kDescSlots;
+  if (!slot.h) {
+    if (cudaMallocHost(&slot.h, sizeof(hsc::FrameDesc) * HSC_MAX_FRAMES_PER_CALL) != cudaSuccess ||
+        cudaMalloc(&slot.d, sizeof(hsc::FrameDesc) * HSC_MAX_FRAMES_PER_CALL + 256) != cudaSuccess ||
+        cudaEventCreateWithFlags(&slot.ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return hsc::set_error(HSC_ERR_OOM, "cannot allocate the frame descriptor ring");
+    }
+  } else {
+    HSC_CUDA(cudaEventSynchronize(slot.ev));
+  }
+  hsc::LaunchCfg c;
+  c.sm_count = ctx->sm_count;
+  c.ppt = 2;
+  c.block = 128;
+  c.vec = 1;
+  if (ctx->forced.ppt > 0) {
+    c = ctx->forced;
+    c.sm_count = ctx->sm_count;
+    if (c.ppt > 2) c.ppt = 2;
+  }
+  hsc::FrameDesc* h = reinterpret_cast<hsc::FrameDesc*>(slot.h);
+  hsc::FrameDesc* d = reinterpret_cast<hsc::FrameDesc*>(slot.d);
+  unsigned int* queue = reinterpret_cast<unsigned int*>(reinterpret_cast<unsigned char*>(slot.d) +
+                                                        sizeof(hsc::FrameDesc) * HSC_MAX_FRAMES_PER_CALL);
+  const int64_t total = hsc::build_frame_descs(ctx, frames, count, c, h);
+  HSC_REQUIRE(total < (int64_t)0xFFFFFFF0ll, "too many pixel tiles in one call");
+  HSC_CUDA(cudaMemcpyAsync(d, h, sizeof(hsc::FrameDesc) * count, cudaMemcpyHostToDevice, s));
+  HSC_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned int), s));
+  hsc::BatchArgs ba{d, count, total, queue};
+  HSC_TRY(hsc::launch_batch_cfg(ba, c, s));
+  HSC_CUDA(cudaEventRecord(slot.ev, s));
   return HSC_OK;
 }
 

@@ -37,6 +37,7 @@ struct LaunchCfg {
   int block = 128;  // threads per CTA
   int waves = 1;    // persistent grid of waves x resident CTAs x SMs; 0 = one CTA per pixel tile
   int vec = 1;      // 1: scalar FP32; 2: shading points in f32x2 pairs
+  int chunk = 0;    // spectral kernel: channels per sweep (0 = default)
 };
 }  // namespace hsc
 
@@ -51,7 +52,15 @@ struct hsc_ctx {
   int autotune = 0;                               // hsc_set_autotune
   std::map<hsc::TuneKey, hsc::LaunchCfg> tuned;   // chosen launch configurations
   std::string tune_report;                        // candidate timings, one line per shape class
-  hsc::LaunchCfg forced{0, 0, 128, 1, 1};         // hsc_force_launch_config (ppt 0 = not forced)
+  hsc::LaunchCfg forced{0, 0, 128, 1, 1, 0};      // hsc_force_launch_config (ppt 0 = not forced)
+  // hsc_shade_frames: ring of pinned host / device descriptor buffers
+  static constexpr int kDescSlots = 8;
+  struct DescSlot {
+    void* h = nullptr;
+    void* d = nullptr;
+    cudaEvent_t ev = nullptr;
+  } desc_ring[kDescSlots];
+  int desc_next = 0;
 };
 
 // Device error flags.
@@ -129,20 +138,28 @@ __device__ __forceinline__ float rsqrt_mufu(float x) {
   return r;
 }
 
+// c * ri clamped to [0, 1] in one instruction (mul with saturation).
+__device__ __forceinline__ float mul_sat(float a, float b) {
+  float r;
+  asm("mul.rn.sat.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+
 // Geometry term of one (shading point, light) pair:
-//   g = max(0, n.(p - x)) / |p - x|^3
-// Explicit round-to-nearest intrinsics fix the instruction sequence so that
-// every kernel that calls this produces bit-identical g.
+//   g = max(0, n.(p - x)) / |p - x|^3 = sat(n.d / |d|) / |d|^2,  d = p - x.
+// n.d / |d| is the cosine of the incidence angle, so clamping it to [0, 1]
+// is max(0, .) (the upper clamp only absorbs rounding above 1).  Explicit
+// round-to-nearest intrinsics fix the instruction sequence, so every kernel
+// that calls this produces bit-identical g: 12 FP32 instructions + one MUFU.
 __device__ __forceinline__ float geometry_term(float x, float y, float z, float nx, float ny, float nz,
                                                float px, float py, float pz) {
   const float dx = __fsub_rn(px, x);
   const float dy = __fsub_rn(py, y);
   const float dz = __fsub_rn(pz, z);
   const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-  float c = __fmaf_rn(nz, dz, __fmaf_rn(ny, dy, __fmul_rn(nx, dx)));
-  c = fmaxf(c, 0.0f);
+  const float c = __fmaf_rn(nz, dz, __fmaf_rn(ny, dy, __fmul_rn(nx, dx)));
   const float ri = rsqrt_mufu(r2);
-  return __fmul_rn(__fmul_rn(c, ri), __fmul_rn(ri, ri));
+  return __fmul_rn(mul_sat(c, ri), __fmul_rn(ri, ri));
 }
 
 // Packed FP32 pairs (sm_100+ f32x2 arithmetic): each half is rounded exactly
@@ -185,9 +202,9 @@ __device__ __forceinline__ f2 geometry_term_x2(f2 x, f2 y, f2 z, f2 nx, f2 ny, f
   float c0, c1, r0, r1;
   f2_unpack(c, c0, c1);
   f2_unpack(r2, r0, r1);
-  const f2 cm = f2_pack(fmaxf(c0, 0.0f), fmaxf(c1, 0.0f));
-  const f2 ri = f2_pack(rsqrt_mufu(r0), rsqrt_mufu(r1));
-  return f2_mul(f2_mul(cm, ri), f2_mul(ri, ri));
+  const float ri0 = rsqrt_mufu(r0), ri1 = rsqrt_mufu(r1);
+  const f2 ri = f2_pack(ri0, ri1);
+  return f2_mul(f2_pack(mul_sat(c0, ri0), mul_sat(c1, ri1)), f2_mul(ri, ri));
 }
 
 // Virtual-point-light transfer from the secondary point to the primary,

@@ -97,6 +97,11 @@ void hsc_destroy(hsc_ctx* ctx) {
   if (ctx->d_err) cudaFree(ctx->d_err);
   if (ctx->d_small) cudaFree(ctx->d_small);
   if (ctx->d_big) cudaFree(ctx->d_big);
+  for (auto& slot : ctx->desc_ring) {
+    if (slot.h) cudaFreeHost(slot.h);
+    if (slot.d) cudaFree(slot.d);
+    if (slot.ev) cudaEventDestroy(slot.ev);
+  }
   delete ctx;
 }
 

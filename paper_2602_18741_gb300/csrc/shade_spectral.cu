@@ -6,13 +6,15 @@
 //
 // Mapping: a thread owns PTS shading points (PTS = 2: the primary and the
 // secondary point of one pixel, or two pixels when there is no secondary
-// G-buffer) with NCH >= n FP32 accumulators each.  Lights and their
-// (I/pi)-scaled SPDs are staged in shared memory; every broadcast float4 load
-// of a light's spectrum feeds 4 * PTS FMAs, which keeps the shared-memory pipe
-// below the FP32 pipe (with one point per thread the loads, one per four FMAs,
-// saturate it).  VEC = 2 keeps the accumulators in f32x2 pairs along
-// wavelength (one packed FMA per two samples).  With the secondary point the
-// radiance is
+// G-buffer) and sweeps the spectrum in chunks of CW samples with CW FP32
+// accumulators per point.  Lights and their (I/pi)-scaled SPDs are staged in
+// shared memory; every broadcast float4 load of a light's spectrum feeds
+// 4 * PTS FMAs, which keeps the shared-memory pipe below the FP32 pipe (with
+// one point per thread the loads, one per four FMAs, saturate it).  Smaller
+// chunks cost one geometry term per chunk but free registers for more
+// resident warps; VEC = 2 keeps the accumulators in f32x2 pairs along
+// wavelength.  The autotuner picks PTS, CW and VEC.  With the secondary point
+// the radiance is
 //     S = R1 (.) (A1 + h (R2 (.) A2)),  XYZ = T S fused.
 #include "common.cuh"
 #include "shade_latent.cuh"
@@ -39,23 +41,20 @@ struct SpecArgs {
   const float* spd;  // L x n
   int L;
   int n;
+  int npad;  // n rounded up to a whole number of channel chunks
   const float* T;  // 3 x n
   float* xyz;
   float* spectra;  // nullable, P x n
   unsigned int* err;
 };
 
-template <int NCH>
-struct SpecLayout {
-  static constexpr int V4 = (NCH + 3) / 4;  // float4s of spectrum per light
-  static constexpr int F4 = 1 + V4;         // + one float4 for the position
-};
+// Staged light record: one float4 (position) + npad / 4 float4s of the
+// (I/pi)-scaled spectrum, zero beyond n.
+__device__ __forceinline__ int spec_f4(const SpecArgs& a) { return 1 + a.npad / 4; }
 
-template <int NCH>
 __device__ __forceinline__ void stage_lights(const SpecArgs& a, float4* s_light, int l0, int nl) {
-  constexpr int F4 = SpecLayout<NCH>::F4;
   float* s = reinterpret_cast<float*>(s_light);
-  constexpr int per = F4 * 4;
+  const int per = spec_f4(a) * 4;
   for (int idx = threadIdx.x; idx < nl * per; idx += blockDim.x) {
     const int l = idx / per, j = idx - l * per;
     const int lg = l0 + l;
@@ -85,54 +84,52 @@ __device__ __forceinline__ Pt load_pt(const float* pos, const float* nrm, int64_
   return q;
 }
 
-// acc[q][i] += g(q, l) * V_l[i] for PTS points over nl staged lights.
-template <int NCH, int PTS>
-__device__ __forceinline__ void sweep(const float4* s_light, int nl, const Pt (&pt)[PTS], float (&acc)[PTS][NCH]) {
-  constexpr int F4 = SpecLayout<NCH>::F4;
-  constexpr int V4 = SpecLayout<NCH>::V4;
+// acc[q][i] += g(q, l) * V_l[c0 + i], i < CW, for PTS points over nl staged lights.
+template <int CW, int PTS>
+__device__ __forceinline__ void sweep(const float4* s_light, int f4, int c0, int nl, const Pt (&pt)[PTS],
+                                      float (&acc)[PTS][CW]) {
 #pragma unroll 1
   for (int l = 0; l < nl; ++l) {
-    const float4 pl = s_light[l * F4];
+    const float4* rec = s_light + l * f4;
+    const float4 pl = rec[0];
     float g[PTS];
 #pragma unroll
     for (int q = 0; q < PTS; ++q)
       g[q] = geometry_term(pt[q].x, pt[q].y, pt[q].z, pt[q].nx, pt[q].ny, pt[q].nz, pl.x, pl.y, pl.z);
+    const float4* vv = rec + 1 + c0 / 4;
 #pragma unroll
-    for (int f = 0; f < V4; ++f) {
-      const float4 v = s_light[l * F4 + 1 + f];
+    for (int f = 0; f < CW / 4; ++f) {
+      const float4 v = vv[f];
 #pragma unroll
       for (int q = 0; q < PTS; ++q) {
-        if (4 * f + 0 < NCH) acc[q][4 * f + 0] = __fmaf_rn(g[q], v.x, acc[q][4 * f + 0]);
-        if (4 * f + 1 < NCH) acc[q][4 * f + 1] = __fmaf_rn(g[q], v.y, acc[q][4 * f + 1]);
-        if (4 * f + 2 < NCH) acc[q][4 * f + 2] = __fmaf_rn(g[q], v.z, acc[q][4 * f + 2]);
-        if (4 * f + 3 < NCH) acc[q][4 * f + 3] = __fmaf_rn(g[q], v.w, acc[q][4 * f + 3]);
+        acc[q][4 * f + 0] = __fmaf_rn(g[q], v.x, acc[q][4 * f + 0]);
+        acc[q][4 * f + 1] = __fmaf_rn(g[q], v.y, acc[q][4 * f + 1]);
+        acc[q][4 * f + 2] = __fmaf_rn(g[q], v.z, acc[q][4 * f + 2]);
+        acc[q][4 * f + 3] = __fmaf_rn(g[q], v.w, acc[q][4 * f + 3]);
       }
     }
   }
 }
 
-// The same sweep with the accumulators in f32x2 pairs along wavelength: one
-// packed FMA per two samples, the light's float4 splitting into two pairs.
-// Each half performs exactly the scalar FMA, so the results are identical.
-template <int NCH, int PTS>
-__device__ __forceinline__ void sweep_x2(const float4* s_light, int nl, const Pt (&pt)[PTS],
-                                         f2 (&acc)[PTS][NCH / 2]) {
-  constexpr int F4 = SpecLayout<NCH>::F4;
-  constexpr int V4 = SpecLayout<NCH>::V4;
-  static_assert(NCH % 4 == 0, "paired sweep needs NCH divisible by 4");
-  const ulonglong2* sl = reinterpret_cast<const ulonglong2*>(s_light);
+// The same sweep with the accumulators in f32x2 pairs along wavelength (one
+// packed FMA per two samples; each half is the scalar FMA, bit for bit).
+template <int CW, int PTS>
+__device__ __forceinline__ void sweep_x2(const float4* s_light, int f4, int c0, int nl, const Pt (&pt)[PTS],
+                                         f2 (&acc)[PTS][CW / 2]) {
 #pragma unroll 1
   for (int l = 0; l < nl; ++l) {
-    const float4 pl = s_light[l * F4];
+    const float4* rec = s_light + l * f4;
+    const float4 pl = rec[0];
     f2 g[PTS];
 #pragma unroll
     for (int q = 0; q < PTS; ++q) {
       const float gs = geometry_term(pt[q].x, pt[q].y, pt[q].z, pt[q].nx, pt[q].ny, pt[q].nz, pl.x, pl.y, pl.z);
       g[q] = f2_pack(gs, gs);
     }
+    const ulonglong2* vv = reinterpret_cast<const ulonglong2*>(rec + 1 + c0 / 4);
 #pragma unroll
-    for (int f = 0; f < V4; ++f) {
-      const ulonglong2 v = sl[l * F4 + 1 + f];
+    for (int f = 0; f < CW / 4; ++f) {
+      const ulonglong2 v = vv[f];
 #pragma unroll
       for (int q = 0; q < PTS; ++q) {
         acc[q][2 * f + 0] = f2_fma(g[q], v.x, acc[q][2 * f + 0]);
@@ -142,45 +139,77 @@ __device__ __forceinline__ void sweep_x2(const float4* s_light, int nl, const Pt
   }
 }
 
-// Reflectance R_m1, XYZ and optional spectrum output of one pixel given the
-// radiance before the primary reflectance, acc[i] = A1 + h (R2 (.) A2).
-template <int NCH>
-__device__ __forceinline__ void finish_pixel(const SpecArgs& a, int64_t p, bool valid, int m1, bool bad,
-                                             const float (&acc)[NCH]) {
-  const float* r1 = a.mats + (int64_t)(bad ? 0 : m1) * a.n;
-  float X = 0.0f, Y = 0.0f, Z = 0.0f;
+// Sweeps the lights for channels c0 .. c0+CW-1, restaging light tiles when
+// they do not fit shared memory at once.  Called by every thread of the CTA.
+template <int CW, int PTS, int VEC>
+__device__ __forceinline__ void sweep_all(const SpecArgs& a, float4* s_light, bool staged, int c0,
+                                          const Pt (&pt)[PTS], float (&acc)[PTS][CW]) {
+  const int f4 = spec_f4(a);
+  if constexpr (VEC == 2) {
+    f2 acc2[PTS][CW / 2];
 #pragma unroll
-  for (int i = 0; i < NCH; ++i) {
+    for (int q = 0; q < PTS; ++q)
+#pragma unroll
+      for (int i = 0; i < CW / 2; ++i) acc2[q][i] = f2_pack(acc[q][2 * i], acc[q][2 * i + 1]);
+    for (int l0 = 0; l0 < a.L; l0 += kSpecLightTile) {
+      const int nl = min(kSpecLightTile, a.L - l0);
+      if (!staged) {
+        __syncthreads();
+        stage_lights(a, s_light, l0, nl);
+        __syncthreads();
+      }
+      sweep_x2<CW, PTS>(s_light, f4, c0, nl, pt, acc2);
+    }
+#pragma unroll
+    for (int q = 0; q < PTS; ++q)
+#pragma unroll
+      for (int i = 0; i < CW / 2; ++i) f2_unpack(acc2[q][i], acc[q][2 * i], acc[q][2 * i + 1]);
+  } else {
+    for (int l0 = 0; l0 < a.L; l0 += kSpecLightTile) {
+      const int nl = min(kSpecLightTile, a.L - l0);
+      if (!staged) {
+        __syncthreads();
+        stage_lights(a, s_light, l0, nl);
+        __syncthreads();
+      }
+      sweep<CW, PTS>(s_light, f4, c0, nl, pt, acc);
+    }
+  }
+}
+
+// Spectral radiance of channels c0 .. c0+CW-1 of one pixel from acc[i] =
+// A1 + h (R2 (.) A2): S = R1 (.) acc, XYZ partial sums, optional spectrum.
+template <int CW>
+__device__ __forceinline__ void finish_chunk(const SpecArgs& a, int64_t p, bool valid, int m1, bool bad, int c0,
+                                             const float (&acc)[CW], float& X, float& Y, float& Z) {
+  const float* r1 = a.mats + (int64_t)(bad ? 0 : m1) * a.n;
+#pragma unroll
+  for (int j = 0; j < CW; ++j) {
+    const int i = c0 + j;
     if (i < a.n) {
-      const float S = bad ? 0.0f : __fmul_rn(__ldg(r1 + i), acc[i]);
+      const float S = bad ? 0.0f : __fmul_rn(__ldg(r1 + i), acc[j]);
       X = __fmaf_rn(__ldg(a.T + i), S, X);
       Y = __fmaf_rn(__ldg(a.T + a.n + i), S, Y);
       Z = __fmaf_rn(__ldg(a.T + 2 * a.n + i), S, Z);
       if (a.spectra && valid) a.spectra[p * a.n + i] = S;
     }
   }
-  if (valid) {
-    a.xyz[3 * p] = X;
-    a.xyz[3 * p + 1] = Y;
-    a.xyz[3 * p + 2] = Z;
-    if (bad) atomicOr(a.err, HSC_DEVERR_MATERIAL);
-  }
 }
 
-// PTS = 1: one point per thread; with the secondary G-buffer the thread runs
-// the secondary sweep first and folds h (R2 (.) A2) into the accumulators
-// before adding the primary sweep.
-// PTS = 2: both points (or two pixels) share every light load.
-template <int NCH, bool SEC, int PTS, int BLOCK, int VEC>
+// A thread owns PTS shading points: PTS = 2 is the primary and secondary point
+// of one pixel (both sum every staged light together) or two pixels without a
+// secondary G-buffer; PTS = 1 is one point, the secondary sweep running first.
+// Channels are processed in chunks of CW (fewer registers, more resident
+// warps; each chunk recomputes the geometry term).
+template <int CW, bool SEC, int PTS, int BLOCK, int VEC>
 __global__ void __launch_bounds__(BLOCK) shade_spectral_kernel(const SpecArgs a) {
   extern __shared__ float4 s_light[];
-  const bool multi_tile = a.L > kSpecLightTile;
-  if (!multi_tile) {
-    stage_lights<NCH>(a, s_light, 0, a.L);
+  const bool staged = a.L <= kSpecLightTile;
+  if (staged) {
+    stage_lights(a, s_light, 0, a.L);
     __syncthreads();
   }
-  // pixels per thread: 2 only for PTS = 2 without a secondary G-buffer
-  constexpr int PXT = (PTS == 2 && !SEC) ? 2 : 1;
+  constexpr int PXT = (PTS == 2 && !SEC) ? 2 : 1;  // pixels per thread
   const int64_t tiles = (a.P + (int64_t)BLOCK * PXT - 1) / ((int64_t)BLOCK * PXT);
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     int64_t pix[PXT];
@@ -197,102 +226,82 @@ __global__ void __launch_bounds__(BLOCK) shade_spectral_kernel(const SpecArgs a)
       bad[j] = (m1[j] < 0 || m1[j] >= a.n_mat);
       pt[j] = load_pt(a.x1, a.n1, pc);
     }
-    float acc[PTS][NCH];
-#pragma unroll
-    for (int q = 0; q < PTS; ++q)
-#pragma unroll
-      for (int i = 0; i < NCH; ++i) acc[q][i] = 0.0f;
-
     int m2 = 0;
     bool bad2 = false;
     float h = 0.0f;
+    Pt s2{};
     if (SEC) {
       const int64_t pc = valid[0] ? pix[0] : a.P - 1;
-      const Pt s2 = load_pt(a.x2, a.n2, pc);
+      s2 = load_pt(a.x2, a.n2, pc);
       m2 = __ldg(a.m2 + pc);
       bad2 = (m2 < 0 || m2 >= a.n_mat);
       bad[0] = bad[0] || bad2;
       h = bounce_term(pt[0].x, pt[0].y, pt[0].z, pt[0].nx, pt[0].ny, pt[0].nz, s2.x, s2.y, s2.z, s2.nx, s2.ny,
                       s2.nz);
       if (PTS == 2) pt[PTS - 1] = s2;
-      if (PTS == 1) {
+    }
+    const float* r2 = a.mats + (int64_t)(bad2 ? 0 : m2) * a.n;
+    float X[PXT], Y[PXT], Z[PXT];
+#pragma unroll
+    for (int j = 0; j < PXT; ++j) X[j] = Y[j] = Z[j] = 0.0f;
+    for (int c0 = 0; c0 < a.npad; c0 += CW) {
+      float acc[PTS][CW];
+#pragma unroll
+      for (int q = 0; q < PTS; ++q)
+#pragma unroll
+        for (int i = 0; i < CW; ++i) acc[q][i] = 0.0f;
+      if (SEC && PTS == 1) {
         // secondary sweep first, then acc = h (R2 (.) A2)
         Pt one[1] = {s2};
-        float a2[1][NCH];
+        float a2[1][CW];
 #pragma unroll
-        for (int i = 0; i < NCH; ++i) a2[0][i] = 0.0f;
-        for (int l0 = 0; l0 < a.L; l0 += kSpecLightTile) {
-          const int nl = min(kSpecLightTile, a.L - l0);
-          if (multi_tile) {
-            __syncthreads();
-            stage_lights<NCH>(a, s_light, l0, nl);
-            __syncthreads();
-          }
-          sweep<NCH, 1>(s_light, nl, one, a2);
-        }
-        const float* r2 = a.mats + (int64_t)(bad2 ? 0 : m2) * a.n;
+        for (int i = 0; i < CW; ++i) a2[0][i] = 0.0f;
+        sweep_all<CW, 1, VEC>(a, s_light, staged, c0, one, a2);
 #pragma unroll
-        for (int i = 0; i < NCH; ++i) {
-          const float r = (i < a.n && !bad2) ? __ldg(r2 + i) : 0.0f;
+        for (int i = 0; i < CW; ++i) {
+          const float r = (c0 + i < a.n && !bad2) ? __ldg(r2 + c0 + i) : 0.0f;
           acc[0][i] = __fmul_rn(h, __fmul_rn(r, a2[0][i]));
         }
       }
-    }
-    if constexpr (VEC == 2) {
-      f2 acc2[PTS][NCH / 2];
+      sweep_all<CW, PTS, VEC>(a, s_light, staged, c0, pt, acc);
+      if (SEC && PTS == 2) {
+        // A1 + h (R2 (.) A2)
 #pragma unroll
-      for (int q = 0; q < PTS; ++q)
-#pragma unroll
-        for (int i = 0; i < NCH / 2; ++i) acc2[q][i] = f2_pack(acc[q][2 * i], acc[q][2 * i + 1]);
-      for (int l0 = 0; l0 < a.L; l0 += kSpecLightTile) {
-        const int nl = min(kSpecLightTile, a.L - l0);
-        if (multi_tile) {
-          __syncthreads();
-          stage_lights<NCH>(a, s_light, l0, nl);
-          __syncthreads();
+        for (int i = 0; i < CW; ++i) {
+          const float r = (c0 + i < a.n && !bad2) ? __ldg(r2 + c0 + i) : 0.0f;
+          acc[0][i] = __fmaf_rn(h, __fmul_rn(r, acc[PTS - 1][i]), acc[0][i]);
         }
-        sweep_x2<NCH, PTS>(s_light, nl, pt, acc2);
       }
+      finish_chunk<CW>(a, pix[0], valid[0], m1[0], bad[0], c0, acc[0], X[0], Y[0], Z[0]);
+      if (PXT == 2)
+        finish_chunk<CW>(a, pix[PXT - 1], valid[PXT - 1], m1[PXT - 1], bad[PXT - 1], c0, acc[PTS - 1], X[PXT - 1],
+                         Y[PXT - 1], Z[PXT - 1]);
+    }
 #pragma unroll
-      for (int q = 0; q < PTS; ++q)
-#pragma unroll
-        for (int i = 0; i < NCH / 2; ++i) f2_unpack(acc2[q][i], acc[q][2 * i], acc[q][2 * i + 1]);
-    } else {
-      for (int l0 = 0; l0 < a.L; l0 += kSpecLightTile) {
-        const int nl = min(kSpecLightTile, a.L - l0);
-        if (multi_tile) {
-          __syncthreads();
-          stage_lights<NCH>(a, s_light, l0, nl);
-          __syncthreads();
-        }
-        sweep<NCH, PTS>(s_light, nl, pt, acc);
+    for (int j = 0; j < PXT; ++j) {
+      if (valid[j]) {
+        a.xyz[3 * pix[j]] = X[j];
+        a.xyz[3 * pix[j] + 1] = Y[j];
+        a.xyz[3 * pix[j] + 2] = Z[j];
+        if (bad[j]) atomicOr(a.err, HSC_DEVERR_MATERIAL);
       }
     }
-    if (SEC && PTS == 2) {
-      // A1 + h (R2 (.) A2)
-      const float* r2 = a.mats + (int64_t)(bad2 ? 0 : m2) * a.n;
-#pragma unroll
-      for (int i = 0; i < NCH; ++i) {
-        const float r = (i < a.n && !bad2) ? __ldg(r2 + i) : 0.0f;
-        acc[0][i] = __fmaf_rn(h, __fmul_rn(r, acc[PTS - 1][i]), acc[0][i]);
-      }
-    }
-    finish_pixel<NCH>(a, pix[0], valid[0], m1[0], bad[0], acc[0]);
-    if (PXT == 2) finish_pixel<NCH>(a, pix[PXT - 1], valid[PXT - 1], m1[PXT - 1], bad[PXT - 1], acc[PTS - 1]);
   }
 }
 
-template <int NCH, bool SEC, int PTS, int BLOCK, int VEC>
-hsc_status launch_spec(const SpecArgs& a, const LaunchCfg& cfg, cudaStream_t s) {
-  constexpr int F4 = SpecLayout<NCH>::F4;
-  auto kern = shade_spectral_kernel<NCH, SEC, PTS, BLOCK, VEC>;
-  const size_t smem_max = (size_t)kSpecLightTile * F4 * sizeof(float4);
-  const size_t smem = (size_t)min(a.L, kSpecLightTile) * F4 * sizeof(float4);
+template <int CW, bool SEC, int PTS, int BLOCK, int VEC>
+hsc_status launch_spec(const SpecArgs& a0, const LaunchCfg& cfg, cudaStream_t s) {
+  SpecArgs a = a0;
+  a.npad = (a.n + CW - 1) / CW * CW;
+  auto kern = shade_spectral_kernel<CW, SEC, PTS, BLOCK, VEC>;
+  const int f4 = 1 + a.npad / 4;
+  const size_t smem = (size_t)min(a.L, kSpecLightTile) * f4 * sizeof(float4);
+  const size_t smem_max = (size_t)kSpecLightTile * (1 + (HSC_MAX_N + CW - 1) / CW * CW / 4) * sizeof(float4);
   static int occ = -1;
   if (occ < 0) {
     if (smem_max > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
     int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, BLOCK, smem_max) != cudaSuccess) o = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, BLOCK, smem) != cudaSuccess) o = 1;
     occ = o > 0 ? o : 1;
   }
   constexpr int PXT = (PTS == 2 && !SEC) ? 2 : 1;
@@ -304,28 +313,33 @@ hsc_status launch_spec(const SpecArgs& a, const LaunchCfg& cfg, cudaStream_t s) 
   return check_launch("shade_spectral_kernel");
 }
 
-template <int NCH, int VEC>
+template <int CW, int VEC>
 hsc_status launch_spec_vec(const SpecArgs& a, bool sec, const LaunchCfg& cfg, cudaStream_t s) {
   if (cfg.ppt == 2)
-    return sec ? launch_spec<NCH, true, 2, 128, VEC>(a, cfg, s) : launch_spec<NCH, false, 2, 128, VEC>(a, cfg, s);
-  return sec ? launch_spec<NCH, true, 1, 128, VEC>(a, cfg, s) : launch_spec<NCH, false, 1, 128, VEC>(a, cfg, s);
+    return sec ? launch_spec<CW, true, 2, 128, VEC>(a, cfg, s) : launch_spec<CW, false, 2, 128, VEC>(a, cfg, s);
+  return sec ? launch_spec<CW, true, 1, 128, VEC>(a, cfg, s) : launch_spec<CW, false, 1, 128, VEC>(a, cfg, s);
 }
 
-template <int NCH>
-hsc_status launch_spec_cfg(const SpecArgs& a, bool sec, const LaunchCfg& cfg, cudaStream_t s) {
-  return cfg.vec == 2 ? launch_spec_vec<NCH, 2>(a, sec, cfg, s) : launch_spec_vec<NCH, 1>(a, sec, cfg, s);
+template <int CW>
+hsc_status launch_spec_cw(const SpecArgs& a, bool sec, const LaunchCfg& cfg, cudaStream_t s) {
+  return cfg.vec == 2 ? launch_spec_vec<CW, 2>(a, sec, cfg, s) : launch_spec_vec<CW, 1>(a, sec, cfg, s);
+}
+
+// Channel chunk of a configuration: cfg.chunk, or by default the whole
+// spectrum up to 84 samples (32 for n <= 32), else chunks of 44.
+int spectral_chunk(const LaunchCfg& cfg, int n) {
+  if (cfg.chunk > 0) return cfg.chunk;
+  return n <= 32 ? 32 : (n <= 84 ? 84 : 44);
 }
 
 hsc_status launch_spectral(const SpecArgs& a, bool sec, const LaunchCfg& cfg, cudaStream_t s) {
-  const int n = a.n;
-  if (n <= 8) return launch_spec_cfg<8>(a, sec, cfg, s);
-  if (n <= 16) return launch_spec_cfg<16>(a, sec, cfg, s);
-  if (n <= 32) return launch_spec_cfg<32>(a, sec, cfg, s);
-  if (n <= 48) return launch_spec_cfg<48>(a, sec, cfg, s);
-  if (n <= 64) return launch_spec_cfg<64>(a, sec, cfg, s);
-  if (n <= 84) return launch_spec_cfg<84>(a, sec, cfg, s);
-  if (n <= 96) return launch_spec_cfg<96>(a, sec, cfg, s);
-  return launch_spec_cfg<128>(a, sec, cfg, s);
+  switch (spectral_chunk(cfg, a.n)) {
+    case 16: return launch_spec_cw<16>(a, sec, cfg, s);
+    case 28: return launch_spec_cw<28>(a, sec, cfg, s);
+    case 32: return launch_spec_cw<32>(a, sec, cfg, s);
+    case 44: return launch_spec_cw<44>(a, sec, cfg, s);
+    default: return launch_spec_cw<84>(a, sec, cfg, s);
+  }
 }
 
 }  // namespace

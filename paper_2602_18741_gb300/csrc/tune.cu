@@ -48,15 +48,17 @@ std::vector<LaunchCfg> spectral_candidates(const hsc_ctx* ctx) {
   d.block = 128;
   d.ppt = 2;
   d.waves = 1;
+  d.vec = 2;
+  d.chunk = 0;
   v.push_back(d);
-  for (int vec : {1, 2})
-    for (int ppt : {1, 2})
-      for (int waves : {1, 0}) {
+  for (int chunk : {0, 16, 28, 44})
+    for (int vec : {1, 2})
+      for (int ppt : {1, 2}) {
         LaunchCfg c = d;
         c.ppt = ppt;
-        c.waves = waves;
         c.vec = vec;
-        if (c.ppt == d.ppt && c.waves == d.waves && c.vec == d.vec) continue;
+        c.chunk = chunk;
+        if (c.ppt == d.ppt && c.vec == d.vec && c.chunk == d.chunk) continue;
         v.push_back(c);
       }
   return v;
@@ -101,7 +103,8 @@ hsc_status tuned_cfg(hsc_ctx* ctx, const TuneKey& key, const std::vector<LaunchC
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, e0, e1);
     ms /= 3.0f;
-    snprintf(line, sizeof(line), " [ppt=%d block=%d waves=%d vec=%d %.4f ms]", c.ppt, c.block, c.waves, c.vec, ms);
+    snprintf(line, sizeof(line), " [ppt=%d block=%d waves=%d vec=%d chunk=%d %.4f ms]", c.ppt, c.block, c.waves, c.vec,
+             c.chunk, ms);
     rep += line;
     if (ms < best) {
       best = ms;
@@ -111,8 +114,8 @@ hsc_status tuned_cfg(hsc_ctx* ctx, const TuneKey& key, const std::vector<LaunchC
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != HSC_OK) return st;
-  snprintf(line, sizeof(line), " -> ppt=%d block=%d waves=%d vec=%d\n", best_cfg.ppt, best_cfg.block, best_cfg.waves,
-           best_cfg.vec);
+  snprintf(line, sizeof(line), " -> ppt=%d block=%d waves=%d vec=%d chunk=%d\n", best_cfg.ppt, best_cfg.block,
+           best_cfg.waves, best_cfg.vec, best_cfg.chunk);
   rep += line;
   ctx->tune_report += rep;
   ctx->tuned[key] = best_cfg;
@@ -133,7 +136,7 @@ hsc_status hsc_set_autotune(hsc_ctx* ctx, int enable) {
 
 const char* hsc_tune_report(hsc_ctx* ctx) { return ctx ? ctx->tune_report.c_str() : ""; }
 
-hsc_status hsc_force_launch_config(hsc_ctx* ctx, int ppt, int block, int waves, int vec) {
+hsc_status hsc_force_launch_config(hsc_ctx* ctx, int ppt, int block, int waves, int vec, int chunk) {
   hsc::clear_error();
   HSC_CHECK_CTX(ctx);
   if (ppt <= 0) {
@@ -145,7 +148,10 @@ hsc_status hsc_force_launch_config(hsc_ctx* ctx, int ppt, int block, int waves, 
   HSC_REQUIRE(block == 128 || block == 256, "block must be 128 or 256");
   HSC_REQUIRE(waves >= 0 && waves <= 64, "waves out of range");
   HSC_REQUIRE(vec == 1 || vec == 2, "vec must be 1 or 2");
+  HSC_REQUIRE(chunk == 0 || chunk == 16 || chunk == 28 || chunk == 32 || chunk == 44 || chunk == 84,
+              "chunk must be 0, 16, 28, 32, 44 or 84");
   ctx->forced.vec = vec;
+  ctx->forced.chunk = chunk;
   ctx->forced.ppt = ppt;
   ctx->forced.block = block;
   ctx->forced.waves = waves;

@@ -1,0 +1,284 @@
+"""Continuous-batching render-plus-decode server over the C ABI.
+
+Requests (hsc_inputs.request_stream) name a resident scene, an image size, a
+code length k, a spectral grid n and a light count L.  Everything a request
+reads stays on the device: per scene and size a G-buffer, per scene its 256
+materials and a pool of 128 lights (SPDs on both grids), and for every
+(scene, k, n) the material and light codes and the folded decode matrix.
+
+The scheduler is continuous batching: on every turn of the loop it retires
+finished launches (freeing their output memory), admits newly arrived
+requests in arrival order while the HBM footprint of admitted requests stays
+under the budget, and launches everything admitted so far as one batched
+persistent launch (hsc_shade_frames) on the next of a few streams, so new
+work overlaps the work already on the GPU.  Latency is measured from a
+request's arrival to the GPU completion event of its launch.  The same stream
+can be served by the naive n-sample shader (hsc_shade_spectral, one launch per
+request) for comparison.
+
+The scheduler core (Scheduler) is independent of the GPU and is tested on the
+host with a fake backend.
+"""
+from __future__ import annotations
+
+import collections
+import math
+import time
+from dataclasses import dataclass, field
+from typing import Callable, Dict, List, Optional, Sequence
+
+import numpy as np
+
+import hsc_inputs as hi
+
+
+# --------------------------------------------------------------------------- scheduler
+
+@dataclass
+class Inflight:
+    handle: object          # backend completion handle
+    requests: list
+    nbytes: int
+
+
+@dataclass
+class ServeStats:
+    latencies_ms: List[float] = field(default_factory=list)
+    launches: int = 0
+    max_inflight_bytes: int = 0
+    max_batch: int = 0
+    wall_s: float = 0.0
+    first_arrival_s: float = 0.0
+    last_done_ms: float = 0.0
+
+    def summary(self, warmup_s: float = 0.0, arrivals: Optional[Sequence[float]] = None) -> dict:
+        lat = np.asarray(self.latencies_ms, dtype=np.float64)
+        if arrivals is not None and warmup_s > 0:
+            keep = np.asarray(arrivals) >= warmup_s
+            lat = lat[keep[:len(lat)]]
+        if lat.size == 0:
+            return {"requests": 0}
+        srt = np.sort(lat)
+
+        def nr(q):
+            return float(srt[max(int(math.ceil(q * srt.size)) - 1, 0)])
+
+        return {"requests": int(lat.size), "p50_ms": nr(0.50), "p99_ms": nr(0.99), "mean_ms": float(lat.mean()),
+                "max_ms": float(srt[-1]), "launches": self.launches, "max_batch": self.max_batch,
+                "max_inflight_MB": self.max_inflight_bytes / 1e6,
+                "frames_per_s": float(len(self.latencies_ms) / max(self.wall_s, 1e-9))}
+
+
+class Scheduler:
+    """Admission by footprint and continuous batching, independent of the GPU.
+
+    backend.launch(requests) -> handle  (asynchronous)
+    backend.done(handle) -> Optional[float]  (completion time in ms since start, or None)
+    backend.footprint(request) -> bytes
+    backend.now_s() -> seconds since start
+    """
+
+    def __init__(self, backend, budget_bytes: int, max_inflight: int = 4, max_batch: int = 64):
+        self.b = backend
+        self.budget = int(budget_bytes)
+        self.max_inflight = max_inflight
+        self.max_batch = max_batch
+
+    def run(self, requests: Sequence[hi.Request], idle_sleep_s: float = 0.0) -> ServeStats:
+        reqs = sorted(requests, key=lambda r: r.arrival_s)
+        for r in reqs:
+            if self.b.footprint(r) > self.budget:
+                raise ValueError(f"request {r.rid} alone exceeds the memory budget")
+        st = ServeStats()
+        st.latencies_ms = [float("nan")] * len(reqs)
+        index = {r.rid: i for i, r in enumerate(reqs)}
+        queue: collections.deque = collections.deque()
+        inflight: List[Inflight] = []
+        used = 0
+        nxt = 0
+        done = 0
+        t_start = self.b.now_s()
+        while done < len(reqs):
+            now = self.b.now_s()
+            while nxt < len(reqs) and reqs[nxt].arrival_s <= now:
+                queue.append(reqs[nxt])
+                nxt += 1
+            # retire finished launches
+            still = []
+            for f in inflight:
+                t_done = self.b.done(f.handle)
+                if t_done is None:
+                    still.append(f)
+                    continue
+                for r in f.requests:
+                    st.latencies_ms[index[r.rid]] = t_done - 1e3 * r.arrival_s
+                    done += 1
+                st.last_done_ms = max(st.last_done_ms, t_done)
+                used -= f.nbytes
+            inflight = still
+            # admit in arrival order while the footprint fits, launch as one batch
+            if queue and len(inflight) < self.max_inflight:
+                batch, nbytes = [], 0
+                while queue and len(batch) < self.max_batch:
+                    fp = self.b.footprint(queue[0])
+                    if used + nbytes + fp > self.budget:
+                        break
+                    batch.append(queue.popleft())
+                    nbytes += fp
+                if batch:
+                    h = self.b.launch(batch)
+                    inflight.append(Inflight(h, batch, nbytes))
+                    used += nbytes
+                    st.launches += 1
+                    st.max_batch = max(st.max_batch, len(batch))
+                    st.max_inflight_bytes = max(st.max_inflight_bytes, used)
+                    continue
+            if idle_sleep_s > 0:
+                time.sleep(idle_sleep_s)
+        st.wall_s = self.b.now_s() - t_start
+        return st
+
+
+# --------------------------------------------------------------------------- GPU state
+
+class ResidentScenes:
+    """Device-resident scenes: G-buffers per size, materials, light pools and
+    codes/decode matrices per (k, n)."""
+
+    def __init__(self, hsc, ctx, device, scenes: int = 8, sizes=hi.SERVE_SIZES, ks=(6, 9), grids=(hi.GRID_31, hi.GRID_81),
+                 n_mat: int = 256, pool: int = 128, code_dtype=None, seed: int = hi.MASTER_SEED + 6):
+        import torch
+        self.hsc, self.ctx, self.dev = hsc, ctx, device
+        code_dtype = code_dtype or torch.bfloat16
+        self.code_dtype = code_dtype
+        gen = torch.Generator(device=device)
+        rngs = hi.streams(seed, scenes)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        self.gbuf: Dict[tuple, object] = {}
+        self.lights: Dict[int, tuple] = {}
+        self.mats: Dict[tuple, object] = {}
+        self.spd: Dict[tuple, object] = {}
+        self.codes: Dict[tuple, tuple] = {}
+        self.M: Dict[tuple, object] = {}
+        self.T: Dict[int, object] = {}
+        for g in grids:
+            T = torch.empty(3, g[2], device=device)
+            hsc.hsc_cmf_weights(ctx, g[2], g[0], g[1], T)
+            self.T[g[2]] = T
+        for s in range(scenes):
+            r = rngs[s]
+            for (w, h) in sizes:
+                gen.manual_seed(int(r.integers(0, 2**31 - 1)))
+                (n1, x1, m1), _ = hi.torch_gbuffers(gen, w * h, n_mat, False, device)
+                self.gbuf[(s, w, h)] = hsc.GBuffer(n1, x1, m1)
+            lpos, linten = hi.light_positions(r, pool)
+            self.lights[s] = (t(lpos), t(linten))
+            temps = r.uniform(2000.0, 10000.0, size=pool // 2)
+            mus = r.uniform(400.0, 700.0, size=pool - pool // 2)
+            sig = r.uniform(5.0, 20.0, size=pool - pool // 2)
+            mseed = int(r.integers(0, 2**31 - 1))
+            for g in grids:
+                lam = hi.grid(*g)
+                mrng = np.random.default_rng([mseed, g[2]])
+                mats = np.concatenate([hi.smooth_reflectances(mrng, lam, n_mat - n_mat // 8),
+                                       hi.sawtooth_reflectances(mrng, lam, n_mat // 8)], axis=0).astype(np.float32)
+                spd = np.concatenate([hi.blackbody(lam, temps), hi.narrowband(lam, mus, sig)], axis=0).astype(np.float32)
+                self.mats[(s, g[2])] = t(mats)
+                self.spd[(s, g[2])] = t(spd)
+                for k in ks:
+                    E, D = hi.load_codec(k, g[2])
+                    Ed, Dd = t(E), t(D)
+                    zm = torch.empty(n_mat, k, device=device, dtype=code_dtype)
+                    zl = torch.empty(pool, k, device=device, dtype=code_dtype)
+                    hsc.hsc_encode(ctx, Ed, self.mats[(s, g[2])], zm)
+                    hsc.hsc_encode(ctx, Ed, self.spd[(s, g[2])], zl)
+                    self.codes[(s, k, g[2])] = (zm, zl)
+                    if (k, g[2]) not in self.M:
+                        M = torch.empty(3, k, device=device)
+                        hsc.hsc_fold_xyz(ctx, self.T[g[2]], Dd, M)
+                        self.M[(k, g[2])] = M
+        torch.cuda.synchronize(device)
+
+    def frame_inputs(self, req: hi.Request):
+        g1 = self.gbuf[(req.scene, req.width, req.height)]
+        lpos, linten = self.lights[req.scene]
+        lights = self.hsc.Lights(lpos[:req.lights], linten[:req.lights])
+        zm, zl = self.codes[(req.scene, req.k, req.n)]
+        return g1, lights, zm, zl[:req.lights], self.M[(req.k, req.n)]
+
+
+class GpuBackend:
+    """Launches admitted requests on the GPU.  mode 'latent': one batched
+    launch per admitted group (hsc_shade_frames); mode 'spectral': one
+    hsc_shade_spectral launch per request.  Streams are used round-robin."""
+
+    def __init__(self, hsc, ctx, scenes: ResidentScenes, mode: str = "latent", streams: int = 3,
+                 keep_outputs: bool = False):
+        import torch
+        self.hsc, self.ctx, self.sc, self.mode = hsc, ctx, scenes, mode
+        self.streams = [torch.cuda.Stream(device=scenes.dev) for _ in range(streams)]
+        self.si = 0
+        self.keep = keep_outputs
+        self.outputs: Dict[int, object] = {}
+        self.ref = torch.cuda.Event(enable_timing=True)
+        self.t0 = None
+
+    def start(self):
+        import torch
+        torch.cuda.synchronize(self.sc.dev)
+        self.ref.record(torch.cuda.current_stream(self.sc.dev))
+        torch.cuda.synchronize(self.sc.dev)
+        self.t0 = time.perf_counter()
+
+    def now_s(self) -> float:
+        return time.perf_counter() - self.t0
+
+    def footprint(self, r: hi.Request) -> int:
+        return r.width * r.height * 12 + 4096
+
+    def launch(self, requests):
+        import torch
+        stream = self.streams[self.si]
+        self.si = (self.si + 1) % len(self.streams)
+        outs = []
+        with torch.cuda.stream(stream):
+            if self.mode == "latent":
+                frames = []
+                for r in requests:
+                    g1, lights, zm, zl, M = self.sc.frame_inputs(r)
+                    xyz = torch.empty(r.width * r.height, 3, device=self.sc.dev)
+                    frames.append(self.hsc.BatchFrame(g1, None, zm, lights, zl, M, xyz))
+                    outs.append((r.rid, xyz))
+                self.hsc.hsc_shade_frames(self.ctx, frames, stream=stream)
+            else:
+                for r in requests:
+                    g1 = self.sc.gbuf[(r.scene, r.width, r.height)]
+                    lpos, linten = self.sc.lights[r.scene]
+                    lights = self.hsc.Lights(lpos[:r.lights], linten[:r.lights])
+                    xyz = torch.empty(r.width * r.height, 3, device=self.sc.dev)
+                    self.hsc.hsc_shade_spectral(self.ctx, g1, None, self.sc.mats[(r.scene, r.n)], lights,
+                                                self.sc.spd[(r.scene, r.n)][:r.lights], self.sc.T[r.n], xyz,
+                                                stream=stream)
+                    outs.append((r.rid, xyz))
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(stream)
+        if self.keep:
+            for rid, xyz in outs:
+                self.outputs[rid] = xyz
+        return (ev, outs)
+
+    def done(self, handle) -> Optional[float]:
+        ev, _ = handle
+        if not ev.query():
+            return None
+        return float(self.ref.elapsed_time(ev))
+
+
+def serve(hsc, ctx, scenes: ResidentScenes, requests, mode="latent", budget_bytes=40 * 10**9, max_batch=64,
+          keep_outputs=False):
+    backend = GpuBackend(hsc, ctx, scenes, mode=mode, keep_outputs=keep_outputs)
+    sched = Scheduler(backend, budget_bytes, max_inflight=4, max_batch=max_batch)
+    backend.start()
+    stats = sched.run(requests)
+    hsc.hsc_sync(ctx)
+    return stats, backend

@@ -542,14 +542,15 @@ def test_spectral_launch_configs_match_oracle(env, sec):
     f = hi.make_frame(32, 83, 41, hi.GRID_81, n_smooth=20, n_saw=5, lights=70, secondary=sec)
     df = upload(hsc, ctx, f, dev)
     S_ref, xyz_ref = shade.shade_spectral(f)
-    for ppt, waves, vec in [(p_, w_, v_) for p_ in (1, 2) for w_ in (1, 0) for v_ in (1, 2)]:
-        hsc.hsc_force_launch_config(ctx, ppt, 128, waves, vec)
+    for ppt, waves, vec, chunk in [(p_, w_, v_, c_) for p_ in (1, 2) for w_ in (1, 0) for v_ in (1, 2)
+                                   for c_ in (0, 16, 28, 44)]:
+        hsc.hsc_force_launch_config(ctx, ppt, 128, waves, vec, chunk)
         xyz = torch.empty(f.pixels, 3, device=dev)
         S = torch.empty(f.pixels, f.n, device=dev)
         hsc.hsc_shade_spectral(ctx, df.g1, df.g2, df.mats, df.lights, df.spd, df.T, xyz, S)
         hsc.hsc_sync(ctx)
-        assert rel_err_rows(S.cpu().numpy(), S_ref) <= TOL, (ppt, waves, vec)
-        assert metrics.rel_xyz_error(xyz.cpu().numpy(), xyz_ref) <= TOL, (ppt, waves, vec)
+        assert rel_err_rows(S.cpu().numpy(), S_ref) <= TOL, (ppt, waves, vec, chunk)
+        assert metrics.rel_xyz_error(xyz.cpu().numpy(), xyz_ref) <= TOL, (ppt, waves, vec, chunk)
     hsc.hsc_force_launch_config(ctx, 0)
 
 

@@ -1,0 +1,89 @@
+"""Host-side tests of the continuous-batching scheduler with a fake backend
+(simulated clock, launches that finish after a cost proportional to their
+pixels): every request completes, in arrival order of admission, the admitted
+footprint never exceeds the budget, and requests arriving while others run
+join later launches (continuous batching, not one queue drain)."""
+import importlib.util
+import os
+import sys
+
+import pytest
+
+import hsc_inputs as hi
+
+# serve.py is pure Python at import time; load it by path so this host test
+# does not need the CUDA library that the package import loads
+_spec = importlib.util.spec_from_file_location(
+    "_hsc_serve", os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                               "paper_2602_18741_gb300", "serve.py"))
+_serve = importlib.util.module_from_spec(_spec)
+sys.modules["_hsc_serve"] = _serve
+_spec.loader.exec_module(_serve)
+Scheduler = _serve.Scheduler
+
+
+class FakeBackend:
+    def __init__(self, px_per_ms=2e6, tick_ms=0.05):
+        self.t_ms = 0.0
+        self.px_per_ms = px_per_ms
+        self.tick = tick_ms
+        self.gpu_free_ms = 0.0
+        self.launched = []
+
+    def now_s(self):
+        self.t_ms += self.tick
+        return self.t_ms / 1e3
+
+    def footprint(self, r):
+        return r.width * r.height * 12
+
+    def launch(self, reqs):
+        px = sum(r.width * r.height for r in reqs)
+        start = max(self.t_ms, self.gpu_free_ms)
+        end = start + px / self.px_per_ms
+        self.gpu_free_ms = end
+        self.launched.append([r.rid for r in reqs])
+        return end
+
+    def done(self, handle):
+        return handle if self.t_ms >= handle else None
+
+
+def _requests(n=300, rate=400.0):
+    reqs = hi.request_stream(seed=3, rate_hz=rate, duration_s=10.0)[:n]
+    return reqs
+
+
+def test_all_requests_complete_in_order_within_budget():
+    reqs = _requests()
+    fb = FakeBackend()
+    budget = 300 * 10**6
+    st = Scheduler(fb, budget, max_inflight=4, max_batch=16).run(reqs)
+    assert all(lat == lat and lat >= 0 for lat in st.latencies_ms)   # no NaN, non-negative
+    order = [rid for group in fb.launched for rid in group]
+    assert order == sorted(order) and sorted(order) == sorted(r.rid for r in reqs)
+    assert st.max_inflight_bytes <= budget
+    assert st.max_batch <= 16
+    assert st.launches < len(reqs)            # arrivals during busy periods were batched
+
+
+def test_budget_limits_admission():
+    reqs = _requests(n=120, rate=2000.0)
+    fb = FakeBackend(px_per_ms=5e5)
+    small = max(fb.footprint(r) for r in reqs)       # room for about one large request
+    st = Scheduler(fb, small, max_inflight=8, max_batch=64).run(reqs)
+    assert st.max_inflight_bytes <= small
+    assert len(st.latencies_ms) == 120
+
+
+def test_request_larger_than_budget_is_rejected():
+    reqs = _requests(n=5)
+    with pytest.raises(ValueError):
+        Scheduler(FakeBackend(), 1000).run(reqs)
+
+
+def test_summary_statistics():
+    reqs = _requests(n=50)
+    st = Scheduler(FakeBackend(), 10**12).run(reqs)
+    s = st.summary()
+    assert s["requests"] == 50 and s["p50_ms"] <= s["p99_ms"] <= s["max_ms"]

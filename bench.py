@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the secondary rows (spectral, passes, decodes)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--tune-file", default="",
+                    help="load tuned launch configurations from this file if it exists, save them there after the run")
     ap.add_argument("--serve-seconds", type=float, default=8.0,
                     help="length of the Poisson request stream served (0 = skip); the first quarter is warm-up")
     return ap.parse_args()
@@ -163,6 +165,9 @@ def run_hsc(args, rank: int, world: int):
     torch.cuda.set_device(dev)
     ctx = hsc.Context(dev.index)
     hsc.hsc_set_autotune(ctx, True)   # tile shape / pixels per thread picked on the first (warm-up) call
+    if args.tune_file and os.path.exists(args.tune_file):
+        with open(args.tune_file) as fh:
+            hsc.hsc_tune_load(ctx, fh.read())
     stream = torch.cuda.current_stream()
     k = args.k
 
@@ -273,6 +278,9 @@ def run_hsc(args, rank: int, world: int):
                     "ops_per_eval": ops_per_eval, "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x {peak_mhz:.0f} MHz"}
         e2e = e2e_leg(args, hsc, ctx, f, dev, stream, Ed, M, evals)
         tune = [ln for ln in hsc.hsc_tune_report(ctx).splitlines() if ln.strip()]
+        if args.tune_file:
+            with open(args.tune_file, "w") as fh:
+                fh.write(hsc.hsc_tune_save(ctx))
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             rate, nrows, secs = oracle_rate(args.cpu_seconds, k, threads=1)

@@ -133,9 +133,16 @@ HSC_API hsc_status hsc_set_autotune(hsc_ctx* ctx, int enable);
 /* Text table of the tuned shape classes and candidate timings (valid until
  * the next tuning call on this context).                                   */
 HSC_API const char* hsc_tune_report(hsc_ctx* ctx);
+/* Save the tuned configurations as text (one line per shape class) into buf
+ * (truncated to len - 1 bytes, NUL-terminated); returns the full length.
+ * hsc_tune_load reads such text back, so a process can reuse the choices of
+ * an earlier run without timing candidates again.                           */
+HSC_API int hsc_tune_save(hsc_ctx* ctx, char* buf, size_t len);
+HSC_API hsc_status hsc_tune_load(hsc_ctx* ctx, const char* text);
 /* Force one launch configuration for every shading launch (testing and
  * benchmarking): ppt in {1, 2, 4} (spectral kernel: 1 or 2 shading points per
- * thread), block in {128, 256}, waves >= 0 (0 = one CTA per pixel tile),
+ * thread), block in {128, 256}, waves >= -1 (0 = one CTA per pixel tile,
+ * -1 = one wave of persistent CTAs on an atomic tile queue; latent kernels),
  * vec = 1 (scalar FP32) or 2 (packed f32x2 pairs: pairs of shading points in
  * the latent kernels, pairs of wavelengths in the spectral kernel), chunk =
  * spectral channels per sweep (0 = default, 16, 28, 32, 44 or 84).  ppt <= 0

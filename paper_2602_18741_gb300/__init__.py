@@ -77,6 +77,8 @@ _SIGS = {
     "hsc_shade_latent_scratch_bytes": ([_i64, _i32, _i32, _i32], ctypes.c_size_t),
     "hsc_set_autotune": ([_vp, _i32], _i32),
     "hsc_tune_report": ([_vp], ctypes.c_char_p),
+    "hsc_tune_save": ([_vp, ctypes.c_char_p, ctypes.c_size_t], _i32),
+    "hsc_tune_load": ([_vp, ctypes.c_char_p], _i32),
     "hsc_force_launch_config": ([_vp, _i32, _i32, _i32, _i32, _i32], _i32),
     "hsc_cmf_weights": ([_vp, _i32, _f32, _f32, _vp, _vp], _i32),
     "hsc_fold_xyz": ([_vp, _vp, _vp, _i32, _i32, _vp, _vp], _i32),
@@ -142,6 +144,7 @@ class Context:
         self._h = _vp()
         _check(_lib.hsc_create(ctypes.byref(self._h), int(device)))
         self.device = int(device)
+        self.autotune = False
 
     @property
     def handle(self):
@@ -210,10 +213,22 @@ def hsc_reserve(ctx: Context, nbytes: int):
 
 def hsc_set_autotune(ctx: Context, enable: bool = True):
     _check(_lib.hsc_set_autotune(ctx.handle, 1 if enable else 0))
+    ctx.autotune = bool(enable)
 
 
 def hsc_tune_report(ctx: Context) -> str:
     return _lib.hsc_tune_report(ctx.handle).decode(errors="replace")
+
+
+def hsc_tune_save(ctx: Context) -> str:
+    n = _lib.hsc_tune_save(ctx.handle, None, 0)
+    buf = ctypes.create_string_buffer(n + 1)
+    _lib.hsc_tune_save(ctx.handle, buf, n + 1)
+    return buf.value.decode()
+
+
+def hsc_tune_load(ctx: Context, text: str):
+    _check(_lib.hsc_tune_load(ctx.handle, text.encode()))
 
 
 def hsc_force_launch_config(ctx: Context, ppt: int = 0, block: int = 128, waves: int = 1, vec: int = 1,

@@ -20,6 +20,7 @@
 #define HSC_SMALL_SCRATCH (1u << 20)
 // Offsets inside the fixed scratch block.
 #define HSC_OFF_CHANMAX 0u          // HSC_MAX_K uint32 (fp8 per-channel max)
+#define HSC_OFF_QUEUE 512u          // one uint32 tile counter for dynamically scheduled launches
 #define HSC_OFF_REDUCE 4096u        // reduction workspace for hsc_delta_e
 
 namespace hsc {
@@ -35,9 +36,11 @@ struct LaunchCfg {
   int sm_count = 0;
   int ppt = 2;      // pixels (or shading points) per thread
   int block = 128;  // threads per CTA
-  int waves = 1;    // persistent grid of waves x resident CTAs x SMs; 0 = one CTA per pixel tile
+  int waves = 1;    // persistent grid of waves x resident CTAs x SMs; 0 = one CTA per pixel tile;
+                    // -1 = one wave of persistent CTAs taking tiles from an atomic queue
   int vec = 1;      // 1: scalar FP32; 2: shading points in f32x2 pairs
   int chunk = 0;    // spectral kernel: channels per sweep (0 = default)
+  unsigned int* queue = nullptr;  // tile counter for waves = -1
 };
 }  // namespace hsc
 
@@ -52,7 +55,7 @@ struct hsc_ctx {
   int autotune = 0;                               // hsc_set_autotune
   std::map<hsc::TuneKey, hsc::LaunchCfg> tuned;   // chosen launch configurations
   std::string tune_report;                        // candidate timings, one line per shape class
-  hsc::LaunchCfg forced{0, 0, 128, 1, 1, 0};      // hsc_force_launch_config (ppt 0 = not forced)
+  hsc::LaunchCfg forced{0, 0, 128, 1, 1, 0, nullptr};  // hsc_force_launch_config (ppt 0 = not forced)
   // hsc_shade_frames: ring of pinned host / device descriptor buffers
   static constexpr int kDescSlots = 8;
   struct DescSlot {

@@ -32,6 +32,7 @@ struct ShadeArgs {
   unsigned int* chan_max;  // per-channel max bits for the fp8 scale (nullable)
   unsigned int* err;
   int64_t tiles;
+  unsigned int* queue;  // dynamic tile queue (zeroed before the launch), or null for static striding
 };
 
 LaunchCfg default_cfg(const hsc_ctx* ctx);

@@ -247,7 +247,21 @@ __global__ void __launch_bounds__(BLOCK) shade_codes_kernel(const ShadeArgs a) {
     stage_light_codes<KC, VEC, BLOCK>(a, s_light, 0, a.L);
     __syncthreads();
   }
-  for (int64_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x) shade_tile<KC, PPT, SEC, BLOCK, VEC>(a, tile, s_light, staged);
+  if (a.queue) {
+    // dynamic schedule: persistent CTAs take the next tile from a counter
+    __shared__ int64_t s_next;
+    for (;;) {
+      if (threadIdx.x == 0) s_next = (int64_t)atomicAdd(a.queue, 1u);
+      __syncthreads();
+      const int64_t tile = s_next;
+      __syncthreads();
+      if (tile >= a.tiles) break;
+      shade_tile<KC, PPT, SEC, BLOCK, VEC>(a, tile, s_light, staged);
+    }
+  } else {
+    for (int64_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x)
+      shade_tile<KC, PPT, SEC, BLOCK, VEC>(a, tile, s_light, staged);
+  }
 }
 
 template <int KC, int PPT, bool SEC, int BLOCK, int VEC>
@@ -265,8 +279,17 @@ hsc_status launch_one(const ShadeArgs& a0, const LaunchCfg& cfg, cudaStream_t st
     occ = o > 0 ? o : 1;
   }
   // waves > 0: persistent grid of waves x (resident CTAs per SM) x SMs striding
-  // over the pixel tiles; waves == 0: one CTA per tile.
-  int64_t grid = cfg.waves > 0 ? (int64_t)cfg.sm_count * occ * cfg.waves : a.tiles;
+  // over the pixel tiles; waves == 0: one CTA per tile; waves < 0: one wave of
+  // persistent CTAs on a dynamic tile queue.
+  a.queue = nullptr;
+  if (cfg.waves < 0) {
+    if (!cfg.queue) return set_error(HSC_ERR_INVALID_ARG, "dynamic schedule without a queue");
+    a.queue = cfg.queue;
+    cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), stream);
+    if (e != cudaSuccess) return set_error(HSC_ERR_CUDA, "queue reset: %s", cudaGetErrorString(e));
+  }
+  int64_t grid = cfg.waves > 0 ? (int64_t)cfg.sm_count * occ * cfg.waves
+                               : (cfg.waves < 0 ? (int64_t)cfg.sm_count * occ : a.tiles);
   if (grid > a.tiles) grid = a.tiles;
   if (grid < 1) grid = 1;
   kern<<<(unsigned)grid, BLOCK, smem, stream>>>(a);

@@ -2,6 +2,7 @@
 #include "tune.cuh"
 
 #include <stdio.h>
+#include <string.h>
 
 namespace hsc {
 
@@ -25,11 +26,12 @@ TuneKey make_tune_key(int kind, int channels, bool sec, int lights, int64_t pixe
 std::vector<LaunchCfg> latent_candidates(const hsc_ctx* ctx) {
   std::vector<LaunchCfg> v;
   LaunchCfg d = default_cfg(ctx);
+  d.queue = reinterpret_cast<unsigned int*>(ctx->d_small + HSC_OFF_QUEUE);
   v.push_back(d);
   for (int vec : {1, 2})
     for (int ppt : {1, 2, 4})
       for (int block : {128, 256})
-        for (int waves : {1, 0}) {
+        for (int waves : {1, 0, -1}) {
           LaunchCfg c = d;
           c.ppt = ppt;
           c.block = block;
@@ -70,12 +72,15 @@ hsc_status tuned_cfg(hsc_ctx* ctx, const TuneKey& key, const std::vector<LaunchC
   if (ctx->forced.ppt > 0) {
     *out = ctx->forced;
     out->sm_count = ctx->sm_count;
+    out->queue = reinterpret_cast<unsigned int*>(ctx->d_small + HSC_OFF_QUEUE);
     return HSC_OK;
   }
   if (!ctx->autotune || cands.size() < 2) return HSC_OK;
   auto it = ctx->tuned.find(key);
   if (it != ctx->tuned.end()) {
     *out = it->second;
+    out->sm_count = ctx->sm_count;
+    out->queue = reinterpret_cast<unsigned int*>(ctx->d_small + HSC_OFF_QUEUE);
     return HSC_OK;
   }
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -136,6 +141,48 @@ hsc_status hsc_set_autotune(hsc_ctx* ctx, int enable) {
 
 const char* hsc_tune_report(hsc_ctx* ctx) { return ctx ? ctx->tune_report.c_str() : ""; }
 
+int hsc_tune_save(hsc_ctx* ctx, char* buf, size_t len) {
+  if (!ctx) return -1;
+  std::string out;
+  char line[160];
+  for (const auto& kv : ctx->tuned) {
+    const hsc::TuneKey& k = kv.first;
+    const hsc::LaunchCfg& c = kv.second;
+    snprintf(line, sizeof(line), "%d %d %d %d %d %d %d %d %d %d %d\n", k.kind, k.channels, k.sec, k.lbucket, k.pbucket,
+             k.dtype, c.ppt, c.block, c.waves, c.vec, c.chunk);
+    out += line;
+  }
+  if (buf && len > 0) {
+    const size_t n = out.size() < len - 1 ? out.size() : len - 1;
+    memcpy(buf, out.data(), n);
+    buf[n] = '\0';
+  }
+  return (int)out.size();
+}
+
+hsc_status hsc_tune_load(hsc_ctx* ctx, const char* text) {
+  hsc::clear_error();
+  HSC_CHECK_CTX(ctx);
+  HSC_REQUIRE(text != nullptr, "null text");
+  const char* p = text;
+  while (*p) {
+    hsc::TuneKey k;
+    hsc::LaunchCfg c;
+    int used = 0;
+    const int got = sscanf(p, "%d %d %d %d %d %d %d %d %d %d %d%n", &k.kind, &k.channels, &k.sec, &k.lbucket, &k.pbucket,
+                           &k.dtype, &c.ppt, &c.block, &c.waves, &c.vec, &c.chunk, &used);
+    if (got != 11) break;
+    HSC_REQUIRE((c.ppt == 1 || c.ppt == 2 || c.ppt == 4) && (c.block == 128 || c.block == 256) && c.waves >= -1 &&
+                    (c.vec == 1 || c.vec == 2) && c.chunk >= 0,
+                "bad tuning entry");
+    c.sm_count = ctx->sm_count;
+    ctx->tuned[k] = c;
+    p += used;
+    while (*p == '\n' || *p == ' ' || *p == '\r') ++p;
+  }
+  return HSC_OK;
+}
+
 hsc_status hsc_force_launch_config(hsc_ctx* ctx, int ppt, int block, int waves, int vec, int chunk) {
   hsc::clear_error();
   HSC_CHECK_CTX(ctx);
@@ -146,7 +193,7 @@ hsc_status hsc_force_launch_config(hsc_ctx* ctx, int ppt, int block, int waves, 
   }
   HSC_REQUIRE(ppt == 1 || ppt == 2 || ppt == 4, "ppt must be 1, 2 or 4");
   HSC_REQUIRE(block == 128 || block == 256, "block must be 128 or 256");
-  HSC_REQUIRE(waves >= 0 && waves <= 64, "waves out of range");
+  HSC_REQUIRE(waves >= -1 && waves <= 64, "waves out of range");
   HSC_REQUIRE(vec == 1 || vec == 2, "vec must be 1 or 2");
   HSC_REQUIRE(chunk == 0 || chunk == 16 || chunk == 28 || chunk == 32 || chunk == 44 || chunk == 84,
               "chunk must be 0, 16, 28, 32, 44 or 84");

@@ -276,9 +276,18 @@ class GpuBackend:
 
 def serve(hsc, ctx, scenes: ResidentScenes, requests, mode="latent", budget_bytes=40 * 10**9, max_batch=64,
           keep_outputs=False):
+    """Serve `requests` in real time.  Launch-configuration tuning is switched
+    off while serving: tuning a new shape class synchronises the stream, which
+    would stall the requests behind it (a server tunes ahead of time and
+    loads the result with hsc_tune_load)."""
     backend = GpuBackend(hsc, ctx, scenes, mode=mode, keep_outputs=keep_outputs)
     sched = Scheduler(backend, budget_bytes, max_inflight=4, max_batch=max_batch)
-    backend.start()
-    stats = sched.run(requests)
-    hsc.hsc_sync(ctx)
+    was = bool(ctx.autotune) if hasattr(ctx, "autotune") else False
+    hsc.hsc_set_autotune(ctx, False)
+    try:
+        backend.start()
+        stats = sched.run(requests)
+        hsc.hsc_sync(ctx)
+    finally:
+        hsc.hsc_set_autotune(ctx, was)
     return stats, backend

@@ -518,7 +518,7 @@ def test_every_latent_launch_config_is_bit_identical(env):
     M = torch.empty(3, 9, device=dev)
     hsc.hsc_fold_xyz(ctx, df.T, torch.from_numpy(D).to(dev), M)
     outs = []
-    configs = [(p_, b_, w_, v_) for p_ in (1, 2, 4) for b_ in (128, 256) for w_ in (1, 0, 3) for v_ in (1, 2)]
+    configs = [(p_, b_, w_, v_) for p_ in (1, 2, 4) for b_ in (128, 256) for w_ in (1, 0, 3, -1) for v_ in (1, 2)]
     for ppt, block, waves, vec in configs:
         hsc.hsc_force_launch_config(ctx, ppt, block, waves, vec)
         lat = torch.empty(f.pixels, 9, device=dev)

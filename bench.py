@@ -454,6 +454,7 @@ def secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T,
                                           "de76_mean": float(s[3])}
     hsc.hsc_sync(ctx)
     rows.update(batch_rows(args, hsc, ctx, dev, timed))
+    rows.update(chain_rows(args, hsc, ctx, dev, timed))
     if args.serve_seconds > 0:
         rows.update(serve_rows(args, hsc, ctx, dev))
     return rows
@@ -483,6 +484,40 @@ def serve_rows(args, hsc, ctx, dev):
                                                            "p99": spe["p99_ms"] / lat["p99_ms"]}
     del scenes
     return out
+
+
+def chain_rows(args, hsc, ctx, dev, timed):
+    """Multi-bounce chains (the codec-selection proxy of Sec. 3.5): 1,048,576
+    chains of depth 3 over held-out synthetic reflectances and lights, k = 6,
+    n = 81; CIE94 and CIEDE2000 of the latent chain against the spectral chain
+    per depth (the paper reports mean CIE94 per depth on its own data)."""
+    import torch
+    ts = hi.training_set(hi.GRID_81, seed=hi.MASTER_SEED + 200)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+    R, L = t(ts.R), t(ts.L)
+    E, D = hi.load_codec(args.k, 81)
+    T = torch.empty(3, 81, device=dev)
+    hsc.hsc_cmf_weights(ctx, 81, 380.0, 5.0, T)
+    C, depth = 1 << 20, 3
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(hi.MASTER_SEED)
+    cl = torch.randint(0, L.shape[0], (C,), generator=gen, device=dev, dtype=torch.int32)
+    cr = torch.randint(0, R.shape[0], (C, depth), generator=gen, device=dev, dtype=torch.int32)
+    d94 = torch.empty(depth, C, device=dev)
+    d00 = torch.empty(depth, C, device=dev)
+    st = torch.zeros(4 * depth, device=dev, dtype=torch.float64)
+    Ed, Dd = t(E), t(D)
+
+    def run():
+        hsc.hsc_chain_eval(ctx, R, L, Ed, Dd, T, cl, cr, d94, d00, st)
+
+    ms, _ = timed(run, args.steps, args.warmup)
+    hsc.hsc_sync(ctx)
+    s = st.cpu().numpy().reshape(depth, 4)
+    m_ = statistics.mean(ms)
+    return {"chains_depth3": {"ms": m_, "chains_per_s": C / (m_ * 1e-3), "chains": C,
+                              "de94_mean": [float(v) for v in s[:, 0]], "de94_p95": [float(v) for v in s[:, 1]],
+                              "de2000_mean": [float(v) for v in s[:, 2]], "de2000_p95": [float(v) for v in s[:, 3]]}}
 
 
 def batch_rows(args, hsc, ctx, dev, timed):

@@ -326,6 +326,26 @@ HSC_API void hsc_batch_destroy(hsc_batch* batch);
  * unless hsc_force_launch_config overrides it.                              */
 HSC_API hsc_status hsc_shade_frames(hsc_ctx* ctx, const hsc_frame* frames, int count, void* stream);
 
+/* --------------------------------------------------------- multi-bounce chains */
+
+/* Multi-bounce chains, the codec-selection proxy of Sec. 3.5: chain c starts
+ * from light chain_light[c] and multiplies in reflectance chain_refl[c][b] at
+ * bounce b (S(b) = R (.) S(b-1)); the latent chain runs the same recurrence on
+ * codes with the blockwise product (Eq. 5).  At every depth both are taken to
+ * XYZ (T S and M z with M = T D) and to CIELAB relative to the light's white
+ * T L, and compared by CIE94 (spectral chain as reference) and CIEDE2000.
+ *   refl: device n_refl x n;  lights: device n_lights x n;  E: k x n;  D: n x k;
+ *   T: 3 x n (hsc_cmf_weights);  chain_light: device chains int32;
+ *   chain_refl: device chains x depth int32 (depth <= 8);
+ *   de94_out, de2000_out: device depth x chains float32 (depth-major);
+ *   stats_out: device depth x 4 doubles {mean dE94, p95 dE94, mean dE2000, p95 dE2000}
+ *   (p95 by nearest rank).  Out-of-range indices set the device error word.
+ * Uses context scratch (codes) and the reduction scratch.                   */
+HSC_API hsc_status hsc_chain_eval(hsc_ctx* ctx, const float* refl, int n_refl, const float* lights, int n_lights,
+                                  const float* E, const float* D, int k, int n, const float* T,
+                                  const int32_t* chain_light, const int32_t* chain_refl, int64_t chains, int depth,
+                                  float* de94_out, float* de2000_out, double* stats_out, void* stream);
+
 /* ----------------------------------------------------------------- metrics */
 
 /* Colour difference of a test image against a reference image.  Both are

@@ -111,6 +111,16 @@ def xyz_to_lab(xyz, white):
     return np.stack([116.0 * fy - 16.0, 500.0 * (fx - fy), 200.0 * (fy - fz)], axis=1)
 
 
+def xyz_to_lab_rows(xyz, whites):
+    """CIE 1976 L*a*b* of (P,3) XYZ, each row relative to its own white (P,3)."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    w = np.asarray(whites, dtype=np.float64)
+    fx = _lab_f(xyz[:, 0] / w[:, 0])
+    fy = _lab_f(xyz[:, 1] / w[:, 1])
+    fz = _lab_f(xyz[:, 2] / w[:, 2])
+    return np.stack([116.0 * fy - 16.0, 500.0 * (fx - fy), 200.0 * (fy - fz)], axis=1)
+
+
 def delta_e76(lab1, lab2):
     return np.sqrt(((np.asarray(lab1) - np.asarray(lab2)) ** 2).sum(axis=1))
 

@@ -93,6 +93,8 @@ _SIGS = {
     "hsc_decode_spectra": ([_vp, _vp, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _vp], _i32),
     "hsc_shade_spectral": ([_vp, _GB, _GB, _i64, _vp, _i32, _LI, _vp, _i32, _vp, _vp, _vp, _vp], _i32),
     "hsc_delta_e": ([_vp, _vp, _vp, _i64, _vp, _i32, _vp, _vp, _vp], _i32),
+    "hsc_chain_eval": ([_vp, _vp, _i32, _vp, _i32, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp],
+                       _i32),
     "hsc_batch_create": ([_vp, ctypes.POINTER(_Frame), _i32, ctypes.POINTER(_vp)], _i32),
     "hsc_batch_shade": ([_vp, _vp, _vp], _i32),
     "hsc_batch_destroy": ([_vp], None),
@@ -420,3 +422,17 @@ def hsc_shade_frames(ctx: Context, frames: Sequence[BatchFrame], stream=None):
     """Asynchronous one-shot batched launch (continuous batching)."""
     arr = (_Frame * len(frames))(*[f.s for f in frames])
     _check(_lib.hsc_shade_frames(ctx.handle, arr, len(frames), _stream(stream)))
+
+
+def hsc_chain_eval(ctx: Context, refl: torch.Tensor, lights: torch.Tensor, E: torch.Tensor, D: torch.Tensor,
+                   T: torch.Tensor, chain_light: torch.Tensor, chain_refl: torch.Tensor, de94_out: torch.Tensor,
+                   de2000_out: torch.Tensor, stats_out: torch.Tensor, stream=None):
+    """Multi-bounce chain errors (Sec. 3.5 proxy); see include/hsc.h."""
+    k, n = E.shape
+    chains, depth = chain_refl.shape
+    if de94_out.shape != (depth, chains) or de2000_out.shape != (depth, chains) or stats_out.numel() < 4 * depth:
+        raise ValueError("outputs: de (depth, chains), stats 4*depth doubles")
+    _check(_lib.hsc_chain_eval(ctx.handle, _ptr(refl), int(refl.shape[0]), _ptr(lights), int(lights.shape[0]),
+                               _ptr(E), _ptr(D), int(k), int(n), _ptr(T), _ptr(chain_light), _ptr(chain_refl),
+                               int(chains), int(depth), _ptr(de94_out), _ptr(de2000_out), _ptr(stats_out),
+                               _stream(stream)))

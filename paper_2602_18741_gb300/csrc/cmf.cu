@@ -69,6 +69,13 @@ __global__ void fold_kernel(const float* __restrict__ T, const float* __restrict
 
 }  // namespace
 
+namespace hsc {
+hsc_status launch_fold(const float* T, const float* D, int k, int n, float* M, cudaStream_t s) {
+  fold_kernel<<<ceil_div_i(3 * k, 128), 128, 0, s>>>(T, D, k, n, M);
+  return check_launch("fold_kernel");
+}
+}  // namespace hsc
+
 extern "C" {
 
 hsc_status hsc_cmf_weights(hsc_ctx* ctx, int n, float lambda0, float dlambda, float* T_out, void* stream) {
@@ -89,8 +96,7 @@ hsc_status hsc_fold_xyz(hsc_ctx* ctx, const float* T, const float* D, int k, int
   HSC_REQUIRE(k >= 1 && k <= HSC_MAX_K, "k=%d out of range", k);
   HSC_REQUIRE(T && D && M_out, "null pointer");
   HSC_GUARD(ctx);
-  fold_kernel<<<hsc::ceil_div_i(3 * k, 128), 128, 0, hsc::as_stream(stream)>>>(T, D, k, n, M_out);
-  return hsc::check_launch("fold_kernel");
+  return hsc::launch_fold(T, D, k, n, M_out, hsc::as_stream(stream));
 }
 
 }  // extern "C"

@@ -33,6 +33,15 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ E
 
 }  // namespace
 
+namespace hsc {
+hsc_status launch_encode(const float* E, int k, int n, const float* S, int m, void* out, int out_dt, cudaStream_t s) {
+  if (m <= 0) return HSC_OK;
+  const int64_t warps = (int64_t)m * k;
+  encode_kernel<<<ceil_div_i(warps * 32, 256), 256, 0, s>>>(E, k, n, S, m, out, out_dt);
+  return check_launch("encode_kernel");
+}
+}  // namespace hsc
+
 extern "C" hsc_status hsc_encode(hsc_ctx* ctx, const float* E, int k, int n, const float* spectra, int m,
                                  void* codes_out, hsc_dtype out_dt, void* stream) {
   hsc::clear_error();
@@ -46,8 +55,5 @@ extern "C" hsc_status hsc_encode(hsc_ctx* ctx, const float* E, int k, int n, con
   HSC_REQUIRE(hsc::aligned(E, 4) && hsc::aligned(spectra, 4) && hsc::aligned(codes_out, out_dt == HSC_F32 ? 4 : 2),
               "misaligned pointer");
   HSC_GUARD(ctx);
-  const int64_t warps = (int64_t)m * k;
-  encode_kernel<<<hsc::ceil_div_i(warps * 32, 256), 256, 0, hsc::as_stream(stream)>>>(E, k, n, spectra, m, codes_out,
-                                                                                       (int)out_dt);
-  return hsc::check_launch("encode_kernel");
+  return hsc::launch_encode(E, k, n, spectra, m, codes_out, (int)out_dt, hsc::as_stream(stream));
 }

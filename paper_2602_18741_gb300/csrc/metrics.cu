@@ -12,6 +12,7 @@
 //      three passes over 11 / 11 / 10-bit digits, each a histogram kernel and a
 //      one-CTA scan that narrows the prefix and the rank.
 #include "common.cuh"
+#include "colour.cuh"
 
 namespace hsc {
 
@@ -28,75 +29,6 @@ struct Scratch {
   unsigned int hist[2048];
   double partial[1];         // [grid][4]
 };
-
-__device__ __forceinline__ float lab_f(float t) {
-  const float d = 6.0f / 29.0f;
-  return (t > d * d * d) ? cbrtf(t) : t / (3.0f * d * d) + 4.0f / 29.0f;
-}
-
-__device__ __forceinline__ void to_lab(float X, float Y, float Z, const float* w, float& L, float& a, float& b) {
-  const float fx = lab_f(X / w[0]), fy = lab_f(Y / w[1]), fz = lab_f(Z / w[2]);
-  L = 116.0f * fy - 16.0f;
-  a = 500.0f * (fx - fy);
-  b = 200.0f * (fy - fz);
-}
-
-constexpr float kDeg = 57.29577951308232f;
-constexpr float kRad = 0.017453292519943295f;
-
-__device__ __forceinline__ float pow7(float x) {
-  const float x2 = x * x;
-  return x2 * x2 * x2 * x;
-}
-
-// CIEDE2000 (CIE 142-2001), kL = kC = kH = 1; colour 1 is the reference.
-__device__ float de2000(float L1, float a1, float b1, float L2, float a2, float b2) {
-  const float C1 = sqrtf(a1 * a1 + b1 * b1), C2 = sqrtf(a2 * a2 + b2 * b2);
-  const float Cm7 = pow7(0.5f * (C1 + C2));
-  const float G = 0.5f * (1.0f - sqrtf(Cm7 / (Cm7 + 6103515625.0f)));  // 25^7
-  const float ap1 = (1.0f + G) * a1, ap2 = (1.0f + G) * a2;
-  const float Cp1 = sqrtf(ap1 * ap1 + b1 * b1), Cp2 = sqrtf(ap2 * ap2 + b2 * b2);
-  float h1 = (ap1 == 0.0f && b1 == 0.0f) ? 0.0f : atan2f(b1, ap1) * kDeg;
-  float h2 = (ap2 == 0.0f && b2 == 0.0f) ? 0.0f : atan2f(b2, ap2) * kDeg;
-  if (h1 < 0.0f) h1 += 360.0f;
-  if (h2 < 0.0f) h2 += 360.0f;
-  const float dL = L2 - L1, dC = Cp2 - Cp1;
-  const float pc = Cp1 * Cp2;
-  float dh = h2 - h1;
-  if (pc == 0.0f) dh = 0.0f;
-  else if (dh > 180.0f) dh -= 360.0f;
-  else if (dh < -180.0f) dh += 360.0f;
-  const float dH = 2.0f * sqrtf(pc) * sinf(0.5f * dh * kRad);
-  const float Lm = 0.5f * (L1 + L2), Cm = 0.5f * (Cp1 + Cp2);
-  float hm = h1 + h2;
-  if (pc != 0.0f) {
-    if (fabsf(h1 - h2) <= 180.0f) hm *= 0.5f;
-    else if (hm < 360.0f) hm = 0.5f * (hm + 360.0f);
-    else hm = 0.5f * (hm - 360.0f);
-  }
-  const float T = 1.0f - 0.17f * cosf((hm - 30.0f) * kRad) + 0.24f * cosf(2.0f * hm * kRad) +
-                  0.32f * cosf((3.0f * hm + 6.0f) * kRad) - 0.20f * cosf((4.0f * hm - 63.0f) * kRad);
-  const float e = (hm - 275.0f) / 25.0f;
-  const float dtheta = 30.0f * expf(-e * e);
-  const float Cm7b = pow7(Cm);
-  const float RC = 2.0f * sqrtf(Cm7b / (Cm7b + 6103515625.0f));
-  const float l50 = (Lm - 50.0f) * (Lm - 50.0f);
-  const float SL = 1.0f + 0.015f * l50 / sqrtf(20.0f + l50);
-  const float SC = 1.0f + 0.045f * Cm;
-  const float SH = 1.0f + 0.015f * Cm * T;
-  const float RT = -sinf(2.0f * dtheta * kRad) * RC;
-  const float tL = dL / SL, tC = dC / SC, tH = dH / SH;
-  return sqrtf(fmaxf(tL * tL + tC * tC + tH * tH + RT * tC * tH, 0.0f));
-}
-
-// CIE94, graphic arts (kL = 1, K1 = 0.045, K2 = 0.015); colour 1 is the reference.
-__device__ float de94(float L1, float a1, float b1, float L2, float a2, float b2) {
-  const float C1 = sqrtf(a1 * a1 + b1 * b1), C2 = sqrtf(a2 * a2 + b2 * b2);
-  const float dL = L1 - L2, dC = C1 - C2, da = a1 - a2, db = b1 - b2;
-  const float dH2 = fmaxf(da * da + db * db - dC * dC, 0.0f);
-  const float SC = 1.0f + 0.045f * C1, SH = 1.0f + 0.015f * C1;
-  return sqrtf(dL * dL + (dC / SC) * (dC / SC) + dH2 / (SH * SH));
-}
 
 __global__ void ymax_kernel(const float* __restrict__ ref, int64_t P, const float* __restrict__ T, int n,
                             Scratch* sc) {
@@ -276,7 +208,76 @@ __global__ void __launch_bounds__(1024) radix_select_kernel(Scratch* sc, int shi
   }
 }
 
+// Per-CTA FP64 sums of v[0..count) for the generic mean.
+__global__ void __launch_bounds__(kMBlock) sum_kernel(const float* __restrict__ v, int64_t count, Scratch* sc) {
+  __shared__ double s_red[kMBlock / 32];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    acc += (double)__ldg(v + i);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < kMBlock / 32; ++i) t += s_red[i];
+    sc->partial[4 * blockIdx.x] = t;
+  }
+}
+
+// Mean from the partial sums (fixed order) and the rank for the p95 select.
+__global__ void __launch_bounds__(256) mean_fold_kernel(Scratch* sc, int nblocks, int64_t count, double* out) {
+  __shared__ double s_r[256];
+  const int t = threadIdx.x;
+  double a0 = 0.0;
+  for (int i = t; i < nblocks; i += 256) a0 += sc->partial[4 * i];
+  s_r[t] = a0;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (t < w) s_r[t] += s_r[t + w];
+    __syncthreads();
+  }
+  if (t == 0) {
+    out[0] = count > 0 ? s_r[0] / (double)count : 0.0;
+    long long r = (long long)ceil(0.95 * (double)count) - 1;
+    sc->rank = (unsigned long long)(r < 0 ? 0 : r);
+    sc->prefix = 0u;
+  }
+}
+
+int stats_grid(const hsc_ctx* ctx, int64_t count) {
+  int grid = ctx->sm_count * 4;
+  const int64_t need = (count + kMBlock - 1) / kMBlock;
+  if (grid > need) grid = (int)need;
+  return grid < 1 ? 1 : grid;
+}
+
+hsc_status radix_p95(hsc_ctx* ctx, const float* v, int64_t count, Scratch* sc, int grid, double* stats,
+                     cudaStream_t s) {
+  const int shifts[3] = {21, 10, 0};
+  const int widths[3] = {11, 11, 10};
+  for (int i = 0; i < 3; ++i) {
+    radix_hist_kernel<<<grid, kMBlock, 0, s>>>(v, count, sc, shifts[i], widths[i]);
+    HSC_TRY(check_launch("radix_hist_kernel"));
+    radix_select_kernel<<<1, 1024, 0, s>>>(sc, shifts[i], widths[i], stats);
+    HSC_TRY(check_launch("radix_select_kernel"));
+  }
+  return HSC_OK;
+}
+
 }  // namespace
+
+// Mean and nearest-rank p95 of count non-negative floats: out[0] = mean,
+// out[1] = p95 (device doubles).  Uses the context's reduction scratch.
+hsc_status launch_mean_p95(hsc_ctx* ctx, const float* v, int64_t count, double* out, cudaStream_t s) {
+  auto* sc = reinterpret_cast<Scratch*>(ctx->d_small + HSC_OFF_REDUCE);
+  const int grid = stats_grid(ctx, count);
+  HSC_CUDA(cudaMemsetAsync(sc, 0, sizeof(Scratch), s));
+  sum_kernel<<<grid, kMBlock, 0, s>>>(v, count, sc);
+  HSC_TRY(check_launch("sum_kernel"));
+  mean_fold_kernel<<<1, 256, 0, s>>>(sc, grid, count, out);
+  HSC_TRY(check_launch("mean_fold_kernel"));
+  return radix_p95(ctx, v, count, sc, grid, out, s);
+}
 
 }  // namespace hsc
 
@@ -297,10 +298,7 @@ extern "C" hsc_status hsc_delta_e(hsc_ctx* ctx, const float* xyz_test, const flo
     HSC_TRY(hsc::ensure_big(ctx, (size_t)pixels * sizeof(float), s));
     de = reinterpret_cast<float*>(ctx->d_big);
   }
-  int grid = ctx->sm_count * 4;
-  const int64_t need = (pixels + hsc::kMBlock - 1) / hsc::kMBlock;
-  if (grid > need) grid = (int)need;
-  if (grid < 1) grid = 1;
+  const int grid = hsc::stats_grid(ctx, pixels);
   auto* sc = reinterpret_cast<hsc::Scratch*>(ctx->d_small + HSC_OFF_REDUCE);
   HSC_CUDA(cudaMemsetAsync(sc, 0, sizeof(hsc::Scratch), s));
   hsc::ymax_kernel<<<grid, hsc::kMBlock, 0, s>>>(xyz_ref, pixels, T, n, sc);
@@ -309,13 +307,5 @@ extern "C" hsc_status hsc_delta_e(hsc_ctx* ctx, const float* xyz_test, const flo
   HSC_TRY(hsc::check_launch("de_kernel"));
   hsc::fold_kernel<<<1, 256, 0, s>>>(sc, grid, pixels, stats_out);
   HSC_TRY(hsc::check_launch("fold_kernel"));
-  const int shifts[3] = {21, 10, 0};
-  const int widths[3] = {11, 11, 10};
-  for (int i = 0; i < 3; ++i) {
-    hsc::radix_hist_kernel<<<grid, hsc::kMBlock, 0, s>>>(de, pixels, sc, shifts[i], widths[i]);
-    HSC_TRY(hsc::check_launch("radix_hist_kernel"));
-    hsc::radix_select_kernel<<<1, 1024, 0, s>>>(sc, shifts[i], widths[i], stats_out);
-    HSC_TRY(hsc::check_launch("radix_select_kernel"));
-  }
-  return HSC_OK;
+  return hsc::radix_p95(ctx, de, pixels, sc, grid, stats_out, s);
 }

@@ -1,0 +1,70 @@
+"""Multi-bounce chain evaluator (the Sec. 3.5 proxy) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import hsc_inputs as hi
+from oracle import chain, cmf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import paper_2602_18741_gb300 as hsc
+    ctx = hsc.Context(0)
+    yield hsc, ctx, torch.device("cuda:0")
+    ctx.close()
+
+
+def _run(hsc, ctx, dev, R, L, E, D, grid_spec, cl, cr):
+    import torch
+    t = lambda a, dt=np.float32: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(dev)
+    n = grid_spec[2]
+    T = torch.empty(3, n, device=dev)
+    hsc.hsc_cmf_weights(ctx, n, grid_spec[0], grid_spec[1], T)
+    C, depth = cr.shape
+    d94 = torch.empty(depth, C, device=dev)
+    d00 = torch.empty(depth, C, device=dev)
+    st = torch.zeros(4 * depth, device=dev, dtype=torch.float64)
+    hsc.hsc_chain_eval(ctx, t(R), t(L), t(E), t(D), T, t(cl, np.int32), t(cr, np.int32), d94, d00, st)
+    hsc.hsc_sync(ctx)
+    return d94.cpu().numpy(), d00.cpu().numpy(), st.cpu().numpy().reshape(depth, 4)
+
+
+@pytest.mark.parametrize("k,grid_spec", [(6, hi.GRID_81), (9, hi.GRID_31)])
+def test_chain_errors_match_oracle(env, k, grid_spec):
+    # 500 reflectance-light chains of depth 3, the size of the paper's protocol
+    hsc, ctx, dev = env
+    ts = hi.training_set(grid_spec, seed=hi.MASTER_SEED + 200, n_smooth=300, n_saw=40, n_bb=40, n_nb=40, pairs=1)
+    R = ts.R.astype(np.float32)
+    L = ts.L.astype(np.float32)
+    E, D = hi.load_codec(k, grid_spec[2])
+    rng = np.random.default_rng(k)
+    cl = rng.integers(0, L.shape[0], 500)
+    cr = rng.integers(0, R.shape[0], (500, 3))
+    d94, d00, st = _run(hsc, ctx, dev, R, L, E, D, grid_spec, cl, cr)
+    ref = chain.chain_delta_e(R, L, E.astype(np.float64), D.astype(np.float64), cmf.cmf_weights(*grid_spec), cl, cr)
+    assert np.max(np.abs(d94 - ref["de94"])) < 5e-3
+    assert np.max(np.abs(d00 - ref["de2000"])) < 5e-3
+    for b in range(3):
+        assert abs(st[b, 0] - ref["de94_mean"][b]) < 0.01
+        assert abs(st[b, 1] - ref["de94_p95"][b]) < 0.01
+        assert abs(st[b, 2] - ref["de2000_mean"][b]) < 0.01
+        assert abs(st[b, 3] - ref["de2000_p95"][b]) < 0.01
+        # the p95 is the exact nearest rank of the GPU's own values
+        assert st[b, 3] == np.sort(d00[b])[int(np.ceil(0.95 * 500)) - 1]
+
+
+def test_identity_codec_chains_are_exact(env):
+    hsc, ctx, dev = env
+    g = (400.0, 10.0, 30)
+    lam = hi.grid(*g)
+    rng = np.random.default_rng(2)
+    R = hi.smooth_reflectances(rng, lam, 20).astype(np.float32)
+    L = hi.blackbody(lam, [3000.0, 5000.0, 9000.0]).astype(np.float32)
+    E = np.eye(30, dtype=np.float32)
+    cl = rng.integers(0, 3, 64)
+    cr = rng.integers(0, 20, (64, 5))
+    d94, d00, st = _run(hsc, ctx, dev, R, L, E, E.T.copy(), g, cl, cr)
+    assert np.abs(d94).max() < 1e-3 and np.abs(d00).max() < 1e-3

@@ -1,0 +1,58 @@
+"""Pins of the multi-bounce chain oracle (Sec. 3.5 proxy)."""
+import numpy as np
+
+import hsc_inputs as hi
+from oracle import chain, cmf
+
+
+def _sets(n=31, seed=1):
+    lam = hi.grid(400.0, 300.0 / (n - 1), n)
+    rng = np.random.default_rng(seed)
+    R = hi.smooth_reflectances(rng, lam, 12)
+    L = np.concatenate([hi.blackbody(lam, [3000.0, 6500.0]), hi.narrowband(lam, [500.0], [15.0])])
+    return R, L, cmf.cmf_weights(400.0, 300.0 / (n - 1), n)
+
+
+def test_identity_codec_gives_zero_error():
+    R, L, T = _sets(n=30)
+    E = np.eye(30)
+    rng = np.random.default_rng(0)
+    cl = rng.integers(0, 3, 20)
+    cr = rng.integers(0, 12, (20, 3))
+    out = chain.chain_delta_e(R, L, E, E.T, T, cl, cr)
+    assert np.abs(out["de2000"]).max() < 1e-9 and np.abs(out["de94"]).max() < 1e-9
+
+
+def test_constant_reflectance_closed_form():
+    # S(b) = rho^b L: Y relative to the light's white is rho^b, neutral colour
+    n = 31
+    _, L, T = _sets(n)
+    R = np.full((1, n), 0.5)
+    xs, _, white = chain.chain_xyz(R, L, np.eye(n)[:3], np.eye(n)[:, :3], T, [0, 1], [[0, 0, 0], [0, 0, 0]])
+    for b in range(3):
+        lab = cmf.xyz_to_lab_rows(xs[:, b], white)
+        y = 0.5 ** (b + 1)
+        assert np.allclose(lab[:, 0], 116.0 * y ** (1 / 3) - 16.0, atol=1e-10)
+        assert np.allclose(lab[:, 1:], 0.0, atol=1e-10)
+
+
+def test_all_ones_chain_is_the_white():
+    n = 31
+    _, L, T = _sets(n)
+    R = np.ones((1, n))
+    xs, _, white = chain.chain_xyz(R, L, np.eye(n)[:3], np.eye(n)[:, :3], T, [2], [[0, 0]])
+    lab = cmf.xyz_to_lab_rows(xs[:, 1], white)
+    assert np.allclose(lab, [[100.0, 0.0, 0.0]], atol=1e-10)
+
+
+def test_brute_force_matches_vectorised():
+    R, L, T = _sets(n=16, seed=3)
+    rng = np.random.default_rng(5)
+    E = rng.uniform(0, 0.3, (6, 16))
+    D = rng.uniform(0, 1.0, (16, 6))
+    cl = [1, 2]
+    cr = [[3, 4, 5], [0, 11, 7]]
+    xs, xl, _ = chain.chain_xyz(R, L, E, D, T, cl, cr)
+    for c in range(2):
+        bs, bl = chain.brute_force_chain_xyz(R, L, E, D, T, cl[c], cr[c])
+        assert np.allclose(xs[c], bs, rtol=1e-13) and np.allclose(xl[c], bl, rtol=1e-13)

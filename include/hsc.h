@@ -332,8 +332,9 @@ HSC_API hsc_status hsc_shade_frames(hsc_ctx* ctx, const hsc_frame* frames, int c
  * from light chain_light[c] and multiplies in reflectance chain_refl[c][b] at
  * bounce b (S(b) = R (.) S(b-1)); the latent chain runs the same recurrence on
  * codes with the blockwise product (Eq. 5).  At every depth both are taken to
- * XYZ (T S and M z with M = T D) and to CIELAB relative to the light's white
- * T L, and compared by CIE94 (spectral chain as reference) and CIEDE2000.
+ * XYZ (T S and M z with M = T D), scaled by the light's luminance 1 / Y(T L),
+ * converted to CIELAB with the equal-energy white T @ 1, and compared by
+ * CIE94 (spectral chain as reference) and CIEDE2000.
  *   refl: device n_refl x n;  lights: device n_lights x n;  E: k x n;  D: n x k;
  *   T: 3 x n (hsc_cmf_weights);  chain_light: device chains int32;
  *   chain_refl: device chains x depth int32 (depth <= 8);

@@ -8,15 +8,19 @@ space with the blockwise product of Eq. 5, and the two are compared per depth
 by CIE94 colour difference.  Here both chains are taken to colour with the
 CMF weights T; the latent chain is decoded with D first (T (D z)).
 
-Reading where the paper is silent: colours are CIELAB relative to the white
-of the light itself (Xn, Yn, Zn) = T L, the usual object-colour convention, so
-every chain has its own white; CIE94 takes the spectral chain as reference.
-Delta E 2000 and the nearest-rank p95 are reported beside the means.
+Reading where the paper is silent: each chain's colours are scaled by the
+luminance of its light, 1 / Y(T L), and converted to CIELAB with the
+equal-energy white T @ 1 (Yn = 1).  (Taking the light's own T L as the white
+instead makes Lab degenerate for narrow-band lights near the ends of the grid,
+whose white has X or Z near zero.)  CIE94 takes the spectral chain as
+reference; Delta E 2000 and the nearest-rank p95 are reported beside the
+means.
 
 Pins (tests/test_oracle_chain.py): the identity codec (k = n) makes every
 latent chain equal its spectral chain (Delta E 0); constant reflectances rho
-give S(b) = rho^b L, whose L* is 116 (rho^b)^(1/3) - 16 with a* = b* = 0; an
-all-ones chain is the white (100, 0, 0); brute-force loops on tiny inputs.
+under an equal-energy light give S(b) = rho^b, whose L* is 116 (rho^b)^(1/3)
+- 16 with a* = b* = 0; an all-ones chain under that light is the white
+(100, 0, 0); brute-force loops on tiny inputs.
 """
 from __future__ import annotations
 
@@ -56,13 +60,15 @@ def chain_delta_e(R, L, E, D, T, chain_light, chain_refl):
     dict with (depth, C) arrays 'de94', 'de2000' and per-depth lists of the
     means and nearest-rank p95s."""
     from . import metrics
-    xs, xl, white = chain_xyz(R, L, E, D, T, chain_light, chain_refl)
+    xs, xl, light_xyz = chain_xyz(R, L, E, D, T, chain_light, chain_refl)
     C, depth, _ = xs.shape
+    white = np.asarray(T, dtype=np.float64).sum(axis=1)
+    scale = 1.0 / light_xyz[:, 1]
     de94 = np.empty((depth, C))
     de00 = np.empty((depth, C))
     for b in range(depth):
-        lab_s = cmf.xyz_to_lab_rows(xs[:, b], white)
-        lab_l = cmf.xyz_to_lab_rows(xl[:, b], white)
+        lab_s = cmf.xyz_to_lab(xs[:, b] * scale[:, None], white)
+        lab_l = cmf.xyz_to_lab(xl[:, b] * scale[:, None], white)
         de94[b] = cmf.delta_e94(lab_s, lab_l)
         de00[b] = cmf.delta_e2000(lab_s, lab_l)
     return {"de94": de94, "de2000": de00,

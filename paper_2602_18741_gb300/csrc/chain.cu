@@ -2,9 +2,10 @@
 // multiplied by a fresh reflectance at every bounce, S(b) = R(b) (.) S(b-1),
 // S(0) = L; the latent chain runs the same recurrence on codes with the
 // blockwise product (Eq. 5), z(b) = E R(b) (.) z(b-1), z(0) = E L.  Per chain
-// and depth both are projected to XYZ (T S(b) and M z(b), M = T D), converted
-// to CIELAB relative to the light's own white T L, and compared by CIE94
-// (spectral chain as reference) and CIEDE2000.
+// and depth both are projected to XYZ (T S(b) and M z(b), M = T D), scaled by
+// the light's luminance 1 / Y(T L), converted to CIELAB with the
+// equal-energy white T @ 1, and compared by CIE94 (spectral chain as
+// reference) and CIEDE2000.
 //
 // One thread per chain; the spectral chain walks the n samples once, carrying
 // the running product and the XYZ sums of every depth, the latent chain walks
@@ -61,8 +62,8 @@ __global__ void __launch_bounds__(128) chain_kernel(const ChainArgs a) {
     atomicOr(a.err, HSC_DEVERR_MATERIAL);
     l = 0;
   }
-  // spectral chain
-  float wx = 0.0f, wy = 0.0f, wz = 0.0f;
+  // spectral chain; (wx, wy, wz) = T L, (ex, ey, ez) = T @ 1
+  float wx = 0.0f, wy = 0.0f, wz = 0.0f, ex = 0.0f, ey = 0.0f, ez = 0.0f;
   float xs[kMaxDepth][3];
 #pragma unroll
   for (int b = 0; b < kMaxDepth; ++b) xs[b][0] = xs[b][1] = xs[b][2] = 0.0f;
@@ -72,6 +73,9 @@ __global__ void __launch_bounds__(128) chain_kernel(const ChainArgs a) {
     wx = __fmaf_rn(t0, s, wx);
     wy = __fmaf_rn(t1, s, wy);
     wz = __fmaf_rn(t2, s, wz);
+    ex = __fadd_rn(ex, t0);
+    ey = __fadd_rn(ey, t1);
+    ez = __fadd_rn(ez, t2);
 #pragma unroll
     for (int b = 0; b < kMaxDepth; ++b) {
       if (b < a.depth) {
@@ -99,14 +103,18 @@ __global__ void __launch_bounds__(128) chain_kernel(const ChainArgs a) {
       }
     }
   }
+  const bool dark = !(wy > 0.0f);  // a light with no luminance has no colour
+  const float inv = dark ? 0.0f : 1.0f / wy;
+  (void)wx;
+  (void)wz;
 #pragma unroll
   for (int b = 0; b < kMaxDepth; ++b) {
     if (b < a.depth) {
       float L1, a1, b1, L2, a2, b2;
-      to_lab_white(xs[b][0], xs[b][1], xs[b][2], wx, wy, wz, L1, a1, b1);
-      to_lab_white(xl[b][0], xl[b][1], xl[b][2], wx, wy, wz, L2, a2, b2);
-      a.de94[(int64_t)b * a.C + c] = bad ? 0.0f : de94(L1, a1, b1, L2, a2, b2);
-      a.de00[(int64_t)b * a.C + c] = bad ? 0.0f : de2000(L1, a1, b1, L2, a2, b2);
+      to_lab_white(xs[b][0] * inv, xs[b][1] * inv, xs[b][2] * inv, ex, ey, ez, L1, a1, b1);
+      to_lab_white(xl[b][0] * inv, xl[b][1] * inv, xl[b][2] * inv, ex, ey, ez, L2, a2, b2);
+      a.de94[(int64_t)b * a.C + c] = (bad || dark) ? 0.0f : de94(L1, a1, b1, L2, a2, b2);
+      a.de00[(int64_t)b * a.C + c] = (bad || dark) ? 0.0f : de2000(L1, a1, b1, L2, a2, b2);
     }
   }
 }

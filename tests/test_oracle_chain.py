@@ -24,24 +24,31 @@ def test_identity_codec_gives_zero_error():
 
 
 def test_constant_reflectance_closed_form():
-    # S(b) = rho^b L: Y relative to the light's white is rho^b, neutral colour
-    n = 31
-    _, L, T = _sets(n)
+    # equal-energy light of any intensity, S(b) = rho^b: Y / Y(light) = rho^b,
+    # neutral colour; the codec is exact for flat spectra at k = n
+    n = 30
+    _, _, T = _sets(n)
+    L = np.full((2, n), 3.0)
     R = np.full((1, n), 0.5)
-    xs, _, white = chain.chain_xyz(R, L, np.eye(n)[:3], np.eye(n)[:, :3], T, [0, 1], [[0, 0, 0], [0, 0, 0]])
+    E = np.eye(n)
+    out = chain.chain_delta_e(R, L, E, E.T, T, [0, 1], [[0, 0, 0], [0, 0, 0]])
+    xs, _, light = chain.chain_xyz(R, L, E, E.T, T, [0, 1], [[0, 0, 0], [0, 0, 0]])
+    white = T.sum(axis=1)
     for b in range(3):
-        lab = cmf.xyz_to_lab_rows(xs[:, b], white)
+        lab = cmf.xyz_to_lab(xs[:, b] / light[:, 1:2], white)
         y = 0.5 ** (b + 1)
         assert np.allclose(lab[:, 0], 116.0 * y ** (1 / 3) - 16.0, atol=1e-10)
         assert np.allclose(lab[:, 1:], 0.0, atol=1e-10)
+    assert np.abs(out["de2000"]).max() < 1e-9
 
 
 def test_all_ones_chain_is_the_white():
     n = 31
-    _, L, T = _sets(n)
+    _, _, T = _sets(n)
+    L = np.full((1, n), 0.25)
     R = np.ones((1, n))
-    xs, _, white = chain.chain_xyz(R, L, np.eye(n)[:3], np.eye(n)[:, :3], T, [2], [[0, 0]])
-    lab = cmf.xyz_to_lab_rows(xs[:, 1], white)
+    xs, _, light = chain.chain_xyz(R, L, np.eye(n)[:3], np.eye(n)[:, :3], T, [0], [[0, 0]])
+    lab = cmf.xyz_to_lab(xs[:, 1] / light[:, 1:2], T.sum(axis=1))
     assert np.allclose(lab, [[100.0, 0.0, 0.0]], atol=1e-10)
 
 

@@ -249,13 +249,9 @@ def run_hsc(args, rank: int, world: int):
         dist.barrier()
     wall = time.perf_counter() - wall0
     hsc.hsc_sync(ctx)
-    total_ms = sum(per_step)
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(sum(per_step), world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * evals * args.steps / (total_ms * 1e-3)
+    value = whole_job_rate(evals * args.steps, world, total_ms)
 
     result = None
     if rank == 0:
@@ -301,6 +297,22 @@ def run_hsc(args, rank: int, world: int):
         }
     ctx.close()
     return result
+
+
+def max_over_ranks(value: float, world: int, device) -> float:
+    """The slowest rank's value (the job's time is set by its slowest GPU)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, total_ms_max: float) -> float:
+    """Units all ranks processed per second of the slowest rank."""
+    return world * units_per_rank / (total_ms_max * 1e-3)
 
 
 def _pct(xs, q):

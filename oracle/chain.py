@@ -8,16 +8,21 @@ space with the blockwise product of Eq. 5, and the two are compared per depth
 by CIE94 colour difference.  Here both chains are taken to colour with the
 CMF weights T; the latent chain is decoded with D first (T (D z)).
 
-Reading where the paper is silent: each chain's colours are scaled by the
-luminance of its light, 1 / Y(T L), and converted to CIELAB with the
-equal-energy white T @ 1 (Yn = 1).  (Taking the light's own T L as the white
-instead makes Lab degenerate for narrow-band lights near the ends of the grid,
-whose white has X or Z near zero.)  CIE94 takes the spectral chain as
-reference; Delta E 2000 and the nearest-rank p95 are reported beside the
-means.
+Reading where the paper is silent: each chain's colours are scaled by
+1 / max(T L), so that the largest tristimulus value of its light is 1, and
+converted to CIELAB with the equal-energy white T @ 1 (Yn = 1).  The paper's
+chain errors are a few Delta E, which presumes colours in a bounded range:
+taking the light's own T L as the white makes Lab degenerate for narrow-band
+lights near the ends of the grid (X or Z near zero), and scaling by the
+luminance Y(T L) alone leaves such lights with X / Y or Z / Y in the
+hundreds.  A light with max(T L) <= 0 has no colour; its chains get Delta E 0.
+CIE94 takes the spectral chain as reference; Delta E 2000 and the
+nearest-rank p95 are reported beside the means.
 
 Pins (tests/test_oracle_chain.py): the identity codec (k = n) makes every
-latent chain equal its spectral chain (Delta E 0); constant reflectances rho
+latent chain equal its spectral chain (Delta E 0); the exposure maps every
+light's largest tristimulus value to 1 and is invariant to the light's
+intensity, so Delta E is too; constant reflectances rho
 under an equal-energy light give S(b) = rho^b, whose L* is 116 (rho^b)^(1/3)
 - 16 with a* = b* = 0; an all-ones chain under that light is the white
 (100, 0, 0); brute-force loops on tiny inputs.
@@ -55,6 +60,13 @@ def chain_xyz(R, L, E, D, T, chain_light, chain_refl):
     return xs, xl, L[cl] @ T.T
 
 
+def exposure(light_xyz):
+    """Per-chain colour scale 1 / max(X, Y, Z) of the light; 0 for a light
+    with no positive tristimulus value."""
+    m = np.asarray(light_xyz, dtype=np.float64).max(axis=1)
+    return np.where(m > 0.0, 1.0 / np.where(m > 0.0, m, 1.0), 0.0)
+
+
 def chain_delta_e(R, L, E, D, T, chain_light, chain_refl):
     """Per-depth Delta E of the latent chain against the spectral chain:
     dict with (depth, C) arrays 'de94', 'de2000' and per-depth lists of the
@@ -63,7 +75,7 @@ def chain_delta_e(R, L, E, D, T, chain_light, chain_refl):
     xs, xl, light_xyz = chain_xyz(R, L, E, D, T, chain_light, chain_refl)
     C, depth, _ = xs.shape
     white = np.asarray(T, dtype=np.float64).sum(axis=1)
-    scale = 1.0 / light_xyz[:, 1]
+    scale = exposure(light_xyz)
     de94 = np.empty((depth, C))
     de00 = np.empty((depth, C))
     for b in range(depth):

@@ -3,9 +3,9 @@
 // S(0) = L; the latent chain runs the same recurrence on codes with the
 // blockwise product (Eq. 5), z(b) = E R(b) (.) z(b-1), z(0) = E L.  Per chain
 // and depth both are projected to XYZ (T S(b) and M z(b), M = T D), scaled by
-// the light's luminance 1 / Y(T L), converted to CIELAB with the
-// equal-energy white T @ 1, and compared by CIE94 (spectral chain as
-// reference) and CIEDE2000.
+// 1 / max(T L) so that the light's largest tristimulus value is 1, converted
+// to CIELAB with the equal-energy white T @ 1, and compared by CIE94
+// (spectral chain as reference) and CIEDE2000.
 //
 // One thread per chain; the spectral chain walks the n samples once, carrying
 // the running product and the XYZ sums of every depth, the latent chain walks
@@ -103,10 +103,9 @@ __global__ void __launch_bounds__(128) chain_kernel(const ChainArgs a) {
       }
     }
   }
-  const bool dark = !(wy > 0.0f);  // a light with no luminance has no colour
-  const float inv = dark ? 0.0f : 1.0f / wy;
-  (void)wx;
-  (void)wz;
+  const float wmax = fmaxf(wx, fmaxf(wy, wz));
+  const bool dark = !(wmax > 0.0f);  // a light with no tristimulus response has no colour
+  const float inv = dark ? 0.0f : 1.0f / wmax;
 #pragma unroll
   for (int b = 0; b < kMaxDepth; ++b) {
     if (b < a.depth) {

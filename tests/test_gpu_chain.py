@@ -45,13 +45,15 @@ def test_chain_errors_match_oracle(env, k, grid_spec):
     cr = rng.integers(0, R.shape[0], (500, 3))
     d94, d00, st = _run(hsc, ctx, dev, R, L, E, D, grid_spec, cl, cr)
     ref = chain.chain_delta_e(R, L, E.astype(np.float64), D.astype(np.float64), cmf.cmf_weights(*grid_spec), cl, cr)
-    assert np.max(np.abs(d94 - ref["de94"])) < 5e-3
-    assert np.max(np.abs(d00 - ref["de2000"])) < 5e-3
+    # FP32 XYZ and Lab: 5e-3 absolute plus 1e-5 relative (a chain whose
+    # latent colour leaves the unit cube far behind has Delta E in the
+    # hundreds, where FP32 rounding alone reaches a few 1e-4)
+    tol = lambda r: 5e-3 + 1e-5 * np.abs(r)
+    assert np.all(np.abs(d94 - ref["de94"]) < tol(ref["de94"]))
+    assert np.all(np.abs(d00 - ref["de2000"]) < tol(ref["de2000"]))
     for b in range(3):
-        assert abs(st[b, 0] - ref["de94_mean"][b]) < 0.01
-        assert abs(st[b, 1] - ref["de94_p95"][b]) < 0.01
-        assert abs(st[b, 2] - ref["de2000_mean"][b]) < 0.01
-        assert abs(st[b, 3] - ref["de2000_p95"][b]) < 0.01
+        for j, key in enumerate(("de94_mean", "de94_p95", "de2000_mean", "de2000_p95")):
+            assert abs(st[b, j] - ref[key][b]) < 0.01 + 1e-5 * abs(ref[key][b]), (b, key)
         # the p95 is the exact nearest rank of the GPU's own values
         assert st[b, 3] == np.sort(d00[b])[int(np.ceil(0.95 * 500)) - 1]
 

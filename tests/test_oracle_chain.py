@@ -63,3 +63,27 @@ def test_brute_force_matches_vectorised():
     for c in range(2):
         bs, bl = chain.brute_force_chain_xyz(R, L, E, D, T, cl[c], cr[c])
         assert np.allclose(xs[c], bs, rtol=1e-13) and np.allclose(xl[c], bl, rtol=1e-13)
+
+
+def test_exposure_maps_light_peak_to_one_and_is_intensity_invariant():
+    R, L, T = _sets(n=31, seed=4)
+    lam = hi.grid(400.0, 10.0, 31)
+    # narrow bands at both ends of the grid have X or Z far above Y
+    L = np.concatenate([L, hi.narrowband(lam, [400.0, 700.0], [10.0, 10.0])])
+    light = L @ T.T
+    s = chain.exposure(light)
+    assert np.allclose((light * s[:, None]).max(axis=1), 1.0, rtol=1e-14)
+    assert chain.exposure(np.zeros((1, 3)))[0] == 0.0
+    rng = np.random.default_rng(9)
+    E = rng.uniform(0, 0.3, (6, 31))
+    D = rng.uniform(0, 0.5, (31, 6))
+    cl = rng.integers(0, L.shape[0], 40)
+    cr = rng.integers(0, R.shape[0], (40, 3))
+    a = chain.chain_delta_e(R, L, E, D, T, cl, cr)
+    b = chain.chain_delta_e(R, 7.5 * L, E, D, T, cl, cr)
+    assert np.allclose(a["de94"], b["de94"], rtol=1e-10, atol=1e-12)
+    assert np.allclose(a["de2000"], b["de2000"], rtol=1e-10, atol=1e-12)
+    # reflectances in [0, 1]: every scaled spectral colour stays inside the unit cube
+    xs, _, lx = chain.chain_xyz(R, L, E, D, T, cl, cr)
+    sc = chain.exposure(lx)
+    assert (xs * sc[:, None, None]).max() <= 1.0 + 1e-12

@@ -90,7 +90,9 @@ typedef enum { HSC_PASSES = 0, HSC_FUSED = 1 } hsc_mode;
 typedef struct {
   const float* normal;   /* device, P x 3 float32                                 */
   const float* pos;      /* device, P x 3 float32                                 */
-  const int32_t* mat;    /* device, P int32 in [0, n_mat); others set the error word */
+  const int32_t* mat;    /* device, P int32 in [0, n_mat); a pixel with an index
+                          * outside it (in either G-buffer) is shaded black and
+                          * sets the error word                                */
 } hsc_gbuffer;
 
 /* Point lights.                                                              */

@@ -46,21 +46,23 @@ __device__ __forceinline__ int find_frame(const BatchArgs& b, int64_t tile) {
 // Paired (f32x2) points need an even point count: a direct-only frame with
 // one pixel per thread falls back to the scalar form (same results).
 template <int KC, bool SEC, int PPT, int BLOCK, int VEC>
-__device__ __forceinline__ void run_tile(const ShadeArgs& a, int64_t local_tile, float4* s_light, bool restage,
-                                         bool staged) {
+__device__ __forceinline__ void run_tile(const ShadeArgs& a, int64_t local_tile, float4* s_light, float* s_M,
+                                         bool restage, bool staged) {
   constexpr int V = (VEC == 2 && !SEC && PPT == 1) ? 1 : VEC;
-  if (restage && staged) {
+  if (restage) {
     __syncthreads();
-    stage_light_codes<KC, V, BLOCK>(a, s_light, 0, a.L);
+    if (staged) stage_light_codes<KC, V, BLOCK>(a, s_light, 0, a.L);
+    stage_decode_matrix<KC, BLOCK>(a, s_M);
     __syncthreads();
   }
-  shade_tile<KC, PPT, SEC, BLOCK, V>(a, local_tile, s_light, staged);
+  shade_tile<KC, PPT, SEC, BLOCK, V>(a, local_tile, s_light, staged, s_M);
 }
 
 template <int PPT, int BLOCK, int VEC>
 __global__ void __launch_bounds__(BLOCK) shade_batch_kernel(const BatchArgs b) {
   extern __shared__ float4 s_light[];
   __shared__ int64_t s_tile;
+  __shared__ float s_M[3 * 9];
   int staged_frame = -1;
   for (;;) {
     if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(b.queue, 1u);
@@ -76,11 +78,11 @@ __global__ void __launch_bounds__(BLOCK) shade_batch_kernel(const BatchArgs b) {
     const bool staged = a.L <= kLightTile;
     const int64_t local = tile - fd.tile0;
     if (a.k == 6) {
-      if (fd.sec) run_tile<6, true, PPT, BLOCK, VEC>(a, local, s_light, restage, staged);
-      else run_tile<6, false, PPT, BLOCK, VEC>(a, local, s_light, restage, staged);
+      if (fd.sec) run_tile<6, true, PPT, BLOCK, VEC>(a, local, s_light, s_M, restage, staged);
+      else run_tile<6, false, PPT, BLOCK, VEC>(a, local, s_light, s_M, restage, staged);
     } else {
-      if (fd.sec) run_tile<9, true, PPT, BLOCK, VEC>(a, local, s_light, restage, staged);
-      else run_tile<9, false, PPT, BLOCK, VEC>(a, local, s_light, restage, staged);
+      if (fd.sec) run_tile<9, true, PPT, BLOCK, VEC>(a, local, s_light, s_M, restage, staged);
+      else run_tile<9, false, PPT, BLOCK, VEC>(a, local, s_light, s_M, restage, staged);
     }
     if (!staged) staged_frame = -1;  // the light tiles were streamed; restage next time
   }

@@ -62,14 +62,39 @@ __device__ __forceinline__ void stage_light_codes(const ShadeArgs& a, float4* s_
   }
 }
 
+// The KC code channels c0 .. c0+KC-1 of row `row` of a code table in its
+// storage format; one format test per row instead of per channel.
+template <int KC>
+__device__ __forceinline__ void load_code_row(const ShadeArgs& a, int row, float (&z)[KC]) {
+  const int64_t off = (int64_t)row * a.k + a.c0;
+  if (a.code_dt == HSC_F32) {
+    const float* q = reinterpret_cast<const float*>(a.mat_codes) + off;
+#pragma unroll
+    for (int c = 0; c < KC; ++c) z[c] = __ldg(q + c);
+  } else {
+    const unsigned short* q = reinterpret_cast<const unsigned short*>(a.mat_codes) + off;
+    unsigned short u[KC];
+#pragma unroll
+    for (int c = 0; c < KC; ++c) u[c] = __ldg(q + c);
+    if (a.code_dt == HSC_BF16) {
+#pragma unroll
+      for (int c = 0; c < KC; ++c) z[c] = __uint_as_float(((unsigned int)u[c]) << 16);
+    } else {
+#pragma unroll
+      for (int c = 0; c < KC; ++c) z[c] = __half2float(__ushort_as_half(u[c]));
+    }
+  }
+}
+
 // Shades one tile of BLOCK * PPT pixels: loads the shading points, sums every
 // light into KC accumulators per point, applies the blockwise product with the
-// material codes and the bounce, writes the latent channels (and XYZ, and
-// the fp8 channel maxima when asked).  When the lights fit one shared-memory
+// material codes and the bounce, writes the latent channels (and XYZ with the
+// decode matrix staged at s_M, and the fp8 channel maxima when asked).  When the lights fit one shared-memory
 // tile the caller has staged them already (`staged`); otherwise the light
 // tiles are staged here.  Must be called by every thread of the CTA.
 template <int KC, int PPT, bool SEC, int BLOCK, int VEC>
-__device__ __forceinline__ void shade_tile(const ShadeArgs& a, int64_t tile, float4* s_light, bool staged) {
+__device__ __forceinline__ void shade_tile(const ShadeArgs& a, int64_t tile, float4* s_light, bool staged,
+                                           const float* s_M) {
   constexpr int F4 = LightStage<KC, VEC>::F4;
   constexpr int NPT = PPT * (SEC ? 2 : 1);
   static_assert(VEC == 1 || NPT % 2 == 0, "paired points need an even point count");
@@ -113,12 +138,13 @@ __device__ __forceinline__ void shade_tile(const ShadeArgs& a, int64_t tile, flo
           stage(l0, nl);
           __syncthreads();
         }
-#pragma unroll 2
-        for (int l = 0; l < nl; ++l) {
+        const float4* sp = s_light;
+#pragma unroll 4
+        for (int l = 0; l < nl; ++l, sp += F4) {
           float v[F4 * 4];
 #pragma unroll
           for (int f = 0; f < F4; ++f) {
-            const float4 t = s_light[l * F4 + f];
+            const float4 t = sp[f];
             v[4 * f + 0] = t.x;
             v[4 * f + 1] = t.y;
             v[4 * f + 2] = t.z;
@@ -158,12 +184,13 @@ __device__ __forceinline__ void shade_tile(const ShadeArgs& a, int64_t tile, flo
           __syncthreads();
         }
         const ulonglong2* sl = reinterpret_cast<const ulonglong2*>(s_light);
-#pragma unroll 2
-        for (int l = 0; l < nl; ++l) {
+        const ulonglong2* sp = sl;
+#pragma unroll 4
+        for (int l = 0; l < nl; ++l, sp += F4) {
           f2 v[F4 * 2];
 #pragma unroll
           for (int f = 0; f < F4; ++f) {
-            const ulonglong2 t = sl[l * F4 + f];
+            const ulonglong2 t = sp[f];
             v[2 * f + 0] = t.x;
             v[2 * f + 1] = t.y;
           }
@@ -189,26 +216,29 @@ __device__ __forceinline__ void shade_tile(const ShadeArgs& a, int64_t tile, flo
       const int64_t p = pix[j];
       const bool valid = p < a.P;
       const int64_t pc = valid ? p : a.P - 1;
-      int m1 = __ldg(a.m1 + pc);
-      bool bad = (m1 < 0 || m1 >= a.n_mat);
+      // an out-of-range material index (primary or secondary) gives the
+      // pixel zero radiance and flags the error word
+      const int m1 = __ldg(a.m1 + pc);
+      bool bad = (unsigned)m1 >= (unsigned)a.n_mat;
       float zr1[KC], out[KC];
-#pragma unroll
-      for (int c = 0; c < KC; ++c) zr1[c] = bad ? 0.0f : load_code(a.mat_codes, a.code_dt, (int64_t)m1 * a.k + a.c0 + c);
+      load_code_row<KC>(a, bad ? 0 : m1, zr1);
       if (SEC) {
         const int m2 = __ldg(a.m2 + pc);
-        const bool bad2 = (m2 < 0 || m2 >= a.n_mat);
+        const bool bad2 = (unsigned)m2 >= (unsigned)a.n_mat;
         bad = bad || bad2;
+        float zr2[KC];
+        load_code_row<KC>(a, bad2 ? 0 : m2, zr2);
         const float h = bounce_term(px[j], py[j], pz[j], nx[j], ny[j], nz[j], px[PPT + j], py[PPT + j],
                                     pz[PPT + j], nx[PPT + j], ny[PPT + j], nz[PPT + j]);
 #pragma unroll
-        for (int c = 0; c < KC; ++c) {
-          const float zr2 = bad2 ? 0.0f : load_code(a.mat_codes, a.code_dt, (int64_t)m2 * a.k + a.c0 + c);
-          out[c] = __fmul_rn(zr1[c], __fmaf_rn(h, __fmul_rn(zr2, acc[PPT + j][c]), acc[j][c]));
-        }
+        for (int c = 0; c < KC; ++c)
+          out[c] = __fmul_rn(zr1[c], __fmaf_rn(h, __fmul_rn(zr2[c], acc[PPT + j][c]), acc[j][c]));
       } else {
 #pragma unroll
         for (int c = 0; c < KC; ++c) out[c] = __fmul_rn(zr1[c], acc[j][c]);
       }
+#pragma unroll
+      for (int c = 0; c < KC; ++c) out[c] = bad ? 0.0f : out[c];
       if (valid && bad) atomicOr(a.err, HSC_DEVERR_MATERIAL);
       if (valid) {
         if (a.out) {  // the batched launch may ask for XYZ only
@@ -221,7 +251,7 @@ __device__ __forceinline__ void shade_tile(const ShadeArgs& a, int64_t tile, flo
           for (int r = 0; r < 3; ++r) {
             float s = 0.0f;
 #pragma unroll
-            for (int c = 0; c < KC; ++c) s = __fmaf_rn(__ldg(a.M + r * a.k + c), out[c], s);
+            for (int c = 0; c < KC; ++c) s = __fmaf_rn(s_M[r * KC + c], out[c], s);
             a.xyz[3 * p + r] = s;
           }
         }
@@ -239,14 +269,36 @@ __device__ __forceinline__ void shade_tile(const ShadeArgs& a, int64_t tile, flo
   }
 }
 
+// Stages the 3 x KC decode matrix (channels c0 .. c0+KC-1 of M) for the
+// fused XYZ epilogue.
+template <int KC, int BLOCK>
+__device__ __forceinline__ void stage_decode_matrix(const ShadeArgs& a, float* s_M) {
+  if (a.xyz)
+    for (int i = threadIdx.x; i < 3 * KC; i += BLOCK) s_M[i] = __ldg(a.M + (i / KC) * a.k + a.c0 + (i % KC));
+}
+
+// Dynamic tile queue: queue[0] hands out tiles, queue[1] counts the CTAs that
+// have left the tile loop; the last one puts both back to zero, so the next
+// launch on the stream finds a fresh counter without a memset.
+__device__ __forceinline__ void release_queue(unsigned int* queue) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(queue + 1, 1u) == gridDim.x - 1) {
+      atomicExch(queue, 0u);
+      atomicExch(queue + 1, 0u);
+    }
+  }
+}
+
 template <int KC, int PPT, bool SEC, int BLOCK, int VEC>
 __global__ void __launch_bounds__(BLOCK) shade_codes_kernel(const ShadeArgs a) {
   extern __shared__ float4 s_light[];
+  __shared__ float s_M[3 * KC];
   const bool staged = a.L <= kLightTile;
-  if (staged) {
-    stage_light_codes<KC, VEC, BLOCK>(a, s_light, 0, a.L);
-    __syncthreads();
-  }
+  if (staged) stage_light_codes<KC, VEC, BLOCK>(a, s_light, 0, a.L);
+  stage_decode_matrix<KC, BLOCK>(a, s_M);
+  __syncthreads();
   if (a.queue) {
     // dynamic schedule: persistent CTAs take the next tile from a counter
     __shared__ int64_t s_next;
@@ -256,11 +308,12 @@ __global__ void __launch_bounds__(BLOCK) shade_codes_kernel(const ShadeArgs a) {
       const int64_t tile = s_next;
       __syncthreads();
       if (tile >= a.tiles) break;
-      shade_tile<KC, PPT, SEC, BLOCK, VEC>(a, tile, s_light, staged);
+      shade_tile<KC, PPT, SEC, BLOCK, VEC>(a, tile, s_light, staged, s_M);
     }
+    release_queue(a.queue);
   } else {
     for (int64_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x)
-      shade_tile<KC, PPT, SEC, BLOCK, VEC>(a, tile, s_light, staged);
+      shade_tile<KC, PPT, SEC, BLOCK, VEC>(a, tile, s_light, staged, s_M);
   }
 }
 
@@ -283,10 +336,9 @@ hsc_status launch_one(const ShadeArgs& a0, const LaunchCfg& cfg, cudaStream_t st
   // persistent CTAs on a dynamic tile queue.
   a.queue = nullptr;
   if (cfg.waves < 0) {
+    // the counter pair is zero at context creation and reset by the last CTA
     if (!cfg.queue) return set_error(HSC_ERR_INVALID_ARG, "dynamic schedule without a queue");
     a.queue = cfg.queue;
-    cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), stream);
-    if (e != cudaSuccess) return set_error(HSC_ERR_CUDA, "queue reset: %s", cudaGetErrorString(e));
   }
   int64_t grid = cfg.waves > 0 ? (int64_t)cfg.sm_count * occ * cfg.waves
                                : (cfg.waves < 0 ? (int64_t)cfg.sm_count * occ : a.tiles);

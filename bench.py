@@ -328,13 +328,35 @@ def _peak_sm_mhz():
         return 2070.0
 
 
+# Sources whose compiled code the fused shading launch runs; the committed
+# DRAM-traffic figure is used only while their hash matches the one recorded
+# with it (any change to the kernel makes the figure stale).
+TRAFFIC_SOURCES = ("paper_2602_18741_gb300/csrc/shade_latent_kernel.cuh",
+                   "paper_2602_18741_gb300/csrc/shade_latent.cuh",
+                   "paper_2602_18741_gb300/csrc/common.cuh",
+                   "paper_2602_18741_gb300/csrc/shade_latent_k6.cu")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(rel.encode() + b"\0" + fh.read())
+    return h.hexdigest()
+
+
 def _traffic_from_profile():
-    """DRAM bytes per launch of the fused shading kernel from the committed
-    ncu summary (profiles/shade_codes_fused_1080p.txt), or None."""
+    """DRAM bytes (read + write) per launch of the fused shading kernel from
+    the committed ncu summary profiles/shade_codes_fused_1080p.json, or None
+    when the kernel sources changed since it was captured."""
     p = os.path.join(ROOT, "profiles", "shade_codes_fused_1080p.json")
     try:
         with open(p) as fh:
-            return json.load(fh).get("dram_bytes_per_launch")
+            rec = json.load(fh)
+        if rec.get("source_sha256") != kernel_source_hash():
+            return None
+        return rec.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         return None
 

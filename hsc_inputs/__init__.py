@@ -287,6 +287,31 @@ def training_set(grid_spec, seed: int = MASTER_SEED + 100, n_smooth: int = 1024,
     return TrainingSet(R, L, pr, pl, ps)
 
 
+UPSAMPLER_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "upsampler")
+
+
+def upsampler_path(k: int, n: int) -> str:
+    return os.path.join(UPSAMPLER_DIR, f"upsampler_k{k}_n{n}.npz")
+
+
+def load_upsampler(k: int, n: int):
+    """Stored RGB-to-latent network for code length k over n samples: a dict
+    of float32 W1 (128, 3), b1, W2 (128, 128), b2, W3 (k, 128), b3.  Written by
+    the oracle's upsampler-fitting script."""
+    with np.load(upsampler_path(k, n)) as z:
+        return {name: z[name].astype(np.float32) for name in ("W1", "b1", "W2", "b2", "W3", "b3")}
+
+
+def rgb_palette(seed: int = MASTER_SEED + 6, grid_spec=GRID_81, count: int = 4096):
+    """Seeded reflectances standing in for the spectra behind an RGB texture:
+    smooth and saw-tooth spectra in the training set's proportions (the caller
+    takes their colours and codes)."""
+    r_s, r_t = streams(seed, 2)
+    lam = grid(*grid_spec)
+    n_saw = count // 9
+    return np.concatenate([smooth_reflectances(r_s, lam, count - n_saw), sawtooth_reflectances(r_t, lam, n_saw)])
+
+
 def codec_path(k: int, n: int) -> str:
     return os.path.join(CODEC_DIR, f"codec_k{k}_n{n}.npz")
 

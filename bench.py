@@ -489,9 +489,35 @@ def secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T,
     hsc.hsc_sync(ctx)
     rows.update(batch_rows(args, hsc, ctx, dev, timed))
     rows.update(chain_rows(args, hsc, ctx, dev, timed))
+    rows.update(upsample_rows(args, hsc, ctx, dev, timed))
     if args.serve_seconds > 0:
         rows.update(serve_rows(args, hsc, ctx, dev))
     return rows
+
+
+def upsample_rows(args, hsc, ctx, dev, timed):
+    """RGB-to-latent upsampling network (3 -> 128 -> 128 -> 6, SiLU) over a
+    3840x2160 texture of seeded uniform RGB values, fitted k = 6 weights."""
+    import torch
+    w = hi.load_upsampler(6, 81)
+    W = [torch.from_numpy(w[n]).to(dev) for n in ("W1", "b1", "W2", "b2", "W3", "b3")]
+    P = 3840 * 2160
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(hi.MASTER_SEED + 7)
+    rgb = torch.rand(P, 3, device=dev, generator=gen)
+    z = torch.empty(P, 6, device=dev)
+
+    def run():
+        hsc.hsc_upsample_rgb(ctx, rgb, *W, z)
+
+    ms, _ = timed(run, args.steps, args.warmup)
+    m = statistics.mean(ms)
+    flops = P * 2 * (3 * 128 + 128 * 128 + 128 * 6)          # algorithmic
+    mma_flops = P * 2 * (16 * 128 + 128 * 128 + 128 * 16)    # as issued (K and N padded to 16)
+    del rgb, z
+    return {"upsample_rgb_4k": {"ms": m, "Mpx_per_s": P / (m * 1e-3) / 1e6,
+                                "TFLOP_per_s": flops / (m * 1e-3) / 1e12,
+                                "tensor_TFLOP_per_s_issued": mma_flops / (m * 1e-3) / 1e12}}
 
 
 def serve_rows(args, hsc, ctx, dev):

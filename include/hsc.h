@@ -65,6 +65,7 @@ extern "C" {
 #define HSC_MAX_MAT (1 << 24)
 #define HSC_NOALLOC_MAX_K 96  /* channel limit of hsc_quantize_fp8_noalloc   */
 #define HSC_MAX_FRAMES_PER_CALL 512  /* frames per hsc_shade_frames call    */
+#define HSC_UPSAMPLE_HIDDEN 128      /* hidden width of the upsampling network */
 
 typedef struct hsc_ctx hsc_ctx;
 
@@ -328,15 +329,32 @@ HSC_API void hsc_batch_destroy(hsc_batch* batch);
  * unless hsc_force_launch_config overrides it.                              */
 HSC_API hsc_status hsc_shade_frames(hsc_ctx* ctx, const hsc_frame* frames, int count, void* stream);
 
+/* ------------------------------------------------------ RGB-to-latent upsampling */
+
+/* Latent upsampling from RGB (Sec. 4): per pixel a three-layer perceptron
+ *     h1 = silu(W1 c + b1),  h2 = silu(W2 h1 + b2),  z = W3 h2 + b3,
+ * silu(x) = x / (1 + exp(-x)), hidden width HSC_UPSAMPLE_HIDDEN (128).
+ *   rgb: device P x 3 float32 linear RGB;  W1: device 128 x 3, b1: 128,
+ *   W2: device 128 x 128 (row = output unit), b2: 128, W3: device k x 128,
+ *   b3: k, all float32;  z_out: device P x k float32;  1 <= k <= 16.
+ * Precision: the colour, the weights and both hidden activations are rounded
+ * to bf16 for the tensor cores, products accumulate in FP32, biases are FP32,
+ * and SiLU uses the hardware tanh approximation (silu(x) = x/2 (1 + tanh(x/2))).
+ * No scratch memory; asynchronous on `stream`.                              */
+HSC_API hsc_status hsc_upsample_rgb(hsc_ctx* ctx, const float* rgb, int64_t pixels, const float* W1,
+                                    const float* b1, const float* W2, const float* b2, const float* W3,
+                                    const float* b3, int k, float* z_out, void* stream);
+
 /* --------------------------------------------------------- multi-bounce chains */
 
 /* Multi-bounce chains, the codec-selection proxy of Sec. 3.5: chain c starts
  * from light chain_light[c] and multiplies in reflectance chain_refl[c][b] at
  * bounce b (S(b) = R (.) S(b-1)); the latent chain runs the same recurrence on
  * codes with the blockwise product (Eq. 5).  At every depth both are taken to
- * XYZ (T S and M z with M = T D), scaled by the light's luminance 1 / Y(T L),
- * converted to CIELAB with the equal-energy white T @ 1, and compared by
- * CIE94 (spectral chain as reference) and CIEDE2000.
+ * XYZ (T S and M z with M = T D), scaled by 1 / max(T L) so the light's
+ * largest tristimulus value is 1, converted to CIELAB with the equal-energy
+ * white T @ 1, and compared by CIE94 (spectral chain as reference) and
+ * CIEDE2000.
  *   refl: device n_refl x n;  lights: device n_lights x n;  E: k x n;  D: n x k;
  *   T: 3 x n (hsc_cmf_weights);  chain_light: device chains int32;
  *   chain_refl: device chains x depth int32 (depth <= 8);

@@ -95,6 +95,7 @@ _SIGS = {
     "hsc_delta_e": ([_vp, _vp, _vp, _i64, _vp, _i32, _vp, _vp, _vp], _i32),
     "hsc_chain_eval": ([_vp, _vp, _i32, _vp, _i32, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp],
                        _i32),
+    "hsc_upsample_rgb": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp], _i32),
     "hsc_batch_create": ([_vp, ctypes.POINTER(_Frame), _i32, ctypes.POINTER(_vp)], _i32),
     "hsc_batch_shade": ([_vp, _vp, _vp], _i32),
     "hsc_batch_destroy": ([_vp], None),
@@ -422,6 +423,21 @@ def hsc_shade_frames(ctx: Context, frames: Sequence[BatchFrame], stream=None):
     """Asynchronous one-shot batched launch (continuous batching)."""
     arr = (_Frame * len(frames))(*[f.s for f in frames])
     _check(_lib.hsc_shade_frames(ctx.handle, arr, len(frames), _stream(stream)))
+
+
+def hsc_upsample_rgb(ctx: Context, rgb: torch.Tensor, W1: torch.Tensor, b1: torch.Tensor, W2: torch.Tensor,
+                     b2: torch.Tensor, W3: torch.Tensor, b3: torch.Tensor, z_out: torch.Tensor, stream=None):
+    """RGB-to-latent upsampling network (Sec. 4); see include/hsc.h."""
+    P = rgb.shape[0]
+    k = W3.shape[0]
+    if rgb.shape != (P, 3) or W1.shape != (128, 3) or W2.shape != (128, 128) or W3.shape != (k, 128) \
+            or b1.shape != (128,) or b2.shape != (128,) or b3.shape != (k,) or z_out.shape != (P, k):
+        raise ValueError("shapes: rgb (P,3), W1 (128,3), W2 (128,128), W3 (k,128), biases, z_out (P,k)")
+    for t in (rgb, W1, b1, W2, b2, W3, b3, z_out):
+        if t.dtype != torch.float32:
+            raise ValueError("all tensors must be float32")
+    _check(_lib.hsc_upsample_rgb(ctx.handle, _ptr(rgb), int(P), _ptr(W1), _ptr(b1), _ptr(W2), _ptr(b2), _ptr(W3),
+                                 _ptr(b3), int(k), _ptr(z_out), _stream(stream)))
 
 
 def hsc_chain_eval(ctx: Context, refl: torch.Tensor, lights: torch.Tensor, E: torch.Tensor, D: torch.Tensor,

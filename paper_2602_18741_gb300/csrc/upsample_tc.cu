@@ -1,0 +1,292 @@
+// RGB-to-latent upsampling (Sec. 4): per pixel a three-layer perceptron,
+//     h1 = silu(W1 c + b1),  h2 = silu(W2 h1 + b2),  z = W3 h2 + b3,
+// hidden width 128, on the 5th-generation tensor cores.
+//
+// A CTA of 128 threads takes tiles of 128 pixels (thread t owns pixel row t,
+// which is also TMEM lane t).  Per tile three BF16 MMAs with FP32
+// accumulation run in sequence, each issued by one thread and committed to an
+// mbarrier:
+//   layer 1: [128 x 16] x [16 x 128]   (the colour in K columns 0..2),
+//   layer 2: [128 x 128] x [128 x 128] (eight K = 16 steps),
+//   layer 3: [128 x 128] x [128 x 16]  (k <= 16 outputs, zero-padded).
+// Between them every thread reads its accumulator row from TMEM (tcgen05.ld),
+// adds the bias, applies SiLU as 0.5 x (1 + tanh(x / 2)) with the hardware
+// tanh approximation, rounds to bf16 and writes the row into the next
+// layer's A operand in shared memory (no-swizzle K-major layout).  The
+// weights are converted to bf16 and staged once per CTA.  Two CTAs share an
+// SM (256 TMEM columns each), so one CTA's MMAs overlap the other's
+// epilogues.  Every mbarrier wait is bounded; on expiry the kernel sets the
+// timeout bit, frees its TMEM and returns.
+#include "common.cuh"
+#include "tcgen05.cuh"
+
+namespace hsc {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kUpThreads = 128;
+constexpr int kUpRows = 128;            // MMA M, pixels per tile
+constexpr int kHidden = HSC_UPSAMPLE_HIDDEN;
+constexpr int kKBlocks = kHidden / 16;  // K = 16 steps of the hidden layers
+constexpr unsigned kUpTmemCols = 256;   // [0, 128): layers 1 and 2; [128, 144): layer 3
+constexpr int kBlockBytes = kUpRows * 16 * 2;  // one [128 x 16] bf16 K-block
+
+struct UpArgs {
+  const float* rgb;  // P x 3
+  int64_t P;
+  const float* W1;   // 128 x 3
+  const float* b1;
+  const float* W2;   // 128 x 128
+  const float* b2;
+  const float* W3;   // k x 128
+  const float* b3;
+  int k;
+  float* z;          // P x k
+  unsigned int* err;
+};
+
+// Shared-memory plan (offsets from a 1024-byte aligned base).
+constexpr int kOffW1 = 0;                                  // [128 x 16] bf16
+constexpr int kOffW2 = kOffW1 + kBlockBytes;               // 8 x [128 x 16]
+constexpr int kOffW3 = kOffW2 + kKBlocks * kBlockBytes;    // 8 x [16 x 16]
+constexpr int kOffA1 = kOffW3 + kKBlocks * 512;            // [128 x 16]
+constexpr int kOffH = kOffA1 + kBlockBytes;                // 8 x [128 x 16]
+constexpr int kOffBias = kOffH + kKBlocks * kBlockBytes;   // b1, b2 (128 each), b3 (16)
+constexpr int kOffBar = kOffBias + (2 * kHidden + 16) * 4;
+constexpr int kUpSmem = kOffBar + 64 + 1024;               // + alignment slack
+
+__device__ __forceinline__ float tanh_approx(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float silu_tc(float x) {
+  const float h = __fmul_rn(0.5f, x);
+  return __fmaf_rn(h, tanh_approx(h), h);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+         ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+}
+
+__device__ __forceinline__ void issue_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          int accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Hand the shared-memory writes of every thread to the tensor core and order
+// them before the MMA issued after the barrier.
+__device__ __forceinline__ void smem_to_mma_barrier() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Thread 0 waits for the committed MMAs; everyone learns whether they ended.
+__device__ __forceinline__ bool wait_mma(uint32_t bar, uint32_t& phase, int* sOk, unsigned int* err) {
+  if (threadIdx.x == 0 && !mbar_wait(bar, phase)) {
+    *sOk = 0;
+    atomicOr(err, HSC_DEVERR_TIMEOUT);
+  }
+  __syncthreads();
+  phase ^= 1u;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  return *sOk != 0;
+}
+
+// Reads this thread's 128 accumulator columns, applies bias + SiLU, and writes
+// the bf16 row into the A operand `sH` (eight K = 16 blocks).
+__device__ __forceinline__ void hidden_epilogue(uint32_t trow, const float* bias, unsigned char* sH, int row) {
+#pragma unroll
+  for (int c0 = 0; c0 < kHidden; c0 += 32) {
+    uint32_t v[32];
+    TC_LD16(trow + (uint32_t)c0, v);
+    TC_LD16(trow + (uint32_t)(c0 + 16), (v + 16));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {  // 8 columns = 16 bytes of one core-matrix row
+      uint32_t w[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = c0 + 8 * h + 2 * q;
+        const float x0 = silu_tc(__fadd_rn(__uint_as_float(v[8 * h + 2 * q]), bias[c]));
+        const float x1 = silu_tc(__fadd_rn(__uint_as_float(v[8 * h + 2 * q + 1]), bias[c + 1]));
+        w[q] = pack_bf16x2(x0, x1);
+      }
+      const int col = c0 + 8 * h;
+      *reinterpret_cast<uint4*>(sH + (col >> 4) * kBlockBytes + kmajor_off(row, col & 15)) =
+          make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kUpThreads) upsample_tc_kernel(const UpArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* sW1 = base + kOffW1;
+  unsigned char* sW2 = base + kOffW2;
+  unsigned char* sW3 = base + kOffW3;
+  unsigned char* sA1 = base + kOffA1;
+  unsigned char* sH = base + kOffH;
+  float* sB1 = reinterpret_cast<float*>(base + kOffBias);
+  float* sB2 = sB1 + kHidden;
+  float* sB3 = sB2 + kHidden;
+  uint64_t* sBar = reinterpret_cast<uint64_t*>(base + kOffBar);
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(sBar + 1);
+  int* sOk = reinterpret_cast<int*>(sTmem + 1);
+
+  const int t = threadIdx.x;
+  const int warp = t >> 5;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(sTmem)),
+                 "r"(kUpTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(sBar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *sOk = 1;
+  }
+  // weights as bf16 B operands ([N x K], K-major), biases as FP32
+  for (int idx = t; idx < kHidden * 16; idx += kUpThreads) {
+    const int r = idx >> 4, e = idx & 15;
+    const float v = e < 3 ? __ldg(a.W1 + r * 3 + e) : 0.0f;
+    *reinterpret_cast<__nv_bfloat16*>(sW1 + kmajor_off(r, e)) = __float2bfloat16_rn(v);
+  }
+  for (int idx = t; idx < kHidden * kHidden; idx += kUpThreads) {
+    const int r = idx / kHidden, i = idx - r * kHidden;
+    *reinterpret_cast<__nv_bfloat16*>(sW2 + (i >> 4) * kBlockBytes + kmajor_off(r, i & 15)) =
+        __float2bfloat16_rn(__ldg(a.W2 + idx));
+  }
+  for (int idx = t; idx < 16 * kHidden; idx += kUpThreads) {
+    const int r = idx / kHidden, i = idx - r * kHidden;
+    const float v = r < a.k ? __ldg(a.W3 + r * kHidden + i) : 0.0f;
+    *reinterpret_cast<__nv_bfloat16*>(sW3 + (i >> 4) * 512 + kmajor_off(r, i & 15)) = __float2bfloat16_rn(v);
+  }
+  for (int idx = t; idx < kHidden; idx += kUpThreads) {
+    sB1[idx] = __ldg(a.b1 + idx);
+    sB2[idx] = __ldg(a.b2 + idx);
+  }
+  if (t < 16) sB3[t] = t < a.k ? __ldg(a.b3 + t) : 0.0f;
+  // the A1 row's K columns 8..15 stay zero
+  *reinterpret_cast<uint4*>(sA1 + kmajor_off(t, 8)) = make_uint4(0u, 0u, 0u, 0u);
+  smem_to_mma_barrier();
+
+  const uint32_t tmem = *sTmem;
+  const uint32_t bar = smem_u32(sBar);
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's 32 lanes
+  const uint32_t id_hidden = instr_desc_bf16(kUpRows, kHidden);
+  const uint32_t id_out = instr_desc_bf16(kUpRows, 16);
+  uint32_t phase = 0;
+
+  const int64_t tiles = (a.P + kUpRows - 1) / kUpRows;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t p = tile * kUpRows + t;
+    const bool valid = p < a.P;
+    // layer 1 A row: the colour in bf16, K columns 0..2
+    {
+      const float r = valid ? __ldg(a.rgb + 3 * p) : 0.0f;
+      const float g = valid ? __ldg(a.rgb + 3 * p + 1) : 0.0f;
+      const float b = valid ? __ldg(a.rgb + 3 * p + 2) : 0.0f;
+      *reinterpret_cast<uint4*>(sA1 + kmajor_off(t, 0)) = make_uint4(pack_bf16x2(r, g), pack_bf16x2(b, 0.0f), 0u, 0u);
+    }
+    smem_to_mma_barrier();
+    if (t == 0) {
+      issue_mma(tmem, smem_desc(smem_u32(sA1), 128, 256), smem_desc(smem_u32(sW1), 128, 256), id_hidden, 0);
+      commit(bar);
+    }
+    if (!wait_mma(bar, phase, sOk, a.err)) break;
+    hidden_epilogue(trow, sB1, sH, t);
+    smem_to_mma_barrier();
+    if (t == 0) {
+#pragma unroll
+      for (int kb = 0; kb < kKBlocks; ++kb)
+        issue_mma(tmem, smem_desc(smem_u32(sH + kb * kBlockBytes), 128, 256),
+                  smem_desc(smem_u32(sW2 + kb * kBlockBytes), 128, 256), id_hidden, kb > 0);
+      commit(bar);
+    }
+    if (!wait_mma(bar, phase, sOk, a.err)) break;
+    hidden_epilogue(trow, sB2, sH, t);  // h2 replaces h1 (layer 2 has finished reading it)
+    smem_to_mma_barrier();
+    if (t == 0) {
+#pragma unroll
+      for (int kb = 0; kb < kKBlocks; ++kb)
+        issue_mma(tmem + 128u, smem_desc(smem_u32(sH + kb * kBlockBytes), 128, 256),
+                  smem_desc(smem_u32(sW3 + kb * 512), 128, 256), id_out, kb > 0);
+      commit(bar);
+    }
+    if (!wait_mma(bar, phase, sOk, a.err)) break;
+    uint32_t v[16];
+    TC_LD16(trow + 128u, v);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (valid) {
+      float* zo = a.z + p * a.k;
+#pragma unroll
+      for (int o = 0; o < 16; ++o)
+        if (o < a.k) zo[o] = __fadd_rn(__uint_as_float(v[o]), sB3[o]);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kUpTmemCols) : "memory");
+  }
+}
+
+}  // namespace
+
+}  // namespace hsc
+
+extern "C" hsc_status hsc_upsample_rgb(hsc_ctx* ctx, const float* rgb, int64_t pixels, const float* W1,
+                                       const float* b1, const float* W2, const float* b2, const float* W3,
+                                       const float* b3, int k, float* z_out, void* stream) {
+  hsc::clear_error();
+  HSC_CHECK_CTX(ctx);
+  HSC_REQUIRE(pixels >= 0, "negative pixel count");
+  HSC_REQUIRE(k >= 1 && k <= 16, "k=%d out of range [1, 16]", k);
+  HSC_REQUIRE(W1 && b1 && W2 && b2 && W3 && b3, "null weight pointer");
+  if (pixels == 0) return HSC_OK;
+  HSC_REQUIRE(rgb && z_out, "null pointer");
+  HSC_REQUIRE(hsc::aligned(rgb, 4) && hsc::aligned(z_out, 4) && hsc::aligned(W1, 4) && hsc::aligned(W2, 4) &&
+                  hsc::aligned(W3, 4),
+              "misaligned pointer");
+  HSC_GUARD(ctx);
+  hsc::UpArgs a{};
+  a.rgb = rgb;
+  a.P = pixels;
+  a.W1 = W1;
+  a.b1 = b1;
+  a.W2 = W2;
+  a.b2 = b2;
+  a.W3 = W3;
+  a.b3 = b3;
+  a.k = k;
+  a.z = z_out;
+  a.err = ctx->d_err;
+  cudaStream_t s = hsc::as_stream(stream);
+  auto kern = hsc::upsample_tc_kernel;
+  HSC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, hsc::kUpSmem));
+  const int64_t tiles = (pixels + hsc::kUpRows - 1) / hsc::kUpRows;
+  int64_t grid = (int64_t)ctx->sm_count * 2;  // two CTAs per SM (TMEM: 2 x 256 columns)
+  if (grid > tiles) grid = tiles;
+  kern<<<(unsigned)grid, hsc::kUpThreads, hsc::kUpSmem, s>>>(a);
+  return hsc::check_launch("upsample_tc_kernel");
+}

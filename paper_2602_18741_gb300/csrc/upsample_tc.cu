@@ -2,21 +2,26 @@
 //     h1 = silu(W1 c + b1),  h2 = silu(W2 h1 + b2),  z = W3 h2 + b3,
 // hidden width 128, on the 5th-generation tensor cores.
 //
-// A CTA of 128 threads takes tiles of 128 pixels (thread t owns pixel row t,
-// which is also TMEM lane t).  Per tile three BF16 MMAs with FP32
-// accumulation run in sequence, each issued by one thread and committed to an
-// mbarrier:
+// A CTA of 512 threads takes tiles of 128 pixels.  Per tile three BF16 MMAs
+// with FP32 accumulation run in sequence, each issued by one thread and
+// committed to an mbarrier:
 //   layer 1: [128 x 16] x [16 x 128]   (the colour in K columns 0..2),
 //   layer 2: [128 x 128] x [128 x 128] (eight K = 16 steps),
 //   layer 3: [128 x 128] x [128 x 16]  (k <= 16 outputs, zero-padded).
-// Between them every thread reads its accumulator row from TMEM (tcgen05.ld),
-// adds the bias, applies SiLU as 0.5 x (1 + tanh(x / 2)) with the hardware
-// tanh approximation, rounds to bf16 and writes the row into the next
-// layer's A operand in shared memory (no-swizzle K-major layout).  The
-// weights are converted to bf16 and staged once per CTA.  Two CTAs share an
-// SM (256 TMEM columns each), so one CTA's MMAs overlap the other's
-// epilogues.  Every mbarrier wait is bounded; on expiry the kernel sets the
-// timeout bit, frees its TMEM and returns.
+// Between them the epilogue runs on all 16 warps: pixel row r is TMEM lane r,
+// read by the four warps of lane quadrant r / 32, each for 32 of the 128
+// hidden columns (tcgen05.ld); a thread adds the bias, applies SiLU as
+// x/2 (1 + tanh(x/2)) with the hardware tanh approximation, rounds to bf16
+// and writes its 32 values into the next layer's A operand in shared memory
+// (no-swizzle K-major layout).  The weights are converted to bf16 and staged
+// once per CTA.  One CTA per SM works on two tiles at once (two A buffers,
+// two 256-column TMEM regions, one mbarrier each) in the order
+//   MMA1(a) MMA1(b) | epi1(a) MMA2(a) | epi1(b) MMA2(b) | epi2(a) MMA3(a) |
+//   epi2(b) MMA3(b) | out(a) out(b),
+// so each tile's tensor-core work runs while the other tile's epilogue runs;
+// the next pair's colours are loaded while the first layer runs.  Every
+// mbarrier wait is bounded; on expiry the kernel sets the timeout bit, frees
+// its TMEM and returns.
 #include "common.cuh"
 #include "tcgen05.cuh"
 
@@ -26,11 +31,11 @@ namespace {
 
 using namespace tc;
 
-constexpr int kUpThreads = 128;
+constexpr int kUpThreads = 512;
 constexpr int kUpRows = 128;            // MMA M, pixels per tile
 constexpr int kHidden = HSC_UPSAMPLE_HIDDEN;
 constexpr int kKBlocks = kHidden / 16;  // K = 16 steps of the hidden layers
-constexpr unsigned kUpTmemCols = 256;   // [0, 128): layers 1 and 2; [128, 144): layer 3
+constexpr unsigned kUpTmemCols = 512;   // per tile slot s: [256 s, +128) layers 1-2, [256 s + 128, +16) layer 3
 constexpr int kBlockBytes = kUpRows * 16 * 2;  // one [128 x 16] bf16 K-block
 
 struct UpArgs {
@@ -51,10 +56,11 @@ struct UpArgs {
 constexpr int kOffW1 = 0;                                  // [128 x 16] bf16
 constexpr int kOffW2 = kOffW1 + kBlockBytes;               // 8 x [128 x 16]
 constexpr int kOffW3 = kOffW2 + kKBlocks * kBlockBytes;    // 8 x [16 x 16]
-constexpr int kOffA1 = kOffW3 + kKBlocks * 512;            // [128 x 16]
-constexpr int kOffH = kOffA1 + kBlockBytes;                // 8 x [128 x 16]
-constexpr int kOffBias = kOffH + kKBlocks * kBlockBytes;   // b1, b2 (128 each), b3 (16)
-constexpr int kOffBar = kOffBias + (2 * kHidden + 16) * 4;
+constexpr int kOffA1 = kOffW3 + kKBlocks * 512;            // 2 slots x [128 x 16]
+constexpr int kOffH = kOffA1 + 2 * kBlockBytes;            // 2 slots x 8 x [128 x 16]
+constexpr int kSlotH = kKBlocks * kBlockBytes;
+constexpr int kOffBias = kOffH + 2 * kSlotH;               // b1, b2 (128 each), b3 (16)
+constexpr int kOffBar = kOffBias + (2 * kHidden + 16) * 4; // two mbarriers, TMEM address, status
 constexpr int kUpSmem = kOffBar + 64 + 1024;               // + alignment slack
 
 __device__ __forceinline__ float tanh_approx(float x) {
@@ -69,8 +75,8 @@ __device__ __forceinline__ float silu_tc(float x) {
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
-         ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x = lo (low half)
+  return *reinterpret_cast<const uint32_t*>(&v);
 }
 
 __device__ __forceinline__ void issue_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -107,33 +113,34 @@ __device__ __forceinline__ bool wait_mma(uint32_t bar, uint32_t& phase, int* sOk
   return *sOk != 0;
 }
 
-// Reads this thread's 128 accumulator columns, applies bias + SiLU, and writes
-// the bf16 row into the A operand `sH` (eight K = 16 blocks).
-__device__ __forceinline__ void hidden_epilogue(uint32_t trow, const float* bias, unsigned char* sH, int row) {
+// Reads accumulator columns c0 .. c0+31 of this thread's TMEM lane, applies
+// bias + SiLU, and writes them as bf16 into row `row` of the A operand `sH`
+// (eight K = 16 blocks).
+__device__ __forceinline__ void hidden_epilogue(uint32_t trow, int c0, const float* bias, unsigned char* sH,
+                                                int row) {
+  uint32_t v[32];
+  TC_LD16(trow + (uint32_t)c0, v);
+  TC_LD16(trow + (uint32_t)(c0 + 16), (v + 16));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int c0 = 0; c0 < kHidden; c0 += 32) {
-    uint32_t v[32];
-    TC_LD16(trow + (uint32_t)c0, v);
-    TC_LD16(trow + (uint32_t)(c0 + 16), (v + 16));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  for (int h = 0; h < 4; ++h) {  // 8 columns = 16 bytes of one core-matrix row
+    const float4 bl = *reinterpret_cast<const float4*>(bias + c0 + 8 * h);
+    const float4 bh = *reinterpret_cast<const float4*>(bias + c0 + 8 * h + 4);
+    const float bb[8] = {bl.x, bl.y, bl.z, bl.w, bh.x, bh.y, bh.z, bh.w};
+    uint32_t w[4];
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {  // 8 columns = 16 bytes of one core-matrix row
-      uint32_t w[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int c = c0 + 8 * h + 2 * q;
-        const float x0 = silu_tc(__fadd_rn(__uint_as_float(v[8 * h + 2 * q]), bias[c]));
-        const float x1 = silu_tc(__fadd_rn(__uint_as_float(v[8 * h + 2 * q + 1]), bias[c + 1]));
-        w[q] = pack_bf16x2(x0, x1);
-      }
-      const int col = c0 + 8 * h;
-      *reinterpret_cast<uint4*>(sH + (col >> 4) * kBlockBytes + kmajor_off(row, col & 15)) =
-          make_uint4(w[0], w[1], w[2], w[3]);
+    for (int q = 0; q < 4; ++q) {
+      const float x0 = silu_tc(__fadd_rn(__uint_as_float(v[8 * h + 2 * q]), bb[2 * q]));
+      const float x1 = silu_tc(__fadd_rn(__uint_as_float(v[8 * h + 2 * q + 1]), bb[2 * q + 1]));
+      w[q] = pack_bf16x2(x0, x1);
     }
+    const int col = c0 + 8 * h;
+    *reinterpret_cast<uint4*>(sH + (col >> 4) * kBlockBytes + kmajor_off(row, col & 15)) =
+        make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
-__global__ void __launch_bounds__(kUpThreads) upsample_tc_kernel(const UpArgs a) {
+__global__ void __launch_bounds__(kUpThreads, 1) upsample_tc_kernel(const UpArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -145,8 +152,8 @@ __global__ void __launch_bounds__(kUpThreads) upsample_tc_kernel(const UpArgs a)
   float* sB1 = reinterpret_cast<float*>(base + kOffBias);
   float* sB2 = sB1 + kHidden;
   float* sB3 = sB2 + kHidden;
-  uint64_t* sBar = reinterpret_cast<uint64_t*>(base + kOffBar);
-  uint32_t* sTmem = reinterpret_cast<uint32_t*>(sBar + 1);
+  uint64_t* sBar = reinterpret_cast<uint64_t*>(base + kOffBar);  // [2]
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(sBar + 2);
   int* sOk = reinterpret_cast<int*>(sTmem + 1);
 
   const int t = threadIdx.x;
@@ -160,6 +167,7 @@ __global__ void __launch_bounds__(kUpThreads) upsample_tc_kernel(const UpArgs a)
   }
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(sBar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(sBar + 1)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *sOk = 1;
   }
@@ -184,70 +192,108 @@ __global__ void __launch_bounds__(kUpThreads) upsample_tc_kernel(const UpArgs a)
     sB2[idx] = __ldg(a.b2 + idx);
   }
   if (t < 16) sB3[t] = t < a.k ? __ldg(a.b3 + t) : 0.0f;
-  // the A1 row's K columns 8..15 stay zero
-  *reinterpret_cast<uint4*>(sA1 + kmajor_off(t, 8)) = make_uint4(0u, 0u, 0u, 0u);
-  smem_to_mma_barrier();
 
-  const uint32_t tmem = *sTmem;
-  const uint32_t bar = smem_u32(sBar);
-  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's 32 lanes
+  const int quad = warp & 3;                 // TMEM lane quadrant of this warp
+  const int row = quad * 32 + (t & 31);      // pixel row = TMEM lane
+  const int c0 = (warp >> 2) * 32;           // this thread's 32 hidden columns
   const uint32_t id_hidden = instr_desc_bf16(kUpRows, kHidden);
   const uint32_t id_out = instr_desc_bf16(kUpRows, 16);
-  uint32_t phase = 0;
+  uint32_t phase[2] = {0u, 0u};
 
+  // Threads 0..255 feed the colours: thread t loads row t & 127 of slot t >> 7.
+  const int feed_slot = t >> 7, feed_row = t & 127;
   const int64_t tiles = (a.P + kUpRows - 1) / kUpRows;
-  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const int64_t p = tile * kUpRows + t;
-    const bool valid = p < a.P;
-    // layer 1 A row: the colour in bf16, K columns 0..2
-    {
-      const float r = valid ? __ldg(a.rgb + 3 * p) : 0.0f;
-      const float g = valid ? __ldg(a.rgb + 3 * p + 1) : 0.0f;
-      const float b = valid ? __ldg(a.rgb + 3 * p + 2) : 0.0f;
-      *reinterpret_cast<uint4*>(sA1 + kmajor_off(t, 0)) = make_uint4(pack_bf16x2(r, g), pack_bf16x2(b, 0.0f), 0u, 0u);
-    }
-    smem_to_mma_barrier();
-    if (t == 0) {
-      issue_mma(tmem, smem_desc(smem_u32(sA1), 128, 256), smem_desc(smem_u32(sW1), 128, 256), id_hidden, 0);
-      commit(bar);
-    }
-    if (!wait_mma(bar, phase, sOk, a.err)) break;
-    hidden_epilogue(trow, sB1, sH, t);
-    smem_to_mma_barrier();
-    if (t == 0) {
+  const int64_t pairs = (tiles + 1) / 2;
+  float cr = 0.0f, cg = 0.0f, cb = 0.0f;
+  auto load_colour = [&](int64_t pair) {
+    const int64_t p = (2 * pair + feed_slot) * kUpRows + feed_row;
+    const bool ok = t < 2 * kUpRows && pair < pairs && p < a.P;
+    cr = ok ? __ldg(a.rgb + 3 * p) : 0.0f;
+    cg = ok ? __ldg(a.rgb + 3 * p + 1) : 0.0f;
+    cb = ok ? __ldg(a.rgb + 3 * p + 2) : 0.0f;
+  };
+  load_colour(blockIdx.x);
+  if (t < 2 * kUpRows)  // the A1 rows' K columns 8..15 stay zero
+    *reinterpret_cast<uint4*>(sA1 + feed_slot * kBlockBytes + kmajor_off(feed_row, 8)) = make_uint4(0u, 0u, 0u, 0u);
+  smem_to_mma_barrier();
+  const uint32_t tm = *sTmem;  // TMEM base address, published by the barrier above
+
+  auto trow = [&](int slot) { return tm + (uint32_t)(256 * slot) + ((uint32_t)(quad * 32) << 16); };
+  auto wait = [&](int slot) { return wait_mma(smem_u32(sBar + slot), phase[slot], sOk, a.err); };
+  auto mma_hidden = [&](int slot, int layer) {  // layer 1 or 2 into the slot's first 128 columns
+    const uint32_t d = tm + (uint32_t)(256 * slot);
+    if (layer == 1) {
+      issue_mma(d, smem_desc(smem_u32(sA1 + slot * kBlockBytes), 128, 256), smem_desc(smem_u32(sW1), 128, 256),
+                id_hidden, 0);
+    } else {
 #pragma unroll
       for (int kb = 0; kb < kKBlocks; ++kb)
-        issue_mma(tmem, smem_desc(smem_u32(sH + kb * kBlockBytes), 128, 256),
+        issue_mma(d, smem_desc(smem_u32(sH + slot * kSlotH + kb * kBlockBytes), 128, 256),
                   smem_desc(smem_u32(sW2 + kb * kBlockBytes), 128, 256), id_hidden, kb > 0);
-      commit(bar);
     }
-    if (!wait_mma(bar, phase, sOk, a.err)) break;
-    hidden_epilogue(trow, sB2, sH, t);  // h2 replaces h1 (layer 2 has finished reading it)
+    commit(smem_u32(sBar + slot));
+  };
+  auto mma_out = [&](int slot) {
+    const uint32_t d = tm + (uint32_t)(256 * slot + 128);
+#pragma unroll
+    for (int kb = 0; kb < kKBlocks; ++kb)
+      issue_mma(d, smem_desc(smem_u32(sH + slot * kSlotH + kb * kBlockBytes), 128, 256),
+                smem_desc(smem_u32(sW3 + kb * 512), 128, 256), id_out, kb > 0);
+    commit(smem_u32(sBar + slot));
+  };
+  auto out = [&](int slot, int64_t pair) {
+    if (warp < 4) {  // the layer-3 columns, one warp per lane quadrant
+      uint32_t v[16];
+      TC_LD16(trow(slot) + 128u, v);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      const int64_t p = (2 * pair + slot) * kUpRows + row;
+      if (p < a.P) {
+        float* zo = a.z + p * a.k;
+#pragma unroll
+        for (int o = 0; o < 16; ++o)
+          if (o < a.k) zo[o] = __fadd_rn(__uint_as_float(v[o]), sB3[o]);
+      }
+    }
+  };
+
+  for (int64_t pair = blockIdx.x; pair < pairs; pair += gridDim.x) {
+    // layer 1 A rows of both slots: the colours in bf16, K columns 0..2
+    if (t < 2 * kUpRows)
+      *reinterpret_cast<uint4*>(sA1 + feed_slot * kBlockBytes + kmajor_off(feed_row, 0)) =
+          make_uint4(pack_bf16x2(cr, cg), pack_bf16x2(cb, 0.0f), 0u, 0u);
     smem_to_mma_barrier();
     if (t == 0) {
-#pragma unroll
-      for (int kb = 0; kb < kKBlocks; ++kb)
-        issue_mma(tmem + 128u, smem_desc(smem_u32(sH + kb * kBlockBytes), 128, 256),
-                  smem_desc(smem_u32(sW3 + kb * 512), 128, 256), id_out, kb > 0);
-      commit(bar);
+      mma_hidden(0, 1);
+      mma_hidden(1, 1);
     }
-    if (!wait_mma(bar, phase, sOk, a.err)) break;
-    uint32_t v[16];
-    TC_LD16(trow + 128u, v);
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    if (valid) {
-      float* zo = a.z + p * a.k;
-#pragma unroll
-      for (int o = 0; o < 16; ++o)
-        if (o < a.k) zo[o] = __fadd_rn(__uint_as_float(v[o]), sB3[o]);
-    }
+    load_colour(pair + gridDim.x);  // the next pair's colours, in flight from here on
+    if (!wait(0)) break;
+    hidden_epilogue(trow(0), c0, sB1, sH, row);
+    smem_to_mma_barrier();
+    if (t == 0) mma_hidden(0, 2);
+    if (!wait(1)) break;
+    hidden_epilogue(trow(1), c0, sB1, sH + kSlotH, row);
+    smem_to_mma_barrier();
+    if (t == 0) mma_hidden(1, 2);
+    if (!wait(0)) break;
+    hidden_epilogue(trow(0), c0, sB2, sH, row);  // h2 replaces h1 (layer 2 has finished reading it)
+    smem_to_mma_barrier();
+    if (t == 0) mma_out(0);
+    if (!wait(1)) break;
+    hidden_epilogue(trow(1), c0, sB2, sH + kSlotH, row);
+    smem_to_mma_barrier();
+    if (t == 0) mma_out(1);
+    if (!wait(0)) break;
+    out(0, pair);
+    if (!wait(1)) break;
+    out(1, pair);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kUpTmemCols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kUpTmemCols) : "memory");
   }
 }
 
@@ -285,8 +331,9 @@ extern "C" hsc_status hsc_upsample_rgb(hsc_ctx* ctx, const float* rgb, int64_t p
   auto kern = hsc::upsample_tc_kernel;
   HSC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, hsc::kUpSmem));
   const int64_t tiles = (pixels + hsc::kUpRows - 1) / hsc::kUpRows;
-  int64_t grid = (int64_t)ctx->sm_count * 2;  // two CTAs per SM (TMEM: 2 x 256 columns)
-  if (grid > tiles) grid = tiles;
+  const int64_t pairs = (tiles + 1) / 2;
+  int64_t grid = ctx->sm_count;  // one CTA per SM (all 512 TMEM columns)
+  if (grid > pairs) grid = pairs;
   kern<<<(unsigned)grid, hsc::kUpThreads, hsc::kUpSmem, s>>>(a);
   return hsc::check_launch("upsample_tc_kernel");
 }

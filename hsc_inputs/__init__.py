@@ -432,6 +432,61 @@ def torch_gbuffers(gen, pixels: int, n_mat: int, secondary: bool, device):
     return (n1, x1, m1), (n2, x2, m2)
 
 
+# ----------------------------------------------------------------------------
+# Path-traced scene (a Cornell-box stand-in for the paper's Mitsuba scenes)
+# ----------------------------------------------------------------------------
+
+@dataclass
+class PTScene:
+    """Geometry in float32, spectra in float64.
+
+    quads:   (Q, 8) rows (axis, c, u0, u1, v0, v1, normal sign, material):
+             the rectangle {x[axis] = c, u0 <= x[u] <= u1, v0 <= x[v] <= v1}
+             with (u, v) the other two axes in increasing order, its normal
+             along +/- axis; material -1 marks the emitter.
+    spheres: (S, 5) rows (cx, cy, cz, radius, material).
+    refl:    (M, n) reflectances of the materials; emit: (n,) emitted
+             radiance of the emitter (SPD times intensity).
+    cam:     (4, 3) pinhole origin, image-plane lower-left corner, horizontal
+             and vertical spans (pixel (x, y) maps to
+             ll + (x + jx)/W * hor + (y + jy)/H * ver, y up)."""
+    quads: np.ndarray
+    spheres: np.ndarray
+    refl: np.ndarray
+    emit: np.ndarray
+    cam: np.ndarray
+    grid: tuple
+
+
+def cornell_scene(width: int, height: int, grid_spec=GRID_81, light: str = "blackbody",
+                  seed: int = MASTER_SEED + 8, intensity: float = 12.0) -> PTScene:
+    """The unit box [0,1]^3 open towards the camera (z = 0): white floor,
+    ceiling and back wall, red left wall, green right wall, an emitting
+    rectangle just below the ceiling, a smooth and a saw-tooth sphere.  The
+    emitter is a 4000 K blackbody (``light='blackbody'``) or a 20 nm-wide band
+    at 590 nm (``'narrowband'``), unit peak times ``intensity``."""
+    lam = grid(*grid_spec)
+    r_s, r_t = streams(seed, 2)
+    white = np.full_like(lam, 0.78)
+    red = 0.05 + 0.70 * np.exp(-0.5 * ((lam - 640.0) / 40.0) ** 2)
+    green = 0.05 + 0.60 * np.exp(-0.5 * ((lam - 535.0) / 35.0) ** 2)
+    refl = np.stack([white, red, green, smooth_reflectances(r_s, lam, 1)[0], sawtooth_reflectances(r_t, lam, 1)[0]])
+    spd = blackbody(lam, [4000.0])[0] if light == "blackbody" else narrowband(lam, [590.0], [20.0])[0]
+    quads = np.array([
+        [1, 0.0, 0.0, 1.0, 0.0, 1.0, +1, 0],      # floor      y = 0
+        [1, 1.0, 0.0, 1.0, 0.0, 1.0, -1, 0],      # ceiling    y = 1
+        [2, 1.0, 0.0, 1.0, 0.0, 1.0, -1, 0],      # back wall  z = 1
+        [0, 0.0, 0.0, 1.0, 0.0, 1.0, +1, 1],      # left wall  x = 0 (red)
+        [0, 1.0, 0.0, 1.0, 0.0, 1.0, -1, 2],      # right wall x = 1 (green)
+        [1, 0.998, 0.35, 0.65, 0.40, 0.70, -1, -1],  # emitter under the ceiling
+    ], dtype=np.float32)
+    spheres = np.array([[0.28, 0.18, 0.62, 0.18, 3], [0.70, 0.25, 0.38, 0.22, 4]], dtype=np.float32)
+    aspect = width / height
+    cam = np.array([[0.5, 0.5, -1.4], [0.5 - 0.5 * aspect, 0.0, 0.0], [aspect, 0.0, 0.0], [0.0, 1.0, 0.0]],
+                   dtype=np.float32)
+    return PTScene(quads, spheres, refl, intensity * spd, cam, tuple(grid_spec))
+
+
 SERVE_SIZES = ((512, 512), (1024, 1024), (1920, 1080), (2048, 2048), (3840, 2160))
 
 

@@ -345,6 +345,34 @@ HSC_API hsc_status hsc_upsample_rgb(hsc_ctx* ctx, const float* rgb, int64_t pixe
                                     const float* b1, const float* W2, const float* b2, const float* W3,
                                     const float* b3, int k, float* z_out, void* stream);
 
+/* ------------------------------------------------------------- path tracing */
+
+/* Path tracing with per-channel throughput (the renderer of Sec. 5): camera
+ * rays through jittered pixel positions, Lambertian reflection sampled by the
+ * cosine (each reflection multiplies the throughput by the reflectance), a
+ * path ends on an emitting rectangle, on leaving the scene or after `depth`
+ * reflections; pixel = mean over `spp` samples of emit (.) mat_{m_0} (.) ...
+ * With spectra (channels = n, to_xyz = T) this is the naive spectral path
+ * tracer; with codes (channels = k, to_xyz = M = T D) the latent one, the
+ * per-channel product being the blockwise product of Eq. 5.  The paths do
+ * not depend on the channels: both modes trace the same paths.
+ *   quads: device n_quads x 8 float32 rows (axis 0/1/2, c, u0, u1, v0, v1,
+ *     normal sign, material; material -1 = emitter): the rectangle
+ *     x[axis] = c, u0 <= x[u] <= u1, v0 <= x[v] <= v1, (u, v) the other axes
+ *     in increasing order;  spheres: device n_spheres x 5 (centre, radius,
+ *     material);  camera: device 4 x 3 (origin, image-plane lower-left
+ *     corner, horizontal and vertical spans; pixel index y * width + x with
+ *     y up);  materials: device n_mat x channels;  emit: device channels;
+ *   to_xyz: device 3 x channels;  xyz_out: device P x 3;  channels_out:
+ *     device P x channels pixel means (nullable; channels <= 16).
+ * Random numbers: Philox4x32-10 with counter (pixel, sample, vertex, 0) and
+ * key (seed, 0).  Limits: 32 rectangles, 32 spheres, depth <= 16,
+ * n_mat <= 255; out-of-range materials set the error word.               */
+HSC_API hsc_status hsc_path_trace(hsc_ctx* ctx, const float* quads, int n_quads, const float* spheres,
+                                  int n_spheres, const float* camera, int width, int height, int spp, int depth,
+                                  uint32_t seed, const float* materials, int n_mat, const float* emit, int channels,
+                                  const float* to_xyz, float* xyz_out, float* channels_out, void* stream);
+
 /* --------------------------------------------------------- multi-bounce chains */
 
 /* Multi-bounce chains, the codec-selection proxy of Sec. 3.5: chain c starts

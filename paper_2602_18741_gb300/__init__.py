@@ -96,6 +96,8 @@ _SIGS = {
     "hsc_chain_eval": ([_vp, _vp, _i32, _vp, _i32, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp],
                        _i32),
     "hsc_upsample_rgb": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp], _i32),
+    "hsc_path_trace": ([_vp, _vp, _i32, _vp, _i32, _vp, _i32, _i32, _i32, _i32, ctypes.c_uint32, _vp, _i32, _vp,
+                        _i32, _vp, _vp, _vp, _vp], _i32),
     "hsc_batch_create": ([_vp, ctypes.POINTER(_Frame), _i32, ctypes.POINTER(_vp)], _i32),
     "hsc_batch_shade": ([_vp, _vp, _vp], _i32),
     "hsc_batch_destroy": ([_vp], None),
@@ -438,6 +440,24 @@ def hsc_upsample_rgb(ctx: Context, rgb: torch.Tensor, W1: torch.Tensor, b1: torc
             raise ValueError("all tensors must be float32")
     _check(_lib.hsc_upsample_rgb(ctx.handle, _ptr(rgb), int(P), _ptr(W1), _ptr(b1), _ptr(W2), _ptr(b2), _ptr(W3),
                                  _ptr(b3), int(k), _ptr(z_out), _stream(stream)))
+
+
+def hsc_path_trace(ctx: Context, quads: torch.Tensor, spheres: torch.Tensor, camera: torch.Tensor, width: int,
+                   height: int, spp: int, depth: int, seed: int, materials: torch.Tensor, emit: torch.Tensor,
+                   to_xyz: torch.Tensor, xyz_out: torch.Tensor, channels_out: Optional[torch.Tensor] = None,
+                   stream=None):
+    """Path tracing with per-channel throughput (spectra or codes); see include/hsc.h."""
+    C = emit.shape[0]
+    P = width * height
+    if quads.shape[1:] != (8,) or spheres.shape[1:] != (5,) or camera.shape != (4, 3) or \
+            materials.shape[1:] != (C,) or to_xyz.shape != (3, C) or xyz_out.shape != (P, 3):
+        raise ValueError("shapes: quads (Q,8), spheres (S,5), camera (4,3), materials (M,C), to_xyz (3,C), xyz (P,3)")
+    if channels_out is not None and channels_out.shape != (P, C):
+        raise ValueError("channels_out must be (P, C)")
+    _check(_lib.hsc_path_trace(ctx.handle, _ptr(quads), int(quads.shape[0]), _ptr(spheres), int(spheres.shape[0]),
+                               _ptr(camera), int(width), int(height), int(spp), int(depth), int(seed) & 0xFFFFFFFF,
+                               _ptr(materials), int(materials.shape[0]), _ptr(emit), int(C), _ptr(to_xyz),
+                               _ptr(xyz_out), _ptr(channels_out), _stream(stream)))
 
 
 def hsc_chain_eval(ctx: Context, refl: torch.Tensor, lights: torch.Tensor, E: torch.Tensor, D: torch.Tensor,

@@ -490,6 +490,7 @@ def secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T,
     rows.update(batch_rows(args, hsc, ctx, dev, timed))
     rows.update(chain_rows(args, hsc, ctx, dev, timed))
     rows.update(upsample_rows(args, hsc, ctx, dev, timed))
+    rows.update(pathtrace_rows(args, hsc, ctx, dev, timed))
     if args.serve_seconds > 0:
         rows.update(serve_rows(args, hsc, ctx, dev))
     return rows
@@ -518,6 +519,48 @@ def upsample_rows(args, hsc, ctx, dev, timed):
     return {"upsample_rgb_4k": {"ms": m, "Mpx_per_s": P / (m * 1e-3) / 1e6,
                                 "TFLOP_per_s": flops / (m * 1e-3) / 1e12,
                                 "tensor_TFLOP_per_s_issued": mma_flops / (m * 1e-3) / 1e12}}
+
+
+def pathtrace_rows(args, hsc, ctx, dev, timed):
+    """Path tracing of the Cornell-box stand-in at 1920x1080, 16 samples per
+    pixel, up to 3 reflections: the same paths with n = 81 spectral channels
+    and with the k = 6 codes; Delta E 2000 of the latent render against the
+    spectral one."""
+    import torch
+    W, H, spp, depth = 1920, 1080, 16, 3
+    sc = hi.cornell_scene(W, H)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+    n = sc.grid[2]
+    T = torch.empty(3, n, device=dev)
+    hsc.hsc_cmf_weights(ctx, n, sc.grid[0], sc.grid[1], T)
+    E, D = hi.load_codec(6, n)
+    Ed, Dd = t(E), t(D)
+    zr = torch.empty(sc.refl.shape[0], 6, device=dev)
+    ze = torch.empty(1, 6, device=dev)
+    hsc.hsc_encode(ctx, Ed, t(sc.refl), zr)
+    hsc.hsc_encode(ctx, Ed, t(sc.emit[None, :]), ze)
+    M = torch.empty(3, 6, device=dev)
+    hsc.hsc_fold_xyz(ctx, T, Dd, M)
+    geo = (t(sc.quads), t(sc.spheres), t(sc.cam))
+    xs = torch.empty(W * H, 3, device=dev)
+    xl = torch.empty(W * H, 3, device=dev)
+    z = torch.empty(W * H, 6, device=dev)
+    out = {}
+    mats_s, emit_s, emit_z = t(sc.refl), t(sc.emit), ze[0].contiguous()
+    runs = {"spectral_n81": lambda: hsc.hsc_path_trace(ctx, *geo, W, H, spp, depth, 7, mats_s, emit_s, T, xs),
+            "latent_k6": lambda: hsc.hsc_path_trace(ctx, *geo, W, H, spp, depth, 7, zr, emit_z, M, xl, z)}
+    paths = W * H * spp
+    for name, fn in runs.items():
+        ms, _ = timed(fn, max(3, args.steps // 2), args.warmup)
+        m = statistics.mean(ms)
+        out[f"pathtrace_{name}"] = {"ms": m, "Mpaths_per_s": paths / (m * 1e-3) / 1e6, "spp": spp, "depth": depth}
+    out["speedup_pathtrace_latent_vs_spectral"] = out["pathtrace_spectral_n81"]["ms"] / out["pathtrace_latent_k6"]["ms"]
+    st = torch.zeros(8, device=dev, dtype=torch.float64)
+    hsc.hsc_delta_e(ctx, xl, xs, T, st)
+    hsc.hsc_sync(ctx)
+    s = st.cpu().numpy()
+    out["pathtrace_delta_e_latent_vs_spectral"] = {"de2000_mean": float(s[0]), "de2000_p95": float(s[1])}
+    return out
 
 
 def serve_rows(args, hsc, ctx, dev):

@@ -120,8 +120,8 @@ class ClockSampler:
 def oracle_rate(seconds: float, k: int, threads: int = 1, max_rows: int = 1080):
     """Run the FP64 oracle's latent frame (encode, shading, decode to XYZ) on
     consecutive 32-row bands of the 1920x1080 frame in a child process with
-    ``threads`` BLAS/OpenMP threads until ``seconds`` elapse; returns
-    (evals per second, rows done, seconds)."""
+    ``threads`` BLAS/OpenMP threads until ``seconds`` elapse (at least one
+    band); returns (evals per second, rows done, seconds)."""
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = str(threads)
@@ -137,7 +137,7 @@ def oracle_rate(seconds: float, k: int, threads: int = 1, max_rows: int = 1080):
         "band = 32\n"
         "rows = 0; evals = 0\n"
         "t0 = time.perf_counter()\n"
-        f"while rows < {max_rows} and time.perf_counter() - t0 < {seconds}:\n"
+        f"while rows < {max_rows} and (rows == 0 or time.perf_counter() - t0 < {seconds}):\n"
         "    idx = np.arange(rows * W, (rows + band) * W)\n"
         "    g1 = hi.GBuffer(f.g1.normal[idx], f.g1.pos[idx], f.g1.mat[idx])\n"
         "    g2 = hi.GBuffer(f.g2.normal[idx], f.g2.pos[idx], f.g2.mat[idx])\n"

@@ -18,6 +18,13 @@
 //     thread streams the whole tile (128 * n * 4 contiguous bytes) to global
 //     memory with a bulk async copy (cp.async.bulk), which overlaps the next
 //     tile's MMA.
+// FP32 latents (k <= 8) take the same path with each FP32 value split into
+// three bf16 parts, z = hi + mid + lo (each remainder is exact in FP32), and
+// the six products hi.hi, hi.mid, mid.hi, hi.lo, mid.mid, lo.hi laid side by
+// side along K in segments of 8 columns (K = 48: three K = 16 MMAs into one
+// accumulator); every
+// product is exact in FP32 and the dropped ones are below 2^-24 relative, so
+// the result has FP32 accuracy.
 // Every mbarrier wait is bounded; on expiry the kernel sets an error bit,
 // drains its bulk copies, frees its TMEM and returns.
 #include "common.cuh"
@@ -35,7 +42,7 @@ using namespace tc;
 
 struct TcArgs {
   const void* latent;
-  int dt;  // HSC_BF16 or HSC_FP8_E4M3
+  int dt;  // HSC_BF16, HSC_FP8_E4M3 or HSC_F32 (split into three bf16 parts)
   const float* scales;
   int64_t P;
   int k;
@@ -46,31 +53,68 @@ struct TcArgs {
   unsigned int* err;
 };
 
-// Latent row p (k codes) as 8 packed bf16 pairs, zero beyond k (and beyond P).
-__device__ __forceinline__ void load_a_row(const TcArgs& a, int64_t p, bool valid, uint32_t (&w)[8]) {
+__device__ __forceinline__ float to_bf16_value(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// z = hi + mid + lo with each part a bf16 value; the two remainders are exact
+// in FP32, lo is rounded.
+__device__ __forceinline__ void split3(float z, float (&part)[3]) {
+  part[0] = to_bf16_value(z);
+  const float r1 = __fsub_rn(z, part[0]);
+  part[1] = to_bf16_value(r1);
+  part[2] = to_bf16_value(__fsub_rn(r1, part[1]));
+}
+
+// K segments of the split FP32 form: columns 8s .. 8s+7 hold, for every code
+// c < k, parts (hi, hi, mid, hi, mid, lo)[s] of z_c in A and parts
+// kSegB[s] = (hi, mid, hi, lo, mid, hi)[s] of D_{i,c} in B.
+__constant__ int kSegB[6] = {0, 1, 0, 2, 1, 0};
+
+// Latent row p as 8 * KB packed bf16 pairs (K = 16 * KB), zero beyond the
+// used columns (and beyond P).
+template <int KB>
+__device__ __forceinline__ void load_a_row(const TcArgs& a, int64_t p, bool valid, uint32_t (&w)[8 * KB]) {
 #pragma unroll
-  for (int j = 0; j < 8; ++j) w[j] = 0u;
+  for (int j = 0; j < 8 * KB; ++j) w[j] = 0u;
   if (!valid) return;
-#pragma unroll
-  for (int e = 0; e < 16; ++e) {
-    if (e >= a.k) break;
-    float v;
-    if (a.dt == HSC_FP8_E4M3)
-      v = fp8_e4m3_to_float(__ldg(reinterpret_cast<const unsigned char*>(a.latent) + p * a.k + e));
-    else
-      v = __uint_as_float(((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(a.latent) + p * a.k + e)) << 16);
+  auto put = [&](int e, float v) {
     const uint32_t bits = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v));
     w[e >> 1] |= bits << ((e & 1) * 16);
+  };
+  if constexpr (KB == 1) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      if (e >= a.k) break;
+      float v;
+      if (a.dt == HSC_FP8_E4M3)
+        v = fp8_e4m3_to_float(__ldg(reinterpret_cast<const unsigned char*>(a.latent) + p * a.k + e));
+      else
+        v = __uint_as_float(((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(a.latent) + p * a.k + e)) << 16);
+      put(e, v);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (c >= a.k) break;
+      float part[3];
+      split3(__ldg(reinterpret_cast<const float*>(a.latent) + p * a.k + c), part);
+      // segments of 8 columns: hi, hi, mid, hi, mid, lo
+      put(0 + c, part[0]);
+      put(8 + c, part[0]);
+      put(16 + c, part[1]);
+      put(24 + c, part[0]);
+      put(32 + c, part[1]);
+      put(40 + c, part[2]);
+    }
   }
 }
 
-template <int NPAD>
+template <int NPAD, int KB>
 __global__ void __launch_bounds__(kTcThreads) decode_spectra_tc_kernel(const TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* sA = base;                                           // 128 x 16 bf16 = 4096 B
-  unsigned char* sB = base + 4096;                                    // NPAD x 16 bf16
-  float* sOut = reinterpret_cast<float*>(base + 4096 + NPAD * 32);    // [128 x n] staging tile
+  unsigned char* sA = base;                                           // KB x [128 x 16] bf16 (4096 B each)
+  unsigned char* sB = base + KB * 4096;                               // KB x [NPAD x 16] bf16
+  float* sOut = reinterpret_cast<float*>(base + KB * (4096 + NPAD * 32));  // [128 x n] staging tile
   uint64_t* sBar = reinterpret_cast<uint64_t*>(sOut + kTcRows * a.n + 4);
   uint32_t* sTmem = reinterpret_cast<uint32_t*>(sBar + 1);
   int* sOk = reinterpret_cast<int*>(sTmem + 1);
@@ -91,54 +135,70 @@ __global__ void __launch_bounds__(kTcThreads) decode_spectra_tc_kernel(const TcA
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *sOk = 1;
   }
-  for (int idx = t; idx < NPAD * 16; idx += kTcThreads) {
-    const int r = idx >> 4, e = idx & 15;
+  for (int idx = t; idx < NPAD * 16 * KB; idx += kTcThreads) {
+    const int r = idx / (16 * KB), e = idx - r * (16 * KB);
     float v = 0.0f;
-    if (r < n && e < a.k) {
-      v = __ldg(a.D + r * a.k + e);
-      if (a.dt == HSC_FP8_E4M3) v = __fmul_rn(v, __ldg(a.scales + e));
+    if (KB == 1) {
+      if (r < n && e < a.k) {
+        v = __ldg(a.D + r * a.k + e);
+        if (a.dt == HSC_FP8_E4M3) v = __fmul_rn(v, __ldg(a.scales + e));
+      }
+    } else if (r < n && (e & 7) < a.k) {
+      const int seg = e >> 3, c = e & 7;
+      float part[3];
+      split3(__ldg(a.D + r * a.k + c), part);
+      v = part[kSegB[seg]];
     }
-    *reinterpret_cast<__nv_bfloat16*>(sB + kmajor_off(r, e)) = __float2bfloat16_rn(v);
+    *reinterpret_cast<__nv_bfloat16*>(sB + (e >> 4) * (NPAD * 32) + kmajor_off(r, e & 15)) = __float2bfloat16_rn(v);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *sTmem;
   const uint32_t bar = smem_u32(sBar);
-  const uint64_t adesc = smem_desc(smem_u32(sA), 128, 256);
-  const uint64_t bdesc = smem_desc(smem_u32(sB), 128, 256);
+
   constexpr uint32_t idesc = instr_desc_bf16(kTcRows, NPAD);
 
   const int64_t tiles = (a.P + kTcRows - 1) / kTcRows;
   uint32_t phase = 0;
   // this thread's latent row of the first tile, loaded ahead
-  uint32_t wA[8];
+  uint32_t wA[8 * KB];
   {
     const int64_t p = (int64_t)blockIdx.x * kTcRows + t;
-    load_a_row(a, p, blockIdx.x < tiles && p < a.P, wA);
+    load_a_row<KB>(a, p, blockIdx.x < tiles && p < a.P, wA);
   }
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t p0 = tile * kTcRows;
     const int rows = (int)min((int64_t)kTcRows, a.P - p0);
-    // A tile: row t in the canonical K-major layout
-    *reinterpret_cast<uint4*>(sA + kmajor_off(t, 0)) = make_uint4(wA[0], wA[1], wA[2], wA[3]);
-    *reinterpret_cast<uint4*>(sA + kmajor_off(t, 8)) = make_uint4(wA[4], wA[5], wA[6], wA[7]);
+    // A tile: row t in the canonical K-major layout, one [128 x 16] block per K step
+#pragma unroll
+    for (int kb = 0; kb < KB; ++kb) {
+      *reinterpret_cast<uint4*>(sA + kb * 4096 + kmajor_off(t, 0)) =
+          make_uint4(wA[8 * kb + 0], wA[8 * kb + 1], wA[8 * kb + 2], wA[8 * kb + 3]);
+      *reinterpret_cast<uint4*>(sA + kb * 4096 + kmajor_off(t, 8)) =
+          make_uint4(wA[8 * kb + 4], wA[8 * kb + 5], wA[8 * kb + 6], wA[8 * kb + 7]);
+    }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (t == 0) {
-      asm volatile(
-          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-          "l"(adesc), "l"(bdesc), "r"(idesc), "r"(0)
-          : "memory");
+#pragma unroll
+      for (int kb = 0; kb < KB; ++kb) {
+        const uint64_t adesc = smem_desc(smem_u32(sA + kb * 4096), 128, 256);
+        const uint64_t bdesc = smem_desc(smem_u32(sB + kb * NPAD * 32), 128, 256);
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(kb)
+            : "memory");
+      }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
     }
     // next tile's row, in flight while the MMA and this tile's epilogue run
     {
       const int64_t nt = tile + gridDim.x;
       const int64_t p = nt * kTcRows + t;
-      load_a_row(a, p, nt < tiles && p < a.P, wA);
+      load_a_row<KB>(a, p, nt < tiles && p < a.P, wA);
     }
     if (t == 0) {
       if (!mbar_wait(bar, phase)) {
@@ -191,10 +251,10 @@ __global__ void __launch_bounds__(kTcThreads) decode_spectra_tc_kernel(const TcA
   }
 }
 
-template <int NPAD>
+template <int NPAD, int KB>
 hsc_status launch_tc(const TcArgs& a, int sm_count, cudaStream_t s) {
-  const size_t smem = 1024 + 4096 + NPAD * 32 + (size_t)kTcRows * a.n * 4 + 64;
-  auto kern = decode_spectra_tc_kernel<NPAD>;
+  const size_t smem = 1024 + KB * (4096 + NPAD * 32) + (size_t)kTcRows * a.n * 4 + 64;
+  auto kern = decode_spectra_tc_kernel<NPAD, KB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return set_error(HSC_ERR_CUDA, "smem attribute: %s", cudaGetErrorString(e));
   const int64_t tiles = (a.P + kTcRows - 1) / kTcRows;
@@ -208,6 +268,20 @@ hsc_status launch_tc(const TcArgs& a, int sm_count, cudaStream_t s) {
   if (grid < 1) grid = 1;
   kern<<<(unsigned)grid, kTcThreads, smem, s>>>(a);
   return check_launch("decode_spectra_tc_kernel");
+}
+
+template <int KB>
+hsc_status launch_tc_n(const TcArgs& a, int sm_count, cudaStream_t s) {
+  switch (a.npad) {
+    case 16: return launch_tc<16, KB>(a, sm_count, s);
+    case 32: return launch_tc<32, KB>(a, sm_count, s);
+    case 48: return launch_tc<48, KB>(a, sm_count, s);
+    case 64: return launch_tc<64, KB>(a, sm_count, s);
+    case 80: return launch_tc<80, KB>(a, sm_count, s);
+    case 96: return launch_tc<96, KB>(a, sm_count, s);
+    case 112: return launch_tc<112, KB>(a, sm_count, s);
+    default: return launch_tc<128, KB>(a, sm_count, s);
+  }
 }
 
 }  // namespace
@@ -225,16 +299,8 @@ hsc_status launch_decode_spectra_tc(hsc_ctx* ctx, const void* latent, int dt, co
   a.npad = (n + 15) / 16 * 16;
   a.out = out;
   a.err = ctx->d_err;
-  switch (a.npad) {
-    case 16: return launch_tc<16>(a, ctx->sm_count, s);
-    case 32: return launch_tc<32>(a, ctx->sm_count, s);
-    case 48: return launch_tc<48>(a, ctx->sm_count, s);
-    case 64: return launch_tc<64>(a, ctx->sm_count, s);
-    case 80: return launch_tc<80>(a, ctx->sm_count, s);
-    case 96: return launch_tc<96>(a, ctx->sm_count, s);
-    case 112: return launch_tc<112>(a, ctx->sm_count, s);
-    default: return launch_tc<128>(a, ctx->sm_count, s);
-  }
+  if (dt == HSC_F32) return launch_tc_n<3>(a, ctx->sm_count, s);
+  return launch_tc_n<1>(a, ctx->sm_count, s);
 }
 
 }  // namespace hsc

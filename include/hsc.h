@@ -376,6 +376,30 @@ HSC_API hsc_status hsc_path_trace(hsc_ctx* ctx, const float* quads, int n_quads,
                                   uint32_t seed, const float* materials, int n_mat, const float* emit, int channels,
                                   const float* to_xyz, float* xyz_out, float* channels_out, void* stream);
 
+/* ------------------------------------------------------- codec fitting sweep */
+
+/* One Adam step of the paper's codec parameterisation (Sec. 3.2-3.5):
+ * E = softplus(E~), D = softplus(D~) with beta `softplus_beta`, loss Eq. 6
+ * (weights e2e, rec, code, col per variant) on one mini-batch shared by all
+ * `variants`, for every variant at once (one CTA each).
+ *   R_all, L_all: device rows of n float32 (training reflectances, lights);
+ *   pair_r, pair_l: device `pairs` int32 row indices; pair_scale: device
+ *   `pairs` float32 light scales (pair p is R_all[pair_r[p]],
+ *   L_all[pair_l[p]] * pair_scale[p]);  T: device 3 x n (hsc_cmf_weights);
+ *   weights: device variants x 4;  Et: device variants x k x n;  Dt: device
+ *   variants x n x k;  mE, vE, mD, vD: Adam moments of the same shapes (zero
+ *   before step 1); updated in place.  step: 1-based (bias correction).
+ *   losses_out: device variants x 5 (total, e2e, rec, code, col) at the
+ *   parameters before the step, or NULL;  grad_out: device variants x 2kn,
+ *   dL/dE~ then dL/dD~, or NULL.
+ * Limits: k a multiple of 3 up to 15, n <= 128, pairs <= 256.            */
+HSC_API hsc_status hsc_codec_fit_step(hsc_ctx* ctx, int variants, int k, int n, const float* R_all,
+                                      const float* L_all, const int32_t* pair_r, const int32_t* pair_l,
+                                      const float* pair_scale, int pairs, const float* T, const float* weights,
+                                      float* Et, float* Dt, float* mE, float* vE, float* mD, float* vD, int step,
+                                      float lr, float beta1, float beta2, float eps, float softplus_beta,
+                                      float* losses_out, float* grad_out, void* stream);
+
 /* --------------------------------------------------------- multi-bounce chains */
 
 /* Multi-bounce chains, the codec-selection proxy of Sec. 3.5: chain c starts

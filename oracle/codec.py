@@ -24,11 +24,17 @@ Readings where the paper is silent:
   averages band i and column i of D is band i's indicator (for k = n this is
   the identity, a fixed point with zero loss).
 
+The paper's own parameterisation (softplus with beta = 10, Adam) is given by
+``adam_softplus_step``: one bias-corrected Adam step on the raw parameters,
+the gradient through the softplus by the chain rule.
+
 Pins (tests/test_oracle_codec.py): exact linearity of encode/decode; the
 blockwise product equals the element-wise product on R^k; central finite
 differences of the total loss against the analytic gradient; monotone descent;
 the identity codec at k = n has zero loss and stays put; weights and codes stay
-non-negative.
+non-negative; softplus closed forms and its inverse; finite differences of the
+loss through the softplus; the first Adam step moves every parameter with a
+non-zero gradient by lr against its sign.
 """
 from __future__ import annotations
 
@@ -225,3 +231,66 @@ def projected_gradient_fit(batch: Batch, k: int, iters: int = 5000, w=PAPER_WEIG
         E, D, f, gE, gD = En, Dn, fn, gEn, gDn
         hist.append(f)
     return FitResult(E, D, hist, it, float(pg))
+
+
+# ----------------------------------------------------------------------------
+# The paper's parameterisation (Sec. 3.2-3.5): W = softplus_beta(W~) with
+# beta = 10, Adam on mini-batches.  One step, as the batched GPU sweep takes it.
+# ----------------------------------------------------------------------------
+
+SOFTPLUS_BETA = 10.0
+
+
+def softplus(x, beta=SOFTPLUS_BETA):
+    """log(1 + exp(beta x)) / beta, evaluated without overflow."""
+    bx = beta * np.asarray(x, dtype=np.float64)
+    return (np.maximum(bx, 0.0) + np.log1p(np.exp(-np.abs(bx)))) / beta
+
+
+def softplus_grad(x, beta=SOFTPLUS_BETA):
+    """d softplus / dx = sigmoid(beta x)."""
+    bx = beta * np.asarray(x, dtype=np.float64)
+    e = np.exp(-np.abs(bx))
+    return np.where(bx >= 0, 1.0 / (1.0 + e), e / (1.0 + e))
+
+
+def softplus_inverse(y, beta=SOFTPLUS_BETA):
+    """x with softplus(x) = y > 0."""
+    by = beta * np.asarray(y, dtype=np.float64)
+    return (by + np.log(-np.expm1(-by))) / beta
+
+
+@dataclass
+class AdamState:
+    mE: np.ndarray
+    vE: np.ndarray
+    mD: np.ndarray
+    vD: np.ndarray
+    t: int = 0
+
+
+def adam_init(Et, Dt) -> AdamState:
+    return AdamState(np.zeros_like(Et), np.zeros_like(Et), np.zeros_like(Dt), np.zeros_like(Dt), 0)
+
+
+def adam_softplus_step(Et, Dt, st: AdamState, batch: Batch, w=PAPER_WEIGHTS, lr: float = 1e-3,
+                       b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8, beta: float = SOFTPLUS_BETA):
+    """One Adam step (bias-corrected moments) on the raw parameters (E~, D~)
+    of E = softplus(E~), D = softplus(D~) for the Eq. 6 loss on ``batch``;
+    returns the new (E~, D~, state) and the loss terms at the old parameters."""
+    E, D = softplus(Et, beta), softplus(Dt, beta)
+    parts = losses(E, D, batch, w)
+    gE, gD = gradient(E, D, batch, w)
+    g = (gE * softplus_grad(Et, beta), gD * softplus_grad(Dt, beta))
+    t = st.t + 1
+    out = []
+    moments = ((st.mE, st.vE), (st.mD, st.vD))
+    new_m = []
+    for x, gx, (m, v) in zip((Et, Dt), g, moments):
+        m = b1 * m + (1 - b1) * gx
+        v = b2 * v + (1 - b2) * gx * gx
+        mh = m / (1 - b1 ** t)
+        vh = v / (1 - b2 ** t)
+        out.append(x - lr * mh / (np.sqrt(vh) + eps))
+        new_m.append((m, v))
+    return out[0], out[1], AdamState(new_m[0][0], new_m[0][1], new_m[1][0], new_m[1][1], t), parts

@@ -98,6 +98,9 @@ _SIGS = {
     "hsc_upsample_rgb": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp], _i32),
     "hsc_path_trace": ([_vp, _vp, _i32, _vp, _i32, _vp, _i32, _i32, _i32, _i32, ctypes.c_uint32, _vp, _i32, _vp,
                         _i32, _vp, _vp, _vp, _vp], _i32),
+    "hsc_codec_fit_step": ([_vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                            _vp, _i32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                            _vp, _vp, _vp], _i32),
     "hsc_batch_create": ([_vp, ctypes.POINTER(_Frame), _i32, ctypes.POINTER(_vp)], _i32),
     "hsc_batch_shade": ([_vp, _vp, _vp], _i32),
     "hsc_batch_destroy": ([_vp], None),
@@ -458,6 +461,33 @@ def hsc_path_trace(ctx: Context, quads: torch.Tensor, spheres: torch.Tensor, cam
                                _ptr(camera), int(width), int(height), int(spp), int(depth), int(seed) & 0xFFFFFFFF,
                                _ptr(materials), int(materials.shape[0]), _ptr(emit), int(C), _ptr(to_xyz),
                                _ptr(xyz_out), _ptr(channels_out), _stream(stream)))
+
+
+def hsc_codec_fit_step(ctx: Context, R_all: torch.Tensor, L_all: torch.Tensor, pair_r: torch.Tensor,
+                       pair_l: torch.Tensor, pair_scale: torch.Tensor, T: torch.Tensor, weights: torch.Tensor,
+                       Et: torch.Tensor, Dt: torch.Tensor, mE: torch.Tensor, vE: torch.Tensor, mD: torch.Tensor,
+                       vD: torch.Tensor, step: int, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
+                       eps: float = 1e-8, softplus_beta: float = 10.0, losses_out: Optional[torch.Tensor] = None,
+                       grad_out: Optional[torch.Tensor] = None, stream=None):
+    """One Adam step of the softplus-parameterised codec for every variant; see include/hsc.h."""
+    V, k, n = Et.shape
+    P = pair_r.shape[0]
+    if Dt.shape != (V, n, k) or weights.shape != (V, 4) or T.shape != (3, n) or R_all.shape[1] != n \
+            or L_all.shape[1] != n or pair_l.shape != (P,) or pair_scale.shape != (P,):
+        raise ValueError("shapes: Et (V,k,n), Dt (V,n,k), weights (V,4), T (3,n), rows of n, pairs (P,)")
+    for m in (mE, vE):
+        if m.shape != Et.shape:
+            raise ValueError("moments of E~ must match Et")
+    for m in (mD, vD):
+        if m.shape != Dt.shape:
+            raise ValueError("moments of D~ must match Dt")
+    if pair_r.dtype != torch.int32 or pair_l.dtype != torch.int32:
+        raise ValueError("pair indices must be int32")
+    _check(_lib.hsc_codec_fit_step(ctx.handle, int(V), int(k), int(n), _ptr(R_all), _ptr(L_all), _ptr(pair_r),
+                                   _ptr(pair_l), _ptr(pair_scale), int(P), _ptr(T), _ptr(weights), _ptr(Et),
+                                   _ptr(Dt), _ptr(mE), _ptr(vE), _ptr(mD), _ptr(vD), int(step), float(lr),
+                                   float(beta1), float(beta2), float(eps), float(softplus_beta), _ptr(losses_out),
+                                   _ptr(grad_out), _stream(stream)))
 
 
 def hsc_chain_eval(ctx: Context, refl: torch.Tensor, lights: torch.Tensor, E: torch.Tensor, D: torch.Tensor,

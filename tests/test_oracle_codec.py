@@ -139,3 +139,56 @@ def test_loss_terms_follow_their_definitions_on_a_tiny_case():
     assert abs(parts["code"] - code) < 1e-15
     assert abs(parts["col"] - col) < 1e-15
     assert abs(parts["total"] - (0.5 * e2e + 0.75 * rec + 1.0 * code + 0.5 * col)) < 1e-15
+
+
+def test_softplus_closed_forms_and_inverse():
+    b = codec.SOFTPLUS_BETA
+    assert np.isclose(codec.softplus(0.0), np.log(2.0) / b, rtol=1e-15)
+    assert np.isclose(codec.softplus(5.0), 5.0, rtol=1e-15)       # beta x = 50: exp(-50) below the last bit
+    assert 0.0 < codec.softplus(-5.0) < 1e-22
+    y = np.array([1e-4, 0.01, 0.3, 1.0, 3.0])
+    assert np.allclose(codec.softplus(codec.softplus_inverse(y)), y, rtol=1e-12)
+    x = np.linspace(-1, 1, 41)
+    h = 1e-6
+    assert np.allclose(codec.softplus_grad(x), (codec.softplus(x + h) - codec.softplus(x - h)) / (2 * h), atol=1e-8)
+
+
+def _rand_batch(seed=0, P=24, n=12):
+    rng = np.random.default_rng(seed)
+    R = rng.uniform(0, 1, (P, n))
+    L = rng.uniform(0.2, 1, (P, n))
+    T = rng.uniform(0, 0.1, (3, n))
+    return codec.Batch(R, L, T)
+
+
+def test_gradient_through_softplus_by_finite_differences():
+    bt = _rand_batch()
+    rng = np.random.default_rng(3)
+    Et = rng.normal(-0.1, 0.2, (6, 12))
+    Dt = rng.normal(0.0, 0.2, (12, 6))
+    gE, gD = codec.gradient(codec.softplus(Et), codec.softplus(Dt), bt)
+    gEt, gDt = gE * codec.softplus_grad(Et), gD * codec.softplus_grad(Dt)
+    f = lambda a, b: codec.total_loss(codec.softplus(a), codec.softplus(b), bt)
+    h = 1e-6
+    for (X, G, which) in ((Et, gEt, 0), (Dt, gDt, 1)):
+        for idx in [(0, 0), (2, 5), (5, 11)] if which == 0 else [(0, 0), (7, 3), (11, 5)]:
+            Xp, Xm = X.copy(), X.copy()
+            Xp[idx] += h
+            Xm[idx] -= h
+            num = (f(Xp, Dt) - f(Xm, Dt)) / (2 * h) if which == 0 else (f(Et, Xp) - f(Et, Xm)) / (2 * h)
+            assert np.isclose(G[idx], num, rtol=1e-5, atol=1e-9)
+
+
+def test_first_adam_step_moves_by_lr():
+    bt = _rand_batch(1)
+    rng = np.random.default_rng(4)
+    Et = rng.normal(-0.1, 0.2, (6, 12))
+    Dt = rng.normal(0.0, 0.2, (12, 6))
+    st = codec.adam_init(Et, Dt)
+    lr = 1e-3
+    E2, D2, st2, parts = codec.adam_softplus_step(Et, Dt, st, bt, lr=lr, eps=0.0)
+    gE, gD = codec.gradient(codec.softplus(Et), codec.softplus(Dt), bt)
+    # with bias correction m_hat / sqrt(v_hat) = sign(g) after one step
+    assert np.allclose(E2 - Et, -lr * np.sign(gE), rtol=1e-12, atol=1e-15)
+    assert np.allclose(D2 - Dt, -lr * np.sign(gD), rtol=1e-12, atol=1e-15)
+    assert st2.t == 1 and parts["total"] == codec.total_loss(codec.softplus(Et), codec.softplus(Dt), bt)

@@ -491,6 +491,7 @@ def secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T,
     rows.update(chain_rows(args, hsc, ctx, dev, timed))
     rows.update(upsample_rows(args, hsc, ctx, dev, timed))
     rows.update(pathtrace_rows(args, hsc, ctx, dev, timed))
+    rows.update(codec_sweep_rows(args, hsc, ctx, dev))
     if args.serve_seconds > 0:
         rows.update(serve_rows(args, hsc, ctx, dev))
     return rows
@@ -561,6 +562,60 @@ def pathtrace_rows(args, hsc, ctx, dev, timed):
     s = st.cpu().numpy()
     out["pathtrace_delta_e_latent_vs_spectral"] = {"de2000_mean": float(s[0]), "de2000_p95": float(s[1])}
     return out
+
+
+def codec_sweep_rows(args, hsc, ctx, dev):
+    """The hyper-parameter sweep of the codec fit (Sec. 3.5) on the GPU: 700
+    variants (loss weights on a 7 x 5 x 5 x 4 grid) of the k = 6, n = 81 codec,
+    softplus parameterisation, Adam (lr 1e-3), 128 pairs per mini-batch drawn
+    from the seeded training set; one launch per step for all variants."""
+    import itertools
+    import torch
+    k, g, P, steps = 6, hi.GRID_81, 128, 60
+    ts = hi.training_set(g)
+    n = g[2]
+    grid_w = list(itertools.product([0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 2.0], [0.25, 0.5, 0.75, 1.0, 1.5],
+                                    [0.25, 0.5, 1.0, 1.5, 2.0], [0.25, 0.5, 1.0, 2.0]))
+    V = len(grid_w)
+    t = lambda a, dt=np.float32: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(dev)
+    T = torch.empty(3, n, device=dev)
+    hsc.hsc_cmf_weights(ctx, n, g[0], g[1], T)
+    # band initialisation through the softplus inverse, identical for every variant
+    edges = np.linspace(0, n, k + 1)
+    E0 = np.full((k, n), 1e-3)
+    D0 = np.full((n, k), 1e-3)
+    for i in range(k):
+        lo, hi_ = int(round(edges[i])), max(int(round(edges[i + 1])), int(round(edges[i])) + 1)
+        E0[i, lo:hi_] = 1.0 / (hi_ - lo)
+        D0[lo:hi_, i] = 1.0
+    inv = lambda y: (10.0 * y + np.log(-np.expm1(-10.0 * y))) / 10.0
+    Et = t(np.broadcast_to(inv(E0), (V, k, n)))
+    Dt = t(np.broadcast_to(inv(D0), (V, n, k)))
+    mom = [torch.zeros_like(Et), torch.zeros_like(Et), torch.zeros_like(Dt), torch.zeros_like(Dt)]
+    W = t(np.asarray(grid_w))
+    R, L = t(ts.R), t(ts.L)
+    rng = np.random.default_rng(hi.MASTER_SEED + 9)
+    batches = []
+    for _ in range(steps):
+        sel = rng.integers(0, len(ts.pair_r), P)
+        batches.append((t(ts.pair_r[sel], np.int32), t(ts.pair_l[sel], np.int32), t(ts.pair_scale[sel])))
+    losses = torch.empty(V, 5, device=dev)
+    first = None
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for s_, (pr, pl, ps) in enumerate(batches, start=1):
+        hsc.hsc_codec_fit_step(ctx, R, L, pr, pl, ps, T, W, Et, Dt, *mom, step=s_, lr=1e-3, losses_out=losses)
+        if s_ == 1:
+            first = losses[:, 0].clone()
+    b.record()
+    b.synchronize()
+    hsc.hsc_sync(ctx)
+    ms = a.elapsed_time(b)
+    drop = (losses[:, 0] / first).cpu().numpy()
+    return {"codec_sweep_700": {"variants": V, "steps": steps, "pairs_per_step": P, "ms_per_step": ms / steps,
+                                "variant_steps_per_s": V * steps / (ms * 1e-3),
+                                "loss_ratio_last_over_first_median": float(np.median(drop))}}
 
 
 def serve_rows(args, hsc, ctx, dev):

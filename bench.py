@@ -55,6 +55,8 @@ def parse():
                     help="load tuned launch configurations from this file if it exists, save them there after the run")
     ap.add_argument("--serve-seconds", type=float, default=8.0,
                     help="length of the Poisson request stream served (0 = skip); the first quarter is warm-up")
+    ap.add_argument("--sweep-epochs", type=int, default=150,
+                    help="epoch cap of the 700-variant codec sweep (0 = skip the sweep row)")
     return ap.parse_args()
 
 
@@ -491,7 +493,8 @@ def secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T,
     rows.update(chain_rows(args, hsc, ctx, dev, timed))
     rows.update(upsample_rows(args, hsc, ctx, dev, timed))
     rows.update(pathtrace_rows(args, hsc, ctx, dev, timed))
-    rows.update(codec_sweep_rows(args, hsc, ctx, dev))
+    if args.sweep_epochs > 0:
+        rows.update(codec_sweep_rows(args, hsc, ctx, dev))
     if args.serve_seconds > 0:
         rows.update(serve_rows(args, hsc, ctx, dev))
     return rows
@@ -565,57 +568,59 @@ def pathtrace_rows(args, hsc, ctx, dev, timed):
 
 
 def codec_sweep_rows(args, hsc, ctx, dev):
-    """The hyper-parameter sweep of the codec fit (Sec. 3.5) on the GPU: 700
-    variants (loss weights on a 7 x 5 x 5 x 4 grid) of the k = 6, n = 81 codec,
-    softplus parameterisation, Adam (lr 1e-3), 128 pairs per mini-batch drawn
-    from the seeded training set; one launch per step for all variants."""
-    import itertools
+    """The hyper-parameter sweep of the codec fit (Sec. 3.5) on the GPU: the
+    700 loss-weight variants of the k = 6, n = 81 codec, softplus
+    parameterisation, Adam (lr 1e-3), mini-batches of 128 of the 4096 training
+    pairs (32 per epoch), at most 150 epochs with early stopping (patience 15)
+    on a 256-pair validation batch; then every kept codec is scored by 500
+    depth-3 chains (mean CIE94 over the depths) and the best is selected.  The
+    projected-gradient codec used by the shading rows is scored on the same
+    chains beside it."""
     import torch
-    k, g, P, steps = 6, hi.GRID_81, 128, 60
+    from paper_2602_18741_gb300 import sweep
+    k, g, epochs, patience = 6, hi.GRID_81, args.sweep_epochs, 15
     ts = hi.training_set(g)
     n = g[2]
-    grid_w = list(itertools.product([0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 2.0], [0.25, 0.5, 0.75, 1.0, 1.5],
-                                    [0.25, 0.5, 1.0, 1.5, 2.0], [0.25, 0.5, 1.0, 2.0]))
-    V = len(grid_w)
+    sched = hi.sweep_schedule(ts, epochs=epochs, batch=128, val_pairs=256)
     t = lambda a, dt=np.float32: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(dev)
     T = torch.empty(3, n, device=dev)
     hsc.hsc_cmf_weights(ctx, n, g[0], g[1], T)
-    # band initialisation through the softplus inverse, identical for every variant
-    edges = np.linspace(0, n, k + 1)
-    E0 = np.full((k, n), 1e-3)
-    D0 = np.full((n, k), 1e-3)
-    for i in range(k):
-        lo, hi_ = int(round(edges[i])), max(int(round(edges[i + 1])), int(round(edges[i])) + 1)
-        E0[i, lo:hi_] = 1.0 / (hi_ - lo)
-        D0[lo:hi_, i] = 1.0
-    inv = lambda y: (10.0 * y + np.log(-np.expm1(-10.0 * y))) / 10.0
-    Et = t(np.broadcast_to(inv(E0), (V, k, n)))
-    Dt = t(np.broadcast_to(inv(D0), (V, n, k)))
-    mom = [torch.zeros_like(Et), torch.zeros_like(Et), torch.zeros_like(Dt), torch.zeros_like(Dt)]
-    W = t(np.asarray(grid_w))
-    R, L = t(ts.R), t(ts.L)
-    rng = np.random.default_rng(hi.MASTER_SEED + 9)
-    batches = []
-    for _ in range(steps):
-        sel = rng.integers(0, len(ts.pair_r), P)
-        batches.append((t(ts.pair_r[sel], np.int32), t(ts.pair_l[sel], np.int32), t(ts.pair_scale[sel])))
-    losses = torch.empty(V, 5, device=dev)
-    first = None
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    for s_, (pr, pl, ps) in enumerate(batches, start=1):
-        hsc.hsc_codec_fit_step(ctx, R, L, pr, pl, ps, T, W, Et, Dt, *mom, step=s_, lr=1e-3, losses_out=losses)
-        if s_ == 1:
-            first = losses[:, 0].clone()
-    b.record()
-    b.synchronize()
+    W = hi.sweep_weight_grid()
+    V = W.shape[0]
+    E0, D0 = sweep.band_init_raw(k, n)
+    Et0 = t(np.broadcast_to(E0, (V, k, n)))
+    Dt0 = t(np.broadcast_to(D0, (V, n, k)))
+    R, L, Wd = t(ts.R), t(ts.L), t(W)
+    train = (t(sched.train_r, np.int32), t(sched.train_l, np.int32), t(sched.train_s))
+    val = (t(sched.val_r, np.int32), t(sched.val_l, np.int32), t(sched.val_s))
+    res = sweep.fit_variants(hsc, ctx, R, L, T, Wd, train, val, Et0, Dt0, epochs=epochs, patience=patience, lr=1e-3)
+    held = hi.training_set(g, seed=hi.MASTER_SEED + 200)
+    rng = np.random.default_rng(hi.MASTER_SEED + 10)
+    C = 500
+    cl = t(rng.integers(0, held.L.shape[0], C), np.int32)
+    cr = t(rng.integers(0, held.R.shape[0], (C, 3)), np.int32)
+    Rh, Lh = t(held.R), t(held.L)
+    res = sweep.score_variants(hsc, ctx, res, R, L, T, Wd, val, Rh, Lh, cl, cr)
+    # the projected-gradient codec on the same chains
+    Ep, Dp = hi.load_codec(k, n)
+    d94 = torch.empty(3, C, device=dev)
+    d00 = torch.empty(3, C, device=dev)
+    stp = torch.zeros(12, dtype=torch.float64, device=dev)
+    hsc.hsc_chain_eval(ctx, Rh, Lh, t(Ep), t(Dp), T, cl, cr, d94, d00, stp)
     hsc.hsc_sync(ctx)
-    ms = a.elapsed_time(b)
-    drop = (losses[:, 0] / first).cpu().numpy()
-    return {"codec_sweep_700": {"variants": V, "steps": steps, "pairs_per_step": P, "ms_per_step": ms / steps,
-                                "variant_steps_per_s": V * steps / (ms * 1e-3),
-                                "loss_ratio_last_over_first_median": float(np.median(drop))}}
+    pg = stp.cpu().numpy().reshape(3, 4)
+    ep = res.epochs.cpu().numpy()
+    sel = res.selected
+    return {"codec_sweep_700": {
+        "variants": V, "max_epochs": epochs, "patience": patience, "batches_per_epoch": int(sched.train_r.shape[1]),
+        "epochs_run": res.epochs_run, "epochs_mean": float(ep.mean()), "epochs_max": int(ep.max()),
+        "stopped_early": int((ep < epochs).sum()), "step_launches": res.steps, "variant_steps": res.variant_steps,
+        "train_s": res.seconds["train"], "score_s": res.seconds["score"],
+        "variant_steps_per_s": res.variant_steps / res.seconds["train"],
+        "selected_weights_e2e_rec_code_col": [float(x) for x in W[sel]] if sel >= 0 else None,
+        "selected_de94_mean_per_depth": [float(x) for x in res.chain_stats[sel, :, 0]] if sel >= 0 else None,
+        "median_score_de94": float(np.nanmedian(res.scores)),
+        "projected_gradient_codec_de94_mean_per_depth": [float(x) for x in pg[:, 0]]}}
 
 
 def serve_rows(args, hsc, ctx, dev):

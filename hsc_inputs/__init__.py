@@ -287,6 +287,52 @@ def training_set(grid_spec, seed: int = MASTER_SEED + 100, n_smooth: int = 1024,
     return TrainingSet(R, L, pr, pl, ps)
 
 
+def sweep_weight_grid() -> np.ndarray:
+    """The loss-weight grid of the codec sweep (Sec. 3.5) as (700, 4) float32
+    rows (lambda_e2e, lambda_rec, lambda_code, lambda_col): e2e 0-2 by 0.5, rec
+    0-3 by 0.5, code 0-1 by 0.25, col 0.25-1 by 0.25.  The grid as printed has
+    7 x 5 x 5 x 5 = 875 points but is said to give 700 variants; leaving out
+    lambda_col = 0 gives exactly 700 (and no variant without a colour term)."""
+    e2e = np.arange(5) * 0.5
+    rec = np.arange(7) * 0.5
+    code = np.arange(5) * 0.25
+    col = (np.arange(4) + 1) * 0.25
+    g = np.stack(np.meshgrid(e2e, rec, code, col, indexing="ij"), axis=-1).reshape(-1, 4)
+    return g.astype(np.float32)
+
+
+@dataclass
+class SweepSchedule:
+    """Mini-batches of every epoch and the validation batch of a codec sweep.
+    train_r, train_l: (epochs, batches, batch) int32 rows of R and L;
+    train_s: the same shape, float32 light scales; val_r, val_l, val_s: the
+    validation pairs (new pairings of the training spectra)."""
+    train_r: np.ndarray
+    train_l: np.ndarray
+    train_s: np.ndarray
+    val_r: np.ndarray
+    val_l: np.ndarray
+    val_s: np.ndarray
+
+
+def sweep_schedule(ts: TrainingSet, epochs: int, batch: int = 128, val_pairs: int = 256,
+                   seed: int = MASTER_SEED + 300) -> SweepSchedule:
+    """Seeded shuffles of the training pairs, one per epoch, cut into
+    ``len(pairs) // batch`` whole mini-batches (a trailing partial batch is
+    dropped), and ``val_pairs`` validation pairs drawn like the training pairs
+    (reflectance and light rows uniform, light scale U[0.5, 1])."""
+    r_shuffle, r_val = streams(seed, 2)
+    P = len(ts.pair_r)
+    nb = P // batch
+    order = np.stack([r_shuffle.permutation(P)[:nb * batch].reshape(nb, batch) for _ in range(epochs)])
+    vr = r_val.integers(0, ts.R.shape[0], size=val_pairs)
+    vl = r_val.integers(0, ts.L.shape[0], size=val_pairs)
+    vs = r_val.uniform(0.5, 1.0, size=val_pairs)
+    return SweepSchedule(ts.pair_r[order].astype(np.int32), ts.pair_l[order].astype(np.int32),
+                         ts.pair_scale[order].astype(np.float32), vr.astype(np.int32), vl.astype(np.int32),
+                         vs.astype(np.float32))
+
+
 UPSAMPLER_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "upsampler")
 
 

@@ -389,6 +389,8 @@ HSC_API hsc_status hsc_path_trace(hsc_ctx* ctx, const float* quads, int n_quads,
  *   weights: device variants x 4;  Et: device variants x k x n;  Dt: device
  *   variants x n x k;  mE, vE, mD, vD: Adam moments of the same shapes (zero
  *   before step 1); updated in place.  step: 1-based (bias correction).
+ *   active: device `variants` int32 flags or NULL; a variant whose flag is
+ *   0 is skipped (parameters, moments and outputs untouched).
  *   losses_out: device variants x 5 (total, e2e, rec, code, col) at the
  *   parameters before the step, or NULL;  grad_out: device variants x 2kn,
  *   dL/dE~ then dL/dD~, or NULL.
@@ -398,7 +400,38 @@ HSC_API hsc_status hsc_codec_fit_step(hsc_ctx* ctx, int variants, int k, int n, 
                                       const float* pair_scale, int pairs, const float* T, const float* weights,
                                       float* Et, float* Dt, float* mE, float* vE, float* mD, float* vD, int step,
                                       float lr, float beta1, float beta2, float eps, float softplus_beta,
-                                      float* losses_out, float* grad_out, void* stream);
+                                      const int32_t* active, float* losses_out, float* grad_out, void* stream);
+
+/* The Eq. 6 loss terms of every active variant at its current parameters on
+ * one batch (the validation loss of the sweep, Sec. 3.5), without a step;
+ * arguments as hsc_codec_fit_step.  E_out: device variants x k x n
+ * softplus(E~), D_out: device variants x n x k softplus(D~) (each NULL or
+ * written; the decoder and encoder the selection stage evaluates).  At least
+ * one output must be given.                                                 */
+HSC_API hsc_status hsc_codec_fit_eval(hsc_ctx* ctx, int variants, int k, int n, const float* R_all,
+                                      const float* L_all, const int32_t* pair_r, const int32_t* pair_l,
+                                      const float* pair_scale, int pairs, const float* T, const float* weights,
+                                      const float* Et, const float* Dt, float softplus_beta, const int32_t* active,
+                                      float* losses_out, float* E_out, float* D_out, void* stream);
+
+/* Early stopping of the sweep (Sec. 3.5: training stops after `patience`
+ * epochs without a lower validation loss).  Per variant v with active[v] != 0:
+ * if val_loss[v * val_stride] < best_loss[v] the loss becomes best_loss[v],
+ * wait[v] = 0 and Et[v], Dt[v] are copied to best_Et[v], best_Dt[v];
+ * otherwise wait[v] += 1 and active[v] = 0 once wait[v] >= patience.  A NaN
+ * loss is never an improvement.  Inactive variants are left as they are.
+ *   Et, best_Et: device variants x k x n;  Dt, best_Dt: variants x n x k;
+ *   best_loss: device variants float32 (+inf before the first epoch);  wait,
+ *   active: device variants int32 (0 and 1 before the first epoch);
+ *   epochs: device variants int32 or NULL, incremented for every variant
+ *   active at the update (the number of epochs it trained);
+ *   n_active_out: device int32 or NULL: the number of active variants after
+ *   the update.  Uses one word of the context's scratch; launches that share a
+ *   context must not overlap.                                               */
+HSC_API hsc_status hsc_codec_fit_track(hsc_ctx* ctx, int variants, int k, int n, const float* val_loss,
+                                       int val_stride, const float* Et, const float* Dt, float* best_Et,
+                                       float* best_Dt, float* best_loss, int32_t* wait, int32_t* active,
+                                       int32_t* epochs, int patience, int32_t* n_active_out, void* stream);
 
 /* --------------------------------------------------------- multi-bounce chains */
 

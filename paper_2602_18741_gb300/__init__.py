@@ -100,7 +100,11 @@ _SIGS = {
                         _i32, _vp, _vp, _vp, _vp], _i32),
     "hsc_codec_fit_step": ([_vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                             _vp, _i32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
-                            _vp, _vp, _vp], _i32),
+                            _vp, _vp, _vp, _vp], _i32),
+    "hsc_codec_fit_eval": ([_vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp,
+                            ctypes.c_float, _vp, _vp, _vp, _vp, _vp], _i32),
+    "hsc_codec_fit_track": ([_vp, _i32, _i32, _i32, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp,
+                             _vp], _i32),
     "hsc_batch_create": ([_vp, ctypes.POINTER(_Frame), _i32, ctypes.POINTER(_vp)], _i32),
     "hsc_batch_shade": ([_vp, _vp, _vp], _i32),
     "hsc_batch_destroy": ([_vp], None),
@@ -467,27 +471,78 @@ def hsc_codec_fit_step(ctx: Context, R_all: torch.Tensor, L_all: torch.Tensor, p
                        pair_l: torch.Tensor, pair_scale: torch.Tensor, T: torch.Tensor, weights: torch.Tensor,
                        Et: torch.Tensor, Dt: torch.Tensor, mE: torch.Tensor, vE: torch.Tensor, mD: torch.Tensor,
                        vD: torch.Tensor, step: int, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
-                       eps: float = 1e-8, softplus_beta: float = 10.0, losses_out: Optional[torch.Tensor] = None,
-                       grad_out: Optional[torch.Tensor] = None, stream=None):
+                       eps: float = 1e-8, softplus_beta: float = 10.0, active: Optional[torch.Tensor] = None,
+                       losses_out: Optional[torch.Tensor] = None, grad_out: Optional[torch.Tensor] = None,
+                       stream=None):
     """One Adam step of the softplus-parameterised codec for every variant; see include/hsc.h."""
-    V, k, n = Et.shape
+    V, k, n = _fit_shapes(R_all, L_all, pair_r, pair_l, pair_scale, T, weights, Et, Dt, active)
     P = pair_r.shape[0]
-    if Dt.shape != (V, n, k) or weights.shape != (V, 4) or T.shape != (3, n) or R_all.shape[1] != n \
-            or L_all.shape[1] != n or pair_l.shape != (P,) or pair_scale.shape != (P,):
-        raise ValueError("shapes: Et (V,k,n), Dt (V,n,k), weights (V,4), T (3,n), rows of n, pairs (P,)")
     for m in (mE, vE):
         if m.shape != Et.shape:
             raise ValueError("moments of E~ must match Et")
     for m in (mD, vD):
         if m.shape != Dt.shape:
             raise ValueError("moments of D~ must match Dt")
-    if pair_r.dtype != torch.int32 or pair_l.dtype != torch.int32:
-        raise ValueError("pair indices must be int32")
     _check(_lib.hsc_codec_fit_step(ctx.handle, int(V), int(k), int(n), _ptr(R_all), _ptr(L_all), _ptr(pair_r),
                                    _ptr(pair_l), _ptr(pair_scale), int(P), _ptr(T), _ptr(weights), _ptr(Et),
                                    _ptr(Dt), _ptr(mE), _ptr(vE), _ptr(mD), _ptr(vD), int(step), float(lr),
-                                   float(beta1), float(beta2), float(eps), float(softplus_beta), _ptr(losses_out),
-                                   _ptr(grad_out), _stream(stream)))
+                                   float(beta1), float(beta2), float(eps), float(softplus_beta), _ptr(active),
+                                   _ptr(losses_out), _ptr(grad_out), _stream(stream)))
+
+
+def _fit_shapes(R_all, L_all, pair_r, pair_l, pair_scale, T, weights, Et, Dt, active):
+    V, k, n = Et.shape
+    P = pair_r.shape[0]
+    if Dt.shape != (V, n, k) or weights.shape != (V, 4) or T.shape != (3, n) or R_all.shape[1] != n \
+            or L_all.shape[1] != n or pair_l.shape != (P,) or pair_scale.shape != (P,):
+        raise ValueError("shapes: Et (V,k,n), Dt (V,n,k), weights (V,4), T (3,n), rows of n, pairs (P,)")
+    if pair_r.dtype != torch.int32 or pair_l.dtype != torch.int32:
+        raise ValueError("pair indices must be int32")
+    if active is not None and (active.shape != (V,) or active.dtype != torch.int32):
+        raise ValueError("active: (V,) int32")
+    return V, k, n
+
+
+def hsc_codec_fit_eval(ctx: Context, R_all: torch.Tensor, L_all: torch.Tensor, pair_r: torch.Tensor,
+                       pair_l: torch.Tensor, pair_scale: torch.Tensor, T: torch.Tensor, weights: torch.Tensor,
+                       Et: torch.Tensor, Dt: torch.Tensor, softplus_beta: float = 10.0,
+                       active: Optional[torch.Tensor] = None, losses_out: Optional[torch.Tensor] = None,
+                       E_out: Optional[torch.Tensor] = None, D_out: Optional[torch.Tensor] = None, stream=None):
+    """Loss terms (and softplus(E~), softplus(D~)) of every active variant, no step; see include/hsc.h."""
+    V, k, n = _fit_shapes(R_all, L_all, pair_r, pair_l, pair_scale, T, weights, Et, Dt, active)
+    if (losses_out is not None and losses_out.shape != (V, 5)) or (E_out is not None and E_out.shape != (V, k, n)) \
+            or (D_out is not None and D_out.shape != (V, n, k)):
+        raise ValueError("outputs: losses (V,5), E (V,k,n), D (V,n,k)")
+    _check(_lib.hsc_codec_fit_eval(ctx.handle, int(V), int(k), int(n), _ptr(R_all), _ptr(L_all), _ptr(pair_r),
+                                   _ptr(pair_l), _ptr(pair_scale), int(pair_r.shape[0]), _ptr(T), _ptr(weights),
+                                   _ptr(Et), _ptr(Dt), float(softplus_beta), _ptr(active), _ptr(losses_out),
+                                   _ptr(E_out), _ptr(D_out), _stream(stream)))
+
+
+def hsc_codec_fit_track(ctx: Context, val_loss: torch.Tensor, Et: torch.Tensor, Dt: torch.Tensor,
+                        best_Et: torch.Tensor, best_Dt: torch.Tensor, best_loss: torch.Tensor, wait: torch.Tensor,
+                        active: torch.Tensor, patience: int, epochs: Optional[torch.Tensor] = None,
+                        n_active_out: Optional[torch.Tensor] = None, stream=None):
+    """Early-stopping update of every variant; val_loss is (V,) or the (V, 5) loss table (column 0 is used);
+    see include/hsc.h."""
+    V, k, n = Et.shape
+    if Dt.shape != (V, n, k) or best_Et.shape != Et.shape or best_Dt.shape != Dt.shape:
+        raise ValueError("best parameters must match Et (V,k,n) and Dt (V,n,k)")
+    if best_loss.shape != (V,) or wait.shape != (V,) or active.shape != (V,) or wait.dtype != torch.int32 \
+            or active.dtype != torch.int32:
+        raise ValueError("best_loss (V,) float32; wait, active (V,) int32")
+    if epochs is not None and (epochs.shape != (V,) or epochs.dtype != torch.int32):
+        raise ValueError("epochs: (V,) int32")
+    if val_loss.shape == (V,):
+        stride = 1
+    elif val_loss.dim() == 2 and val_loss.shape[0] == V:
+        stride = val_loss.shape[1]
+    else:
+        raise ValueError("val_loss: (V,) or (V, m)")
+    _check(_lib.hsc_codec_fit_track(ctx.handle, int(V), int(k), int(n), _ptr(val_loss), int(stride), _ptr(Et),
+                                    _ptr(Dt), _ptr(best_Et), _ptr(best_Dt), _ptr(best_loss), _ptr(wait),
+                                    _ptr(active), _ptr(epochs), int(patience), _ptr(n_active_out),
+                                    _stream(stream)))
 
 
 def hsc_chain_eval(ctx: Context, refl: torch.Tensor, lights: torch.Tensor, E: torch.Tensor, D: torch.Tensor,

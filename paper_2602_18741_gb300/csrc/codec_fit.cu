@@ -15,7 +15,12 @@
 //      dL/dD, dL/dzRL, dL/dzR, dL/dzL and dL/dE, accumulated in per-warp
 //      copies of the gradient that are summed in warp order (deterministic);
 //   D. the softplus chain rule and the Adam update of every parameter.
-// The loss terms written are those at the parameters before the step.
+// The loss terms written are those at the parameters before the step.  The
+// same kernel in evaluation mode stops after B (validation losses, and E, D
+// for the selection stage); variants whose `active` flag is 0 return at once.
+// hsc_codec_fit_track keeps the early-stopping state of every variant
+// (Sec. 3.5: best validation loss, epochs without improvement, the best
+// parameters) and counts the variants still training.
 #include "common.cuh"
 
 namespace hsc {
@@ -47,6 +52,10 @@ struct FitArgs {
   float lr, b1, b2, eps, beta;
   float* losses;        // V x 5: total, e2e, rec, code, col (nullable)
   float* grad;          // V x (k n + n k): dL/dE~ then dL/dD~ (nullable)
+  const int32_t* active;  // V flags (nullable): 0 = variant skipped
+  int eval_only;        // 1: losses (and E, D) only, no update
+  float* E_out;         // V x k x n softplus(E~) (evaluation mode, nullable)
+  float* D_out;         // V x n x k softplus(D~) (evaluation mode, nullable)
 };
 
 __device__ __forceinline__ float softplus_f(float x, float beta) {
@@ -79,6 +88,7 @@ __global__ void __launch_bounds__(kFitThreads) codec_fit_kernel(const FitArgs a)
   constexpr int k = K;
   const int n = a.n, P = a.P, v = blockIdx.x;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if (a.active && __ldg(a.active + v) == 0) return;  // uniform over the CTA
   float* sE = sm;                       // k x n
   float* sD = sE + k * n;               // n x k
   float* sT = sD + n * k;               // 3 x n
@@ -101,7 +111,8 @@ __global__ void __launch_bounds__(kFitThreads) codec_fit_kernel(const FitArgs a)
   for (int i = t; i < k * n; i += kFitThreads) sE[i] = softplus_f(__ldg(Et + i), a.beta);
   for (int i = t; i < n * k; i += kFitThreads) sD[i] = softplus_f(__ldg(Dt + i), a.beta);
   for (int i = t; i < 3 * n; i += kFitThreads) sT[i] = __ldg(a.T + i);
-  for (int i = t; i < kFitWarps * G; i += kFitThreads) gw[i] = 0.0f;
+  if (!a.eval_only)
+    for (int i = t; i < kFitWarps * G; i += kFitThreads) gw[i] = 0.0f;
   __syncthreads();
   for (int idx = t; idx < P * k; idx += kFitThreads) {
     const int p = idx / k, c = idx - p * k;
@@ -208,6 +219,13 @@ __global__ void __launch_bounds__(kFitThreads) codec_fit_kernel(const FitArgs a)
     lo[3] = L_code;
     lo[4] = L_col;
   }
+  if (a.eval_only) {
+    if (a.E_out)
+      for (int i = t; i < k * n; i += kFitThreads) a.E_out[(int64_t)v * k * n + i] = sE[i];
+    if (a.D_out)
+      for (int i = t; i < n * k; i += kFitThreads) a.D_out[(int64_t)v * n * k + i] = sD[i];
+    return;
+  }
 
   // C. gradients, per pair, into this warp's copy
   float* gE = gw + warp * G;  // k x n
@@ -311,31 +329,115 @@ __global__ void __launch_bounds__(kFitThreads) codec_fit_kernel(const FitArgs a)
   }
 }
 
+struct TrackArgs {
+  int V, GE, GD;            // variants, k n, n k
+  const float* val;         // validation loss of variant v at val[v * val_stride]
+  int val_stride;
+  const float* Et;
+  const float* Dt;
+  float* best_Et;
+  float* best_Dt;
+  float* best_loss;         // V
+  int32_t* wait;            // V epochs without improvement
+  int32_t* active;          // V
+  int32_t* epochs;          // V updates seen while active (nullable)
+  int patience;
+  int32_t* n_active;        // nullable: variants still active after this update
+  unsigned int* ticket;     // arrival counter, zero between launches
+};
+
+constexpr int kTrackThreads = 256;
+
+// One CTA per variant: an active variant whose validation loss is below its
+// best so far takes it as the new best and copies its parameters; otherwise
+// its count of epochs without improvement grows and reaching `patience`
+// deactivates it.  The last CTA to arrive counts the active flags and resets
+// the ticket.
+__global__ void __launch_bounds__(kTrackThreads) codec_track_kernel(const TrackArgs a) {
+  __shared__ int s_improved, s_last;
+  __shared__ int s_part[kTrackThreads / 32];
+  const int v = blockIdx.x, t = threadIdx.x;
+  if (t == 0) {
+    int imp = 0;
+    if (a.active[v]) {
+      if (a.epochs) a.epochs[v] += 1;
+      const float val = a.val[(int64_t)v * a.val_stride];
+      if (val < a.best_loss[v]) {
+        a.best_loss[v] = val;
+        a.wait[v] = 0;
+        imp = 1;
+      } else {
+        const int w = a.wait[v] + 1;
+        a.wait[v] = w;
+        if (w >= a.patience) a.active[v] = 0;
+      }
+    }
+    s_improved = imp;
+  }
+  __syncthreads();
+  if (s_improved) {
+    for (int i = t; i < a.GE; i += kTrackThreads) a.best_Et[(int64_t)v * a.GE + i] = a.Et[(int64_t)v * a.GE + i];
+    for (int i = t; i < a.GD; i += kTrackThreads) a.best_Dt[(int64_t)v * a.GD + i] = a.Dt[(int64_t)v * a.GD + i];
+  }
+  if (t == 0) {
+    __threadfence();
+    s_last = atomicAdd(a.ticket, 1u) == (unsigned)(a.V - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  int cnt = 0;
+  const volatile int32_t* act = a.active;
+  for (int i = t; i < a.V; i += kTrackThreads) cnt += act[i] != 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((t & 31) == 0) s_part[t >> 5] = cnt;
+  __syncthreads();
+  if (t == 0) {
+    int total = 0;
+    for (int q = 0; q < kTrackThreads / 32; ++q) total += s_part[q];
+    if (a.n_active) *a.n_active = total;
+    atomicExch(a.ticket, 0u);
+  }
+}
+
+// Launches codec_fit_kernel for the arguments in `a` (validated by the caller).
+hsc_status launch_fit(const FitArgs& a, cudaStream_t stream) {
+  const int k = a.k, n = a.n, P = a.P;
+  const int G = 2 * k * n;
+  const size_t grad_floats = a.eval_only ? 0 : (size_t)kFitWarps * G;
+  const size_t smem = sizeof(float) * ((size_t)2 * k * n + 3 * n + 3 * (size_t)P * k + 6 * (size_t)P +
+                                       kFitWarps * 8 + grad_floats);
+  auto kern = k == 3 ? codec_fit_kernel<3>
+              : k == 6 ? codec_fit_kernel<6>
+              : k == 9 ? codec_fit_kernel<9>
+              : k == 12 ? codec_fit_kernel<12>
+                        : codec_fit_kernel<15>;
+  HSC_REQUIRE(smem <= 227 * 1024, "shared memory plan of %zu bytes too large", smem);
+  if (smem > 48 * 1024) HSC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<(unsigned)a.V, kFitThreads, smem, stream>>>(a);
+  return check_launch("codec_fit_kernel");
+}
+
 }  // namespace
 
 }  // namespace hsc
 
-extern "C" hsc_status hsc_codec_fit_step(hsc_ctx* ctx, int variants, int k, int n, const float* R_all,
-                                         const float* L_all, const int32_t* pair_r, const int32_t* pair_l,
-                                         const float* pair_scale, int pairs, const float* T, const float* weights,
-                                         float* Et, float* Dt, float* mE, float* vE, float* mD, float* vD, int step,
-                                         float lr, float beta1, float beta2, float eps, float softplus_beta,
-                                         float* losses_out, float* grad_out, void* stream) {
-  hsc::clear_error();
-  HSC_CHECK_CTX(ctx);
+namespace {
+
+hsc_status check_fit_shape(int variants, int k, int n, int pairs) {
   HSC_REQUIRE(variants >= 0, "negative variant count");
   HSC_REQUIRE(k >= 3 && k <= hsc::kFitMaxK && k % 3 == 0, "k=%d must be a multiple of 3 in [3, %d]", k,
               hsc::kFitMaxK);
   HSC_REQUIRE(n >= 1 && n <= hsc::kFitMaxN, "n=%d out of range [1, %d]", n, hsc::kFitMaxN);
   HSC_REQUIRE(pairs >= 1 && pairs <= hsc::kFitMaxP, "pairs=%d out of range [1, %d]", pairs, hsc::kFitMaxP);
-  HSC_REQUIRE(step >= 1, "step numbers start at 1");
-  HSC_REQUIRE(lr > 0.0f && beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f && eps >= 0.0f &&
-                  softplus_beta > 0.0f,
-              "invalid optimiser settings");
-  if (variants == 0) return HSC_OK;
-  HSC_REQUIRE(R_all && L_all && pair_r && pair_l && pair_scale && T && weights && Et && Dt && mE && vE && mD && vD,
-              "null pointer");
-  HSC_GUARD(ctx);
+  return HSC_OK;
+}
+
+hsc::FitArgs fit_args(int variants, int k, int n, const float* R_all, const float* L_all, const int32_t* pair_r,
+                      const int32_t* pair_l, const float* pair_scale, int pairs, const float* T,
+                      const float* weights, const float* Et, const float* Dt, float softplus_beta,
+                      const int32_t* active) {
   hsc::FitArgs a{};
   a.V = variants;
   a.k = k;
@@ -348,8 +450,34 @@ extern "C" hsc_status hsc_codec_fit_step(hsc_ctx* ctx, int variants, int k, int 
   a.pair_scale = pair_scale;
   a.T = T;
   a.w = weights;
-  a.Et = Et;
-  a.Dt = Dt;
+  a.Et = const_cast<float*>(Et);
+  a.Dt = const_cast<float*>(Dt);
+  a.beta = softplus_beta;
+  a.active = active;
+  return a;
+}
+
+}  // namespace
+
+extern "C" hsc_status hsc_codec_fit_step(hsc_ctx* ctx, int variants, int k, int n, const float* R_all,
+                                         const float* L_all, const int32_t* pair_r, const int32_t* pair_l,
+                                         const float* pair_scale, int pairs, const float* T, const float* weights,
+                                         float* Et, float* Dt, float* mE, float* vE, float* mD, float* vD, int step,
+                                         float lr, float beta1, float beta2, float eps, float softplus_beta,
+                                         const int32_t* active, float* losses_out, float* grad_out, void* stream) {
+  hsc::clear_error();
+  HSC_CHECK_CTX(ctx);
+  HSC_TRY(check_fit_shape(variants, k, n, pairs));
+  HSC_REQUIRE(step >= 1, "step numbers start at 1");
+  HSC_REQUIRE(lr > 0.0f && beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f && eps >= 0.0f &&
+                  softplus_beta > 0.0f,
+              "invalid optimiser settings");
+  if (variants == 0) return HSC_OK;
+  HSC_REQUIRE(R_all && L_all && pair_r && pair_l && pair_scale && T && weights && Et && Dt && mE && vE && mD && vD,
+              "null pointer");
+  HSC_GUARD(ctx);
+  hsc::FitArgs a = fit_args(variants, k, n, R_all, L_all, pair_r, pair_l, pair_scale, pairs, T, weights, Et, Dt,
+                            softplus_beta, active);
   a.mE = mE;
   a.vE = vE;
   a.mD = mD;
@@ -359,20 +487,64 @@ extern "C" hsc_status hsc_codec_fit_step(hsc_ctx* ctx, int variants, int k, int 
   a.b1 = beta1;
   a.b2 = beta2;
   a.eps = eps;
-  a.beta = softplus_beta;
   a.losses = losses_out;
   a.grad = grad_out;
-  const int G = 2 * k * n;
-  const size_t smem =
-      sizeof(float) * ((size_t)2 * k * n + 3 * n + 3 * (size_t)pairs * k + 6 * (size_t)pairs +
-                       hsc::kFitWarps * 8 + (size_t)hsc::kFitWarps * G);
-  auto kern = k == 3 ? hsc::codec_fit_kernel<3>
-              : k == 6 ? hsc::codec_fit_kernel<6>
-              : k == 9 ? hsc::codec_fit_kernel<9>
-              : k == 12 ? hsc::codec_fit_kernel<12>
-                        : hsc::codec_fit_kernel<15>;
-  if (smem > 48 * 1024) HSC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  HSC_REQUIRE(smem <= 227 * 1024, "shared memory plan of %zu bytes too large", smem);
-  kern<<<(unsigned)variants, hsc::kFitThreads, smem, hsc::as_stream(stream)>>>(a);
-  return hsc::check_launch("codec_fit_kernel");
+  return hsc::launch_fit(a, hsc::as_stream(stream));
+}
+
+extern "C" hsc_status hsc_codec_fit_eval(hsc_ctx* ctx, int variants, int k, int n, const float* R_all,
+                                         const float* L_all, const int32_t* pair_r, const int32_t* pair_l,
+                                         const float* pair_scale, int pairs, const float* T, const float* weights,
+                                         const float* Et, const float* Dt, float softplus_beta,
+                                         const int32_t* active, float* losses_out, float* E_out, float* D_out,
+                                         void* stream) {
+  hsc::clear_error();
+  HSC_CHECK_CTX(ctx);
+  HSC_TRY(check_fit_shape(variants, k, n, pairs));
+  HSC_REQUIRE(softplus_beta > 0.0f, "softplus beta must be positive");
+  if (variants == 0) return HSC_OK;
+  HSC_REQUIRE(R_all && L_all && pair_r && pair_l && pair_scale && T && weights && Et && Dt, "null pointer");
+  HSC_REQUIRE(losses_out || E_out || D_out, "nothing to write");
+  HSC_GUARD(ctx);
+  hsc::FitArgs a = fit_args(variants, k, n, R_all, L_all, pair_r, pair_l, pair_scale, pairs, T, weights, Et, Dt,
+                            softplus_beta, active);
+  a.eval_only = 1;
+  a.losses = losses_out;
+  a.E_out = E_out;
+  a.D_out = D_out;
+  return hsc::launch_fit(a, hsc::as_stream(stream));
+}
+
+extern "C" hsc_status hsc_codec_fit_track(hsc_ctx* ctx, int variants, int k, int n, const float* val_loss,
+                                          int val_stride, const float* Et, const float* Dt, float* best_Et,
+                                          float* best_Dt, float* best_loss, int32_t* wait, int32_t* active,
+                                          int32_t* epochs, int patience, int32_t* n_active_out, void* stream) {
+  hsc::clear_error();
+  HSC_CHECK_CTX(ctx);
+  HSC_REQUIRE(variants >= 0, "negative variant count");
+  HSC_REQUIRE(k >= 1 && n >= 1 && (int64_t)k * n <= (1 << 24), "bad parameter shape k=%d n=%d", k, n);
+  HSC_REQUIRE(val_stride >= 1, "val_stride must be >= 1");
+  HSC_REQUIRE(patience >= 1, "patience must be >= 1");
+  if (variants == 0) return HSC_OK;
+  HSC_REQUIRE(val_loss && Et && Dt && best_Et && best_Dt && best_loss && wait && active, "null pointer");
+  HSC_GUARD(ctx);
+  hsc::TrackArgs a{};
+  a.V = variants;
+  a.GE = k * n;
+  a.GD = n * k;
+  a.val = val_loss;
+  a.val_stride = val_stride;
+  a.Et = Et;
+  a.Dt = Dt;
+  a.best_Et = best_Et;
+  a.best_Dt = best_Dt;
+  a.best_loss = best_loss;
+  a.wait = wait;
+  a.active = active;
+  a.epochs = epochs;
+  a.patience = patience;
+  a.n_active = n_active_out;
+  a.ticket = reinterpret_cast<unsigned int*>(ctx->d_small + HSC_OFF_FITTICKET);
+  hsc::codec_track_kernel<<<(unsigned)variants, hsc::kTrackThreads, 0, hsc::as_stream(stream)>>>(a);
+  return hsc::check_launch("codec_track_kernel");
 }

@@ -21,6 +21,7 @@
 // Offsets inside the fixed scratch block.
 #define HSC_OFF_CHANMAX 0u          // HSC_MAX_K uint32 (fp8 per-channel max)
 #define HSC_OFF_QUEUE 512u          // one uint32 tile counter for dynamically scheduled launches
+#define HSC_OFF_FITTICKET 1024u     // one uint32 arrival ticket of hsc_codec_fit_track
 #define HSC_OFF_REDUCE 4096u        // reduction workspace for hsc_delta_e
 
 namespace hsc {

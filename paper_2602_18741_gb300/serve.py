@@ -22,6 +22,7 @@ host with a fake backend.
 from __future__ import annotations
 
 import collections
+import gc
 import math
 import time
 from dataclasses import dataclass, field
@@ -223,6 +224,17 @@ class GpuBackend:
         self.ref = torch.cuda.Event(enable_timing=True)
         self.t0 = None
 
+    def reserve(self, requests):
+        """Allocate and release one output of every request size on every
+        stream, so that the caching allocator holds the blocks before the
+        first arrival and no request waits on a device allocation."""
+        import torch
+        sizes = sorted({r.width * r.height for r in requests})
+        for s in self.streams:
+            with torch.cuda.stream(s):
+                held = [torch.empty(px, 3, device=self.sc.dev) for px in sizes]
+                del held
+
     def start(self):
         import torch
         torch.cuda.synchronize(self.sc.dev)
@@ -279,15 +291,22 @@ def serve(hsc, ctx, scenes: ResidentScenes, requests, mode="latent", budget_byte
     """Serve `requests` in real time.  Launch-configuration tuning is switched
     off while serving: tuning a new shape class synchronises the stream, which
     would stall the requests behind it (a server tunes ahead of time and
-    loads the result with hsc_tune_load)."""
+    loads the result with hsc_tune_load).  Output blocks are reserved per
+    stream before the first arrival and the garbage collector is paused for
+    the loop."""
     backend = GpuBackend(hsc, ctx, scenes, mode=mode, keep_outputs=keep_outputs)
     sched = Scheduler(backend, budget_bytes, max_inflight=4, max_batch=max_batch)
     was = bool(ctx.autotune) if hasattr(ctx, "autotune") else False
     hsc.hsc_set_autotune(ctx, False)
+    gc_was = gc.isenabled()
+    gc.disable()                   # no collector pause inside the real-time loop
     try:
+        backend.reserve(requests)
         backend.start()
         stats = sched.run(requests)
         hsc.hsc_sync(ctx)
     finally:
+        if gc_was:
+            gc.enable()
         hsc.hsc_set_autotune(ctx, was)
     return stats, backend

@@ -1,0 +1,227 @@
+"""The codec sweep on the GPU (Sec. 3.5) against the oracle: validation
+losses, the early-stopping state, masked steps, a whole small sweep, and the
+selection by the multi-bounce proxy.
+
+Tolerances: loss terms are FP32 sums over up to 256 x n elements (1e-4
+relative, as for the single step); the early-stopping state is compared
+exactly where both sides see the same float32 losses; whole sweeps are
+compared per epoch at 1e-4 relative (parameters whose FP32 and FP64
+gradients differ in sign move by 2 lr either way, which leaves the loss
+unchanged to first order), and stop epochs only where every decision has a
+margin above that tolerance."""
+import math
+
+import numpy as np
+import pytest
+
+import hsc_inputs as hi
+from oracle import cmf, codec
+from oracle import sweep as osw
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import paper_2602_18741_gb300 as hsc
+    ctx = hsc.Context(0)
+    yield hsc, ctx, torch.device("cuda:0")
+    ctx.close()
+
+
+def _t(a, dev, dt=np.float32):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(dev)
+
+
+def test_track_state_matches_the_rule_exactly(env):
+    hsc, ctx, dev = env
+    import torch
+    V, k, n, epochs, patience = 37, 3, 10, 30, 4
+    rng = np.random.default_rng(0)
+    # a falling trend plus noise, rounded to a coarse grid (ties with the best), and NaN
+    vals = np.round((rng.uniform(0.0, 0.25, (epochs, V)) + np.linspace(1.0, 0, epochs)[:, None]) * 16) / 16
+    vals[rng.uniform(size=vals.shape) < 0.05] = np.nan
+    vals = vals.astype(np.float32)
+    snaps = rng.normal(size=(epochs, V, 2 * k * n)).astype(np.float32)
+    best_Et = torch.zeros(V, k, n, device=dev)
+    best_Dt = torch.zeros(V, n, k, device=dev)
+    best = torch.full((V,), math.inf, device=dev)
+    wait = torch.zeros(V, dtype=torch.int32, device=dev)
+    active = torch.ones(V, dtype=torch.int32, device=dev)
+    ep = torch.zeros(V, dtype=torch.int32, device=dev)
+    n_act = torch.empty(1, dtype=torch.int32, device=dev)
+    st = osw.early_stop_init(V)
+    kept = np.zeros((V, 2 * k * n), np.float32)
+    for e in range(epochs):
+        Et = _t(snaps[e, :, :k * n].reshape(V, k, n), dev)
+        Dt = _t(snaps[e, :, k * n:].reshape(V, n, k), dev)
+        tab = _t(np.stack([vals[e]] + [np.zeros(V, np.float32)] * 4, axis=1), dev)   # (V, 5), column 0 used
+        hsc.hsc_codec_fit_track(ctx, tab, Et, Dt, best_Et, best_Dt, best, wait, active, patience, epochs=ep,
+                                n_active_out=n_act)
+        imp = osw.early_stop_update(st, vals[e].astype(np.float64), patience)
+        kept[imp] = snaps[e][imp]
+        hsc.hsc_sync(ctx)
+        assert np.array_equal(best.cpu().numpy(), st.best.astype(np.float32))
+        assert np.array_equal(wait.cpu().numpy(), st.wait)
+        assert np.array_equal(active.cpu().numpy().astype(bool), st.active)
+        assert np.array_equal(ep.cpu().numpy(), st.epochs)
+        assert int(n_act.item()) == int(st.active.sum())
+    got = np.concatenate([best_Et.cpu().numpy().reshape(V, -1), best_Dt.cpu().numpy().reshape(V, -1)], axis=1)
+    improved_once = np.isfinite(st.best)
+    assert np.array_equal(got[improved_once], kept[improved_once])
+    assert not st.active.all() and st.active.any()          # both kinds of variant occurred
+
+
+def _problem(k, grid_spec, V, P, seed, epochs=1, batch=None):
+    ts = hi.training_set(grid_spec, n_smooth=64, n_saw=16, n_bb=16, n_nb=16, pairs=P)
+    sched = hi.sweep_schedule(ts, epochs=epochs, batch=batch or P, val_pairs=min(256, 2 * P), seed=seed)
+    T = cmf.cmf_weights(*grid_spec)
+    rng = np.random.default_rng(seed)
+    E0, D0 = osw.band_init_raw(k, grid_spec[2])
+    Et = np.stack([E0 + rng.normal(0, 0.02, E0.shape) for _ in range(V)]).astype(np.float32)
+    Dt = np.stack([D0 + rng.normal(0, 0.02, D0.shape) for _ in range(V)]).astype(np.float32)
+    W = rng.uniform(0.0, 1.5, (V, 4)).astype(np.float32)
+    W[:, 3] = np.maximum(W[:, 3], 0.1)
+    return ts, sched, T, Et, Dt, W
+
+
+def test_validation_losses_and_softplus_outputs(env):
+    hsc, ctx, dev = env
+    import torch
+    k, g, V, P = 6, hi.GRID_81, 5, 128
+    ts, sched, T, Et, Dt, W = _problem(k, g, V, P, seed=4)
+    R32, L32 = ts.R.astype(np.float32), ts.L.astype(np.float32)
+    val = [_t(sched.val_r, dev, np.int32), _t(sched.val_l, dev, np.int32), _t(sched.val_s, dev)]
+    losses = torch.full((V, 5), -1.0, device=dev)
+    E = torch.empty(V, k, g[2], device=dev)
+    D = torch.empty(V, g[2], k, device=dev)
+    active = _t(np.array([1, 0, 1, 1, 0]), dev, np.int32)
+    hsc.hsc_codec_fit_eval(ctx, _t(R32, dev), _t(L32, dev), *val, _t(T, dev), _t(W, dev), _t(Et, dev), _t(Dt, dev),
+                           active=active, losses_out=losses, E_out=E, D_out=D)
+    hsc.hsc_sync(ctx)
+    Lg, Eg, Dg = losses.cpu().numpy(), E.cpu().numpy(), D.cpu().numpy()
+    vb = osw._pairs(R32.astype(np.float64), L32.astype(np.float64), sched.val_r, sched.val_l, sched.val_s,
+                    np.asarray(T, np.float64))
+    for v in range(V):
+        if v in (1, 4):
+            assert np.all(Lg[v] == -1.0)                     # skipped: untouched
+            continue
+        Ev, Dv = codec.softplus(Et[v].astype(np.float64)), codec.softplus(Dt[v].astype(np.float64))
+        assert np.allclose(Eg[v], Ev, rtol=2e-6, atol=1e-9) and np.allclose(Dg[v], Dv, rtol=2e-6, atol=1e-9)
+        ref = codec.losses(Ev, Dv, vb, {"e2e": W[v, 0], "rec": W[v, 1], "code": W[v, 2], "col": W[v, 3]})
+        for j, key in enumerate(("total", "e2e", "rec", "code", "col")):
+            assert abs(Lg[v, j] - ref[key]) <= 1e-4 * abs(ref[key]) + 1e-12, (v, key)
+
+
+def test_masked_step_skips_exactly(env):
+    hsc, ctx, dev = env
+    import torch
+    k, g, V, P = 6, hi.GRID_31, 6, 64
+    ts, sched, T, Et, Dt, W = _problem(k, g, V, P, seed=8)
+    args = [_t(ts.R, dev), _t(ts.L, dev), _t(sched.train_r[0, 0], dev, np.int32),
+            _t(sched.train_l[0, 0], dev, np.int32), _t(sched.train_s[0, 0], dev), _t(T, dev), _t(W, dev)]
+
+    def run(active):
+        e, d = _t(Et, dev), _t(Dt, dev)
+        mom = [torch.full_like(e, 0.25), torch.full_like(e, 0.5), torch.full_like(d, 0.25), torch.full_like(d, 0.5)]
+        lo = torch.full((V, 5), -1.0, device=dev)
+        for s in (1, 2, 3):
+            hsc.hsc_codec_fit_step(ctx, *args, e, d, *mom, step=s, lr=1e-3, active=active, losses_out=lo)
+        hsc.hsc_sync(ctx)
+        return [x.cpu() for x in [e, d, *mom, lo]]
+
+    mask = np.array([1, 0, 0, 1, 1, 0])
+    full = run(None)
+    part = run(_t(mask, dev, np.int32))
+    init = [torch.from_numpy(Et), torch.from_numpy(Dt)]
+    for v in range(V):
+        for i, (a, b) in enumerate(zip(full, part)):
+            if mask[v]:
+                assert torch.equal(a[v], b[v])
+            elif i < 2:
+                assert torch.equal(b[v], init[i][v])
+            elif i < 6:
+                assert torch.all(b[v] == (0.25 if i % 2 == 0 else 0.5))
+            else:
+                assert torch.all(b[v] == -1.0)
+
+
+def _device_sweep(hsc, ctx, dev, ts, sched, T, Et, Dt, W, epochs, patience, lr):
+    from paper_2602_18741_gb300 import sweep
+    train = tuple(_t(a, dev, dt) for a, dt in ((sched.train_r, np.int32), (sched.train_l, np.int32),
+                                                  (sched.train_s, np.float32)))
+    val = tuple(_t(a, dev, dt) for a, dt in ((sched.val_r, np.int32), (sched.val_l, np.int32),
+                                                (sched.val_s, np.float32)))
+    R, L, Td, Wd = _t(ts.R, dev), _t(ts.L, dev), _t(T, dev), _t(W, dev)
+    res = sweep.fit_variants(hsc, ctx, R, L, Td, Wd, train, val, _t(Et, dev), _t(Dt, dev), epochs=epochs,
+                             patience=patience, lr=lr)
+    return res, (R, L, Td, Wd, val)
+
+
+def test_small_sweep_follows_the_oracle(env):
+    hsc, ctx, dev = env
+    k, g, V, P, epochs, patience, lr = 3, (400.0, 20.0, 16), 4, 96, 8, 2, 0.05
+    ts, sched, T, Et, Dt, W = _problem(k, g, V, P, seed=5, epochs=epochs, batch=32)
+    res, _ = _device_sweep(hsc, ctx, dev, ts, sched, T, Et, Dt, W, epochs, patience, lr)
+    hist = res.history.cpu().numpy()
+    ep = res.epochs.cpu().numpy()
+    R = ts.R.astype(np.float32).astype(np.float64)
+    L = ts.L.astype(np.float32).astype(np.float64)
+    robust = 0
+    for v in range(V):
+        ref = osw.train_variant(R, L, T, W[v].astype(np.float64), sched, Et[v].astype(np.float64),
+                                Dt[v].astype(np.float64), epochs, patience, lr=lr)
+        h = np.asarray(ref.history)
+        m = min(len(h), int(ep[v]))
+        assert np.allclose(hist[:m, v, 0], h[:m], rtol=1e-4, atol=0), (v, hist[:m, v, 0], h[:m])
+        # decisions whose margin is above the tolerance must agree
+        best, margins = np.inf, []
+        for x in h:
+            margins.append(abs(x - best) / abs(x) if np.isfinite(best) else np.inf)
+            best = min(best, x)
+        if min(margins) > 1e-3:
+            robust += 1
+            assert int(ep[v]) == ref.epochs
+            assert abs(float(res.best_loss[v]) - ref.best) <= 1e-4 * ref.best
+    assert robust >= 2
+
+
+def test_sweep_is_deterministic_and_variants_independent(env):
+    hsc, ctx, dev = env
+    import torch
+    k, g, V, P, epochs, patience, lr = 6, hi.GRID_31, 6, 128, 5, 2, 0.02
+    ts, sched, T, Et, Dt, W = _problem(k, g, V, P, seed=6, epochs=epochs, batch=64)
+    a, _ = _device_sweep(hsc, ctx, dev, ts, sched, T, Et, Dt, W, epochs, patience, lr)
+    b, _ = _device_sweep(hsc, ctx, dev, ts, sched, T, Et, Dt, W, epochs, patience, lr)
+    for x, y in ((a.best_Et, b.best_Et), (a.best_Dt, b.best_Dt), (a.best_loss, b.best_loss), (a.epochs, b.epochs)):
+        assert torch.equal(x, y)
+    one, _ = _device_sweep(hsc, ctx, dev, ts, sched, T, Et[3:4], Dt[3:4], W[3:4], epochs, patience, lr)
+    assert torch.equal(one.best_Et[0], a.best_Et[3]) and torch.equal(one.best_Dt[0], a.best_Dt[3])
+    assert int(one.epochs[0]) == int(a.epochs[3])
+
+
+def test_selection_by_the_chain_proxy(env):
+    hsc, ctx, dev = env
+    from paper_2602_18741_gb300 import sweep
+    k, g, V, P, epochs, patience, lr = 6, hi.GRID_31, 5, 128, 3, 3, 0.01
+    ts, sched, T, Et, Dt, W = _problem(k, g, V, P, seed=7, epochs=epochs, batch=64)
+    res, (R, L, Td, Wd, val) = _device_sweep(hsc, ctx, dev, ts, sched, T, Et, Dt, W, epochs, patience, lr)
+    held = hi.training_set(g, seed=hi.MASTER_SEED + 201, n_smooth=64, n_saw=16, n_bb=16, n_nb=16, pairs=8)
+    rng = np.random.default_rng(2)
+    C = 500
+    cl = rng.integers(0, held.L.shape[0], C).astype(np.int32)
+    cr = rng.integers(0, held.R.shape[0], (C, 3)).astype(np.int32)
+    res = sweep.score_variants(hsc, ctx, res, R, L, Td, Wd, val, _t(held.R, dev), _t(held.L, dev),
+                               _t(cl, dev, np.int32), _t(cr, dev, np.int32))
+    # the kept parameters re-evaluate to their recorded validation loss, bit for bit
+    assert np.array_equal(res.kept_loss[:, 0].cpu().numpy(), res.best_loss.cpu().numpy())
+    codecs = [(res.best_Et[v].cpu().numpy().astype(np.float64), res.best_Dt[v].cpu().numpy().astype(np.float64))
+              for v in range(V)]
+    ref = osw.selection_scores(held.R.astype(np.float32), held.L.astype(np.float32), T, codecs, cl, cr)
+    assert np.allclose(res.scores, ref, rtol=1e-4, atol=5e-3), (res.scores, ref)
+    order = np.sort(ref)
+    if order[1] - order[0] > 2e-2:
+        assert res.selected == osw.select(ref)
+    assert 0 <= res.selected < V and res.scores[res.selected] == np.nanmin(res.scores)

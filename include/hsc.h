@@ -148,8 +148,12 @@ HSC_API hsc_status hsc_tune_load(hsc_ctx* ctx, const char* text);
  * -1 = one wave of persistent CTAs on an atomic tile queue; latent kernels),
  * vec = 1 (scalar FP32) or 2 (packed f32x2 pairs: pairs of shading points in
  * the latent kernels, pairs of wavelengths in the spectral kernel), chunk =
- * spectral channels per sweep (0 = default, 16, 28, 32, 44 or 84).  ppt <= 0
- * removes the override.                                                     */
+ * spectral channels per sweep (0 = default, 16, 28, 32, 44 or 84), or 1 for
+ * the lane-group spectral kernel (8 lanes share 8 shading points, each lane
+ * a register tile of 8 points x n/8 wavelengths, one geometry term per point
+ * and light; ppt and vec ignored, waves 0 = one CTA per tile, > 0 =
+ * persistent).
+ * ppt <= 0 removes the override.                                            */
 HSC_API hsc_status hsc_force_launch_config(hsc_ctx* ctx, int ppt, int block, int waves, int vec, int chunk);
 
 /* ----------------------------------------------------- colour projection */

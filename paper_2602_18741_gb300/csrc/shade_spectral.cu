@@ -289,6 +289,289 @@ __global__ void __launch_bounds__(BLOCK) shade_spectral_kernel(const SpecArgs a)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Lane-group form.  Eight consecutive lanes own a group of 8 shading points
+// (4 pixels with their secondary points, or 8 pixels) and hold a register tile
+// of 8 points x TL wavelengths each: lane g accumulates samples g TL .. g TL +
+// TL - 1 of all 8 points, acc[q][i] += G(q, l) V_l[g TL + i].  The last
+// R = n - 8 TL samples (R < 8) each lane takes for its own point only, so no
+// lane does padded work.  Per light each lane computes the geometry term of
+// its own point once (the geometry term is per (point, light), not per
+// sample), and the group reads the 8 terms back from a per-warp exchange row
+// of shared memory, kLB lights at a time.  Lights are staged once per CTA when
+// they fit one stage, so the tile loop has no block barrier.  The XYZ partial
+// sums of the 8 lanes are added by a butterfly whose every lane ends with the
+// same bits.  For every (point, wavelength) the lights are summed in the same
+// order with the same FMAs as in the chunked form, so the spectra are the
+// same bits; only the XYZ sum is grouped differently.
+constexpr int kLB = 4;   // lights per geometry exchange
+constexpr int kLT = 64;  // lights per stage
+
+template <int TL, int R>
+struct LaneShape {
+  static constexpr int VS = (TL + 3) / 4 * 4;               // floats per group row (16-byte aligned)
+  static constexpr bool INPAD = R > 0 && R <= VS - TL;      // remainder in every row's padding
+  static constexpr int RS = INPAD ? 0 : (R + 3) / 4 * 4;    // floats of a separate remainder row
+  static constexpr int VROW = 8 * VS + RS;                  // floats per staged spectrum
+  static constexpr int ROFF = INPAD ? TL : 8 * VS;          // remainder offset (from the group row / row)
+};
+
+// Sample held at offset r of a staged row, or -1 for padding.
+template <int TL, int R>
+__device__ __forceinline__ int lane_row_sample(int r, int n) {
+  using SH = LaneShape<TL, R>;
+  int lam = -1;
+  if (r < 8 * SH::VS) {
+    const int g = r / SH::VS, j = r - g * SH::VS;
+    if (j < TL) lam = g * TL + j;
+    else if (SH::INPAD && j - TL < R) lam = 8 * TL + (j - TL);
+  } else if (r - 8 * SH::VS < R) {
+    lam = 8 * TL + (r - 8 * SH::VS);
+  }
+  return lam < n ? lam : -1;
+}
+
+// Stages lights l0 .. l0+nl-1 (positions and (I/pi)-scaled spectra) and pads
+// the stage to a whole number of kLB lights with far-away dark lights
+// (spectrum 0: every FMA with them adds +0 to a non-negative sum, which
+// leaves it unchanged bit for bit).
+template <int TL, int R, int BLOCK>
+__device__ __forceinline__ void stage_lane_lights(const SpecArgs& a, float* s_V, float4* s_pos, int l0, int nl) {
+  constexpr int VROW = LaneShape<TL, R>::VROW;
+  const int npad = (nl + kLB - 1) / kLB * kLB;
+  for (int i = threadIdx.x; i < npad * VROW; i += BLOCK) {
+    const int l = i / VROW, r = i - l * VROW, lam = lane_row_sample<TL, R>(r, a.n);
+    float v = 0.0f;
+    if (lam >= 0 && l < nl) {
+      const float sc = __fmul_rn(__ldg(a.linten + l0 + l), kInvPi);
+      v = __fmul_rn(__ldg(a.spd + (int64_t)(l0 + l) * a.n + lam), sc);
+    }
+    s_V[i] = v;
+  }
+  for (int l = threadIdx.x; l < npad; l += BLOCK)
+    s_pos[l] = l < nl ? make_float4(__ldg(a.lpos + 3 * (l0 + l)), __ldg(a.lpos + 3 * (l0 + l) + 1),
+                                    __ldg(a.lpos + 3 * (l0 + l) + 2), 0.0f)
+                      : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+}
+
+// EXACT: n = 8 TL + R (no sample index reaches n); WS: spectra are written.
+template <int TL, int R, bool SEC, bool EXACT, bool WS>
+__global__ void __launch_bounds__(128, TL <= 12 ? 4 : 2) shade_spectral_lanes_kernel(const SpecArgs a) {
+  using SH = LaneShape<TL, R>;
+  constexpr int BLOCK = 128;
+  constexpr int VS = SH::VS;
+  constexpr int VROW = SH::VROW;
+  constexpr int RN = R > 0 ? R : 1;
+  constexpr int QP = SEC ? 4 : 8;              // pixels per lane group
+  constexpr int PX = 16 * QP;                  // pixels per CTA tile (16 lane groups)
+  extern __shared__ float4 smem4[];
+  float* s_V = reinterpret_cast<float*>(smem4);                 // kLT x VROW
+  float4* s_pos = reinterpret_cast<float4*>(s_V + kLT * VROW);  // kLT
+  float* s_T = reinterpret_cast<float*>(s_pos + kLT);           // 3 x VROW
+  float* s_gx = s_T + 3 * VROW;                                 // 4 warps x kLB x 32
+  const int tid = threadIdx.x, lane = tid & 31, grp = lane & 7;
+  const int pg = tid >> 3;                     // lane group within the CTA
+  for (int i = tid; i < 3 * VROW; i += BLOCK) {
+    const int c = i / VROW, r = i - c * VROW, lam = lane_row_sample<TL, R>(r, a.n);
+    s_T[i] = lam >= 0 ? __ldg(a.T + c * a.n + lam) : 0.0f;
+  }
+  const bool one_stage = a.L <= kLT;
+  if (one_stage) stage_lane_lights<TL, R, BLOCK>(a, s_V, s_pos, 0, a.L);
+  __syncthreads();
+  float* gx = s_gx + (tid >> 5) * (kLB * 32);
+  const float* vr = s_V + grp * VS;            // this lane's group row of light 0
+  const float* tw = s_T + grp * VS;
+  const float* vrem = SH::INPAD ? vr + SH::ROFF : s_V + SH::ROFF;
+  const float* trem = SH::INPAD ? tw + SH::ROFF : s_T + SH::ROFF;
+  const int64_t tiles = (a.P + PX - 1) / PX;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t pix0 = tile * PX + (int64_t)pg * QP;   // first pixel of this lane group
+    // this lane's shading point; lanes grp < QP also hold pixel grp's record
+    const bool second = SEC && grp >= 4;
+    const int64_t mypix = pix0 + (SEC ? (grp & 3) : grp);
+    const int64_t pc = mypix < a.P ? mypix : a.P - 1;
+    const Pt pt = second ? load_pt(a.x2, a.n2, pc) : load_pt(a.x1, a.n1, pc);
+    int m1 = __ldg(a.m1 + pc), m2 = 0;
+    bool bad = m1 < 0 || m1 >= a.n_mat;
+    if (SEC) {
+      m2 = __ldg(a.m2 + pc);
+      bad = bad || m2 < 0 || m2 >= a.n_mat;
+    }
+    float h = 0.0f;
+    if (SEC) {
+      // the secondary point of pixel grp & 3 lives on lane grp + 4 of the group
+      const float sx = __shfl_down_sync(0xffffffffu, pt.x, 4, 8), sy = __shfl_down_sync(0xffffffffu, pt.y, 4, 8);
+      const float sz = __shfl_down_sync(0xffffffffu, pt.z, 4, 8), snx = __shfl_down_sync(0xffffffffu, pt.nx, 4, 8);
+      const float sny = __shfl_down_sync(0xffffffffu, pt.ny, 4, 8), snz = __shfl_down_sync(0xffffffffu, pt.nz, 4, 8);
+      if (grp < 4) h = bounce_term(pt.x, pt.y, pt.z, pt.nx, pt.ny, pt.nz, sx, sy, sz, snx, sny, snz);
+    }
+    if (bad && grp < QP && mypix < a.P) atomicOr(a.err, HSC_DEVERR_MATERIAL);
+    float acc[8][TL];
+    float accr[RN];                            // this lane's point, the last R samples
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+      for (int i = 0; i < TL; ++i) acc[q][i] = 0.0f;
+#pragma unroll
+    for (int r = 0; r < RN; ++r) accr[r] = 0.0f;
+    for (int l0 = 0; l0 < a.L; l0 += kLT) {
+      const int nl = min(kLT, a.L - l0);
+      if (!one_stage) {
+        __syncthreads();
+        stage_lane_lights<TL, R, BLOCK>(a, s_V, s_pos, l0, nl);
+        __syncthreads();
+      }
+      for (int lb = 0; lb < nl; lb += kLB) {
+        float gown[kLB];
+        __syncwarp();
+#pragma unroll
+        for (int b = 0; b < kLB; ++b) {
+          const float4 pl = s_pos[lb + b];
+          gown[b] = geometry_term(pt.x, pt.y, pt.z, pt.nx, pt.ny, pt.nz, pl.x, pl.y, pl.z);
+          gx[b * 32 + lane] = gown[b];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int b = 0; b < kLB; ++b) {
+          const float4 ga = *reinterpret_cast<const float4*>(gx + b * 32 + (lane & ~7));
+          const float4 gb = *reinterpret_cast<const float4*>(gx + b * 32 + (lane & ~7) + 4);
+          const float gq[8] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
+          const int l = lb + b;
+#pragma unroll
+          for (int f = 0; f < VS / 4; ++f) {
+            const float4 t = *reinterpret_cast<const float4*>(vr + l * VROW + 4 * f);
+            const float v[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int i = 4 * f + e;
+              if (i < TL) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc[q][i] = __fmaf_rn(gq[q], v[e], acc[q][i]);
+              } else if (SH::INPAD && i - TL < R) {
+                accr[i - TL] = __fmaf_rn(gown[b], v[e], accr[i - TL]);
+              }
+            }
+          }
+          if constexpr (R > 0) {
+            if constexpr (!SH::INPAD) {
+#pragma unroll
+              for (int f = 0; f < SH::RS / 4; ++f) {
+                const float4 t = *reinterpret_cast<const float4*>(vrem + l * VROW + 4 * f);
+                const float w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                  if (4 * f + e < R) accr[4 * f + e] = __fmaf_rn(gown[b], w[e], accr[4 * f + e]);
+              }
+            }
+          }
+        }
+      }
+    }
+    // the last R samples of this lane's pixel (lanes grp < QP); added below to
+    // the lane's own partial sums of that pixel
+    float rX = 0.0f, rY = 0.0f, rZ = 0.0f;
+    if constexpr (R > 0) {
+      const float* r1o = a.mats + (int64_t)(bad ? 0 : m1) * a.n;
+      const float* r2o = a.mats + (int64_t)(bad ? 0 : m2) * a.n;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int lam = 8 * TL + r;
+        float A = accr[r];
+        if (SEC) {
+          const float A2 = __shfl_down_sync(0xffffffffu, accr[r], 4, 8);
+          A = __fmaf_rn(h, __fmul_rn(__ldg(r2o + lam), A2), A);
+        }
+        const float S = bad ? 0.0f : __fmul_rn(__ldg(r1o + lam), A);
+        rX = __fmaf_rn(trem[r], S, rX);
+        rY = __fmaf_rn(trem[VROW + r], S, rY);
+        rZ = __fmaf_rn(trem[2 * VROW + r], S, rZ);
+        if (WS && grp < QP && mypix < a.P) a.spectra[mypix * a.n + lam] = S;
+      }
+    }
+    // radiance of the group's pixels over this lane's wavelengths; XYZ by butterfly
+#pragma unroll
+    for (int j = 0; j < QP; ++j) {
+      const int jm1 = __shfl_sync(0xffffffffu, bad ? -1 : m1, j, 8);
+      const int jm2 = __shfl_sync(0xffffffffu, bad ? 0 : m2, j, 8);
+      const float jh = __shfl_sync(0xffffffffu, h, j, 8);
+      const int64_t pix = pix0 + j;
+      const bool jbad = jm1 < 0;
+      const float* r1 = a.mats + (int64_t)(jbad ? 0 : jm1) * a.n + grp * TL;
+      const float* r2 = a.mats + (int64_t)jm2 * a.n + grp * TL;
+      float X = 0.0f, Y = 0.0f, Z = 0.0f;
+#pragma unroll
+      for (int i = 0; i < TL; ++i) {
+        if (EXACT || grp * TL + i < a.n) {
+          float A = acc[j][i];
+          if (SEC) A = __fmaf_rn(jh, __fmul_rn(__ldg(r2 + i), acc[QP + j][i]), A);
+          const float S = jbad ? 0.0f : __fmul_rn(__ldg(r1 + i), A);
+          X = __fmaf_rn(tw[i], S, X);
+          Y = __fmaf_rn(tw[VROW + i], S, Y);
+          Z = __fmaf_rn(tw[2 * VROW + i], S, Z);
+          if (WS && pix < a.P) a.spectra[pix * a.n + grp * TL + i] = S;
+        }
+      }
+      if (R > 0 && grp == j) {
+        X = __fadd_rn(X, rX);
+        Y = __fadd_rn(Y, rY);
+        Z = __fadd_rn(Z, rZ);
+      }
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) {
+        X = __fadd_rn(X, __shfl_xor_sync(0xffffffffu, X, o, 8));
+        Y = __fadd_rn(Y, __shfl_xor_sync(0xffffffffu, Y, o, 8));
+        Z = __fadd_rn(Z, __shfl_xor_sync(0xffffffffu, Z, o, 8));
+      }
+      if (grp == j && pix < a.P) {
+        a.xyz[3 * pix] = X;
+        a.xyz[3 * pix + 1] = Y;
+        a.xyz[3 * pix + 2] = Z;
+      }
+    }
+  }
+}
+
+template <int TL, int R, bool SEC, bool EXACT, bool WS>
+hsc_status launch_lanes_t(const SpecArgs& a, const LaunchCfg& cfg, cudaStream_t s) {
+  auto kern = shade_spectral_lanes_kernel<TL, R, SEC, EXACT, WS>;
+  constexpr int VROW = LaneShape<TL, R>::VROW;
+  static_assert(kLT % kLB == 0, "light stages hold whole exchange batches");
+  const size_t smem = sizeof(float) * ((size_t)kLT * VROW + 4 * kLT + 3 * VROW + 4 * kLB * 32);
+  static int occ = -1;
+  if (occ < 0) {
+    if (smem > 48 * 1024 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return set_error(HSC_ERR_CUDA, "shared memory attribute of the lane-group spectral kernel");
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, 128, smem) != cudaSuccess) o = 1;
+    occ = o > 0 ? o : 1;
+  }
+  constexpr int PX = 16 * (SEC ? 4 : 8);
+  const int64_t tiles = (a.P + PX - 1) / PX;
+  int64_t grid = cfg.waves > 0 ? (int64_t)cfg.sm_count * occ * cfg.waves : tiles;
+  if (grid > tiles) grid = tiles;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, 128, smem, s>>>(a);
+  return check_launch("shade_spectral_lanes_kernel");
+}
+
+template <int TL, int R, bool EXACT>
+hsc_status launch_lanes_n(const SpecArgs& a, bool sec, const LaunchCfg& cfg, cudaStream_t s) {
+  const bool ws = a.spectra != nullptr;
+  if (sec)
+    return ws ? launch_lanes_t<TL, R, true, EXACT, true>(a, cfg, s) : launch_lanes_t<TL, R, true, EXACT, false>(a, cfg, s);
+  return ws ? launch_lanes_t<TL, R, false, EXACT, true>(a, cfg, s) : launch_lanes_t<TL, R, false, EXACT, false>(a, cfg, s);
+}
+
+// n = 81 and n = 31 split exactly (8 x 10 + 1, 8 x 3 + 7); other n round up
+// to 8 groups of TL samples.
+hsc_status launch_lanes(const SpecArgs& a, bool sec, const LaunchCfg& cfg, cudaStream_t s) {
+  if (a.n == 81) return launch_lanes_n<10, 1, true>(a, sec, cfg, s);
+  if (a.n == 31) return launch_lanes_n<3, 7, true>(a, sec, cfg, s);
+  if (a.n <= 32) return launch_lanes_n<4, 0, false>(a, sec, cfg, s);
+  if (a.n <= 88) return launch_lanes_n<11, 0, false>(a, sec, cfg, s);
+  return launch_lanes_n<16, 0, false>(a, sec, cfg, s);
+}
+
 template <int CW, bool SEC, int PTS, int BLOCK, int VEC>
 hsc_status launch_spec(const SpecArgs& a0, const LaunchCfg& cfg, cudaStream_t s) {
   SpecArgs a = a0;
@@ -333,6 +616,7 @@ int spectral_chunk(const LaunchCfg& cfg, int n) {
 }
 
 hsc_status launch_spectral(const SpecArgs& a, bool sec, const LaunchCfg& cfg, cudaStream_t s) {
+  if (cfg.chunk == 1) return launch_lanes(a, sec, cfg, s);
   switch (spectral_chunk(cfg, a.n)) {
     case 16: return launch_spec_cw<16>(a, sec, cfg, s);
     case 28: return launch_spec_cw<28>(a, sec, cfg, s);

@@ -45,14 +45,20 @@ std::vector<LaunchCfg> latent_candidates(const hsc_ctx* ctx) {
 
 std::vector<LaunchCfg> spectral_candidates(const hsc_ctx* ctx) {
   std::vector<LaunchCfg> v;
+  // default: the persistent lane-group kernel (one geometry term per point and
+  // light, register tiles of 8 points)
   LaunchCfg d;
   d.sm_count = ctx->sm_count;
   d.block = 128;
-  d.ppt = 2;
+  d.ppt = 1;
   d.waves = 1;
-  d.vec = 2;
-  d.chunk = 0;
+  d.vec = 1;
+  d.chunk = 1;
   v.push_back(d);
+  LaunchCfg one_cta_per_tile = d;
+  one_cta_per_tile.waves = 0;
+  v.push_back(one_cta_per_tile);
+  // the chunked kernel (geometry term recomputed per chunk of the spectrum)
   for (int chunk : {0, 16, 28, 44})
     for (int vec : {1, 2})
       for (int ppt : {1, 2}) {
@@ -60,7 +66,6 @@ std::vector<LaunchCfg> spectral_candidates(const hsc_ctx* ctx) {
         c.ppt = ppt;
         c.vec = vec;
         c.chunk = chunk;
-        if (c.ppt == d.ppt && c.vec == d.vec && c.chunk == d.chunk) continue;
         v.push_back(c);
       }
   return v;
@@ -195,8 +200,8 @@ hsc_status hsc_force_launch_config(hsc_ctx* ctx, int ppt, int block, int waves, 
   HSC_REQUIRE(block == 128 || block == 256, "block must be 128 or 256");
   HSC_REQUIRE(waves >= -1 && waves <= 64, "waves out of range");
   HSC_REQUIRE(vec == 1 || vec == 2, "vec must be 1 or 2");
-  HSC_REQUIRE(chunk == 0 || chunk == 16 || chunk == 28 || chunk == 32 || chunk == 44 || chunk == 84,
-              "chunk must be 0, 16, 28, 32, 44 or 84");
+  HSC_REQUIRE(chunk == 0 || chunk == 1 || chunk == 16 || chunk == 28 || chunk == 32 || chunk == 44 || chunk == 84,
+              "chunk must be 0, 1, 16, 28, 32, 44 or 84");
   ctx->forced.vec = vec;
   ctx->forced.chunk = chunk;
   ctx->forced.ppt = ppt;

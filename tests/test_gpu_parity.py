@@ -174,8 +174,10 @@ def test_passes_bit_identical_to_fused(env, w, h, grid_spec, L, sec, k):
 @pytest.mark.parametrize("grid_spec,k,sec", [(hi.GRID_81, 81, False), (hi.GRID_81, 81, True), (hi.GRID_31, 33, False)])
 def test_identity_codec_latent_equals_spectral(env, grid_spec, k, sec):
     # k = n with E = D = I (n = 31 padded to k = 33) is an exact codec; with
-    # direct light only the two kernels then run the same FP32 operations per
-    # channel, so their outputs agree bit for bit.
+    # direct light only the latent kernel and the chunked spectral kernel then
+    # run the same FP32 operations per channel, so their outputs agree bit for
+    # bit.  The lane-group spectral kernel gives the same spectra and adds the
+    # XYZ terms in another order.
     hsc, ctx, dev = env
     import torch
     f = hi.make_frame(91, 23, 19, grid_spec, n_smooth=9, n_saw=3, lights=13, secondary=sec)
@@ -192,8 +194,15 @@ def test_identity_codec_latent_equals_spectral(env, grid_spec, k, sec):
     hsc.hsc_shade_latent(ctx, df.g1, df.g2, zm, df.lights, zl, hsc.HSC_FUSED, lat, xyz_out=xl, M_xyz=M)
     xs = torch.empty(f.pixels, 3, device=dev)
     S = torch.empty(f.pixels, n, device=dev)
+    xg = torch.empty(f.pixels, 3, device=dev)
+    Sg = torch.empty(f.pixels, n, device=dev)
+    hsc.hsc_shade_spectral(ctx, df.g1, df.g2, df.mats, df.lights, df.spd, df.T, xg, Sg)   # default: lane groups
+    hsc.hsc_force_launch_config(ctx, 2, 128, 1, 1, 0)                                        # chunked
     hsc.hsc_shade_spectral(ctx, df.g1, df.g2, df.mats, df.lights, df.spd, df.T, xs, S)
+    hsc.hsc_force_launch_config(ctx, 0)
     hsc.hsc_sync(ctx)
+    assert torch.equal(Sg, S)
+    assert metrics.rel_xyz_error(xg.cpu().numpy(), xs.cpu().numpy().astype(np.float64)) <= 1e-6
     if sec:
         assert rel_err_rows(lat[:, :n].cpu().numpy(), S.cpu().numpy()) <= 1e-6
         assert metrics.rel_xyz_error(xl.cpu().numpy(), xs.cpu().numpy().astype(np.float64)) <= 1e-6
@@ -552,6 +561,67 @@ def test_spectral_launch_configs_match_oracle(env, sec):
         assert rel_err_rows(S.cpu().numpy(), S_ref) <= TOL, (ppt, waves, vec, chunk)
         assert metrics.rel_xyz_error(xyz.cpu().numpy(), xyz_ref) <= TOL, (ppt, waves, vec, chunk)
     hsc.hsc_force_launch_config(ctx, 0)
+
+
+@pytest.mark.parametrize("grid_spec,sec,lights,w,h", [
+    (hi.GRID_81, True, 64, 41, 13),            # the bench's shape class (8 x 10 + 1), ragged tail
+    (hi.GRID_81, False, 70, 33, 17),           # two light stages, no secondary point
+    (hi.GRID_31, True, 7, 128, 3),             # 8 x 3 + 7, a padded light batch
+    ((400.0, 10.0, 30), False, 5, 13, 7),      # 8 groups of 4, two padded samples
+    ((400.0, 4.0, 90), True, 65, 9, 29),       # 8 groups of 16, 65 lights
+    ((380.0, 5.0, 60), True, 130, 6, 6),       # 8 groups of 11, three light stages
+    ((380.0, 3.2, 128), False, 3, 300, 1),     # 8 groups of 16
+    (hi.GRID_81, True, 1, 1, 1),               # one pixel, one light
+])
+def test_lane_group_spectral_kernel(env, grid_spec, sec, lights, w, h):
+    """The lane-group spectral kernel against the oracle, with and without
+    the spectra written; its spectra equal the chunked kernel's (two points
+    per thread) bit for bit: every (point, wavelength) sums the lights in the
+    same order with the same FMAs."""
+    hsc, ctx, dev = env
+    import torch
+    f = hi.make_frame(40 + lights, w, h, grid_spec, n_smooth=20, n_saw=5, lights=lights, secondary=sec)
+    df = upload(hsc, ctx, f, dev)
+    S_ref, xyz_ref = shade.shade_spectral(f)
+    outs = {}
+    for waves, chunk, ppt in ((0, 1, 1), (1, 1, 1), (1, 0, 2)):
+        hsc.hsc_force_launch_config(ctx, ppt, 128, waves, 1, chunk)
+        xyz = torch.empty(f.pixels, 3, device=dev)
+        S = torch.empty(f.pixels, f.n, device=dev)
+        hsc.hsc_shade_spectral(ctx, df.g1, df.g2, df.mats, df.lights, df.spd, df.T, xyz, S)
+        hsc.hsc_sync(ctx)
+        outs[(waves, chunk)] = (xyz.cpu(), S.cpu())
+        assert rel_err_rows(S.cpu().numpy(), S_ref) <= TOL, (waves, chunk)
+        assert metrics.rel_xyz_error(xyz.cpu().numpy(), xyz_ref) <= TOL, (waves, chunk)
+    hsc.hsc_force_launch_config(ctx, 1, 128, 1, 1, 1)
+    xyz_only = torch.empty(f.pixels, 3, device=dev)
+    hsc.hsc_shade_spectral(ctx, df.g1, df.g2, df.mats, df.lights, df.spd, df.T, xyz_only)
+    hsc.hsc_sync(ctx)
+    hsc.hsc_force_launch_config(ctx, 0)
+    assert torch.equal(outs[(0, 1)][0], outs[(1, 1)][0]) and torch.equal(outs[(0, 1)][1], outs[(1, 1)][1])
+    assert torch.equal(outs[(0, 1)][1], outs[(1, 0)][1])
+    assert torch.equal(xyz_only.cpu(), outs[(1, 1)][0])
+
+
+def test_lane_group_spectral_kernel_bad_material(env):
+    hsc, ctx, dev = env
+    import torch
+    f = hi.make_frame(3, 20, 20, hi.GRID_81, n_smooth=6, n_saw=0, lights=5, secondary=True)
+    f.g2.mat[7] = 1000
+    f.g1.mat[300] = -2
+    df = upload(hsc, ctx, f, dev)
+    for waves in (0, 1):
+        hsc.hsc_force_launch_config(ctx, 1, 128, waves, 1, 1)
+        xyz = torch.empty(f.pixels, 3, device=dev)
+        S = torch.empty(f.pixels, f.n, device=dev)
+        hsc.hsc_shade_spectral(ctx, df.g1, df.g2, df.mats, df.lights, df.spd, df.T, xyz, S)
+        hsc.hsc_force_launch_config(ctx, 0)
+        with pytest.raises(hsc.HscError) as ei:
+            hsc.hsc_sync(ctx)
+        assert ei.value.status == hsc.HSC_ERR_DEVICE_CHECK
+        for p in (7, 300):
+            assert float(xyz[p].abs().max()) == 0.0 and float(S[p].abs().max()) == 0.0
+        assert float(xyz[8].abs().max()) > 0.0
 
 
 def test_autotune_picks_a_config_without_changing_results(env):

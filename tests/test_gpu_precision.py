@@ -72,7 +72,7 @@ def test_precision_variants_against_oracle(k):
         report[name] = {"rel_xyz": metrics.rel_xyz_error(xs, x_ref),
                         "rel_spectra": float(np.max(np.abs(sp - S_ref)) / np.abs(S_ref).max()),
                         "de2000_mean": m, "de2000_p95": p95,
-                        "spectral_decode": "f32 cuda cores" if name == "f32" else "bf16 tensor cores"}
+                        "spectral_decode": "f32 tensor cores (bf16 three-part split)" if name == "f32" else "bf16 tensor cores"}
     ctx.close()
     path = os.environ.get("HSC_PRECISION_REPORT")
     if path:

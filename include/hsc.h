@@ -211,14 +211,17 @@ HSC_API hsc_status hsc_reassemble(hsc_ctx* ctx, const float* const* passes, int 
  *         (then latent_scales, device k float32, receives the per-channel
  *         scales max_p z_c / 448 and the codes are RNE(z / scale), saturating).
  *   xyz_out: NULL, or device P x 3 float32 receiving XYZ = M_xyz z computed
- *         from the FP32 latent (fused for FUSED and k <= 15);  M_xyz: device
- *         3 x k from hsc_fold_xyz (required when xyz_out is set).
+ *         from the FP32 latent (fused for FUSED and k <= 15);
+ *   srgb8_out: NULL, or device P x 3 bytes receiving the 8-bit sRGB of that
+ *         XYZ, the same bytes hsc_decode_xyz gives for the FP32 latent (fused
+ *         into the shading epilogue for FUSED and k <= 15);
+ *   M_xyz: device 3 x k from hsc_fold_xyz (required when either is set).
  * Uses context scratch for PASSES images and for the fp8 path.               */
 HSC_API hsc_status hsc_shade_latent(hsc_ctx* ctx, const hsc_gbuffer* g1, const hsc_gbuffer* g2, int64_t pixels,
                             const void* mat_codes, int n_mat, const hsc_lights* lights,
                             const void* light_codes, int k, hsc_dtype code_dt, hsc_mode mode,
                             void* latent_out, hsc_dtype latent_dt, float* latent_scales,
-                            float* xyz_out, const float* M_xyz, void* stream);
+                            float* xyz_out, uint8_t* srgb8_out, const float* M_xyz, void* stream);
 
 /* Per-channel fp8 quantisation of an FP32 latent image: scale_c = max_p z_c / 448
  * (1 for an all-zero channel), code = RNE_e4m3(z * (1/scale_c)) saturating.

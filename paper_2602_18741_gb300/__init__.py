@@ -86,7 +86,7 @@ _SIGS = {
     "hsc_shade_pass": ([_vp, _GB, _GB, _i64, _vp, _i32, _LI, _vp, _i32, _i32, _i32, _vp, _vp], _i32),
     "hsc_reassemble": ([_vp, ctypes.POINTER(_vp), _i32, _i64, _vp, _vp], _i32),
     "hsc_shade_latent": ([_vp, _GB, _GB, _i64, _vp, _i32, _LI, _vp, _i32, _i32, _i32, _vp, _i32, _vp, _vp, _vp,
-                          _vp], _i32),
+                          _vp, _vp], _i32),
     "hsc_quantize_fp8": ([_vp, _vp, _i64, _i32, _vp, _vp, _vp], _i32),
     "hsc_quantize_fp8_noalloc": ([_vp, _i64, _i32, _vp, _vp, _vp], _i32),
     "hsc_decode_xyz": ([_vp, _vp, _i32, _vp, _i64, _i32, _vp, _vp, _vp, _vp], _i32),
@@ -296,16 +296,18 @@ def hsc_reassemble(ctx: Context, passes: Sequence[torch.Tensor], latent_out: tor
 def hsc_shade_latent(ctx: Context, g1: GBuffer, g2: Optional[GBuffer], mat_codes: torch.Tensor, lights: Lights,
                      light_codes: torch.Tensor, mode: int, latent_out: torch.Tensor,
                      latent_scales: Optional[torch.Tensor] = None, xyz_out: Optional[torch.Tensor] = None,
-                     M_xyz: Optional[torch.Tensor] = None, stream=None):
+                     M_xyz: Optional[torch.Tensor] = None, stream=None, srgb8_out: Optional[torch.Tensor] = None):
     k = mat_codes.shape[1]
     if light_codes.shape != (lights.count, k) or light_codes.dtype != mat_codes.dtype:
         raise ValueError("light_codes must be (L,k) with the material codes' dtype")
     if latent_out.shape != (g1.pixels, k):
         raise ValueError("latent_out must be (P,k)")
+    if srgb8_out is not None and (srgb8_out.shape != (g1.pixels, 3) or srgb8_out.dtype != torch.uint8):
+        raise ValueError("srgb8_out must be (P,3) uint8")
     _check(_lib.hsc_shade_latent(ctx.handle, _gb(g1), _gb(g2), g1.pixels, _ptr(mat_codes), int(mat_codes.shape[0]),
                                  ctypes.byref(lights._s), _ptr(light_codes), int(k), _dt(mat_codes), int(mode),
-                                 _ptr(latent_out), _dt(latent_out), _ptr(latent_scales), _ptr(xyz_out), _ptr(M_xyz),
-                                 _stream(stream)))
+                                 _ptr(latent_out), _dt(latent_out), _ptr(latent_scales), _ptr(xyz_out),
+                                 _ptr(srgb8_out), _ptr(M_xyz), _stream(stream)))
 
 
 def hsc_quantize_fp8(ctx: Context, latent: torch.Tensor, codes_out: torch.Tensor, scales_out: torch.Tensor,

@@ -66,7 +66,7 @@ static ShadeArgs base_args(hsc_ctx* ctx, const hsc_gbuffer* g1, const hsc_gbuffe
 
 // One shading launch of `kc` channels in the tuned (or default) configuration.
 static hsc_status shade_launch(hsc_ctx* ctx, const ShadeArgs& a, int kc, bool sec, cudaStream_t s) {
-  const TuneKey key = make_tune_key(kTuneLatent, kc, sec, a.L, a.P, a.code_dt);
+  const TuneKey key = make_tune_key(a.srgb8 ? kTuneLatentSrgb : kTuneLatent, kc, sec, a.L, a.P, a.code_dt);
   auto launch = [&](const LaunchCfg& c) { return launch_shade_codes(a, kc, sec, c, s); };
   LaunchCfg cfg;
   HSC_TRY(tuned_cfg(ctx, key, latent_candidates(ctx), launch, s, &cfg));
@@ -122,7 +122,8 @@ hsc_status hsc_reassemble(hsc_ctx* ctx, const float* const* passes, int B, int64
 hsc_status hsc_shade_latent(hsc_ctx* ctx, const hsc_gbuffer* g1, const hsc_gbuffer* g2, int64_t pixels,
                             const void* mat_codes, int n_mat, const hsc_lights* lights, const void* light_codes,
                             int k, hsc_dtype code_dt, hsc_mode mode, void* latent_out, hsc_dtype latent_dt,
-                            float* latent_scales, float* xyz_out, const float* M_xyz, void* stream) {
+                            float* latent_scales, float* xyz_out, uint8_t* srgb8_out, const float* M_xyz,
+                            void* stream) {
   hsc::clear_error();
   HSC_CHECK_CTX(ctx);
   HSC_TRY(hsc::validate_common(g1, g2, pixels, mat_codes, n_mat, lights, light_codes, k, code_dt));
@@ -135,6 +136,7 @@ hsc_status hsc_shade_latent(hsc_ctx* ctx, const hsc_gbuffer* g1, const hsc_gbuff
               "fp8 latent needs a latent_scales array");
   HSC_REQUIRE(!xyz_out || (M_xyz && hsc::aligned(xyz_out, 4) && hsc::aligned(M_xyz, 4)),
               "xyz_out needs M_xyz (both 4-byte aligned)");
+  HSC_REQUIRE(!srgb8_out || (M_xyz && hsc::aligned(M_xyz, 4)), "srgb8_out needs M_xyz (4-byte aligned)");
   if (pixels == 0) return HSC_OK;
   HSC_GUARD(ctx);
   cudaStream_t s = hsc::as_stream(stream);
@@ -175,6 +177,7 @@ hsc_status hsc_shade_latent(hsc_ctx* ctx, const hsc_gbuffer* g1, const hsc_gbuff
       fa.out_stride = k;
       fa.out_c0 = c0;
       fa.xyz = (k <= 15) ? xyz_out : nullptr;
+      fa.srgb8 = (k <= 15) ? srgb8_out : nullptr;
       fa.M = M_xyz;
       fa.chan_max = (latent_dt == HSC_FP8_E4M3) ? chan_max : nullptr;
       HSC_TRY(hsc::shade_launch(ctx, fa, kc, sec, s));
@@ -183,8 +186,8 @@ hsc_status hsc_shade_latent(hsc_ctx* ctx, const hsc_gbuffer* g1, const hsc_gbuff
   if (latent_dt == HSC_FP8_E4M3)
     HSC_TRY(hsc::launch_quantize(lat32, pixels, k, chan_max, reinterpret_cast<uint8_t*>(latent_out), latent_scales,
                                  ctx->sm_count, s));
-  if (xyz_out && (mode == HSC_PASSES || k > 15))
-    HSC_TRY(hsc::launch_decode_xyz(lat32, HSC_F32, nullptr, pixels, k, M_xyz, xyz_out, nullptr, ctx->sm_count, s));
+  if ((xyz_out || srgb8_out) && (mode == HSC_PASSES || k > 15))
+    HSC_TRY(hsc::launch_decode_xyz(lat32, HSC_F32, nullptr, pixels, k, M_xyz, xyz_out, srgb8_out, ctx->sm_count, s));
   return HSC_OK;
 }
 

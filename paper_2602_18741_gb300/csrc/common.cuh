@@ -229,6 +229,30 @@ __device__ __forceinline__ float bounce_term(float x1, float y1, float z1, float
   return (den > 0.0f) ? __fmul_rn(h, kInvPi) : 0.0f;
 }
 
+// XYZ to 8-bit sRGB (IEC 61966-2-1): linear sRGB by the standard matrix with
+// each sum in a fixed order, clamped to [0, 1], the transfer function (its
+// power through the fast exp2/log2 intrinsics: the 8-bit output quantises
+// it), u8 = floor(255 v + 0.5).  Shared by the decode kernels and the fused
+// shading epilogue, so both give the same bytes for the same XYZ.
+__device__ __forceinline__ float srgb_oetf(float v) {
+  v = __saturatef(v);
+  return (v <= 0.0031308f) ? __fmul_rn(12.92f, v) : __fmaf_rn(1.055f, __powf(v, 1.0f / 2.4f), -0.055f);
+}
+
+// u8 = floor(255 v + 0.5): one conversion rounding toward minus infinity.
+__device__ __forceinline__ uint8_t srgb_u8(float v) {
+  return (uint8_t)__float2uint_rd(__fmaf_rn(v, 255.0f, 0.5f));
+}
+
+__device__ __forceinline__ void xyz_to_srgb8(float X, float Y, float Z, uint8_t* out) {
+  const float r = __fmaf_rn(-0.4986f, Z, __fmaf_rn(-1.5372f, Y, __fmul_rn(3.2406f, X)));
+  const float g = __fmaf_rn(0.0415f, Z, __fmaf_rn(1.8758f, Y, __fmul_rn(-0.9689f, X)));
+  const float b = __fmaf_rn(1.0570f, Z, __fmaf_rn(-0.2040f, Y, __fmul_rn(0.0557f, X)));
+  out[0] = srgb_u8(srgb_oetf(r));
+  out[1] = srgb_u8(srgb_oetf(g));
+  out[2] = srgb_u8(srgb_oetf(b));
+}
+
 // Load element i of a code array stored as F32 / BF16 / F16 as float.
 __device__ __forceinline__ float load_code(const void* base, int dt, int64_t i) {
   if (dt == HSC_F32) return __ldg(reinterpret_cast<const float*>(base) + i);

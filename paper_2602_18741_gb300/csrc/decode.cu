@@ -11,16 +11,6 @@ namespace {
 
 constexpr int kDBlock = 256;
 
-// IEC 61966-2-1 XYZ -> linear sRGB.
-__constant__ float c_srgb[9] = {3.2406f, -1.5372f, -0.4986f, -0.9689f, 1.8758f, 0.0415f, 0.0557f, -0.2040f, 1.0570f};
-
-// sRGB transfer function.  The 8-bit output quantises it, so the power uses
-// the fast exp2/log2 hardware intrinsics.
-__device__ __forceinline__ float srgb_encode(float v) {
-  v = fminf(fmaxf(v, 0.0f), 1.0f);
-  return (v <= 0.0031308f) ? 12.92f * v : 1.055f * __powf(v, 1.0f / 2.4f) - 0.055f;
-}
-
 template <int DT>
 __device__ __forceinline__ float load_lat(const void* base, int64_t i, const float* s_scale, int c) {
   if (DT == HSC_F32) return __ldg(reinterpret_cast<const float*>(base) + i);
@@ -55,13 +45,7 @@ __global__ void __launch_bounds__(kDBlock) decode_xyz_kernel(const void* __restr
       xyz[3 * p + 1] = Y;
       xyz[3 * p + 2] = Z;
     }
-    if (srgb8) {
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        const float lin = __fmaf_rn(c_srgb[3 * r + 2], Z, __fmaf_rn(c_srgb[3 * r + 1], Y, __fmul_rn(c_srgb[3 * r], X)));
-        srgb8[3 * p + r] = (uint8_t)floorf(srgb_encode(lin) * 255.0f + 0.5f);
-      }
-    }
+    if (srgb8) xyz_to_srgb8(X, Y, Z, srgb8 + 3 * p);
   }
 }
 

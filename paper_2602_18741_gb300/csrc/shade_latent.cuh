@@ -28,6 +28,7 @@ struct ShadeArgs {
   int out_stride;
   int out_c0;      // channel offset of c0 inside an output row
   float* xyz;      // fused XYZ (only when this launch covers all k channels)
+  uint8_t* srgb8;  // fused 8-bit sRGB of the same XYZ (same condition)
   const float* M;  // 3 x k
   unsigned int* chan_max;  // per-channel max bits for the fp8 scale (nullable)
   unsigned int* err;

@@ -92,7 +92,7 @@ __device__ __forceinline__ void load_code_row(const ShadeArgs& a, int row, float
 // decode matrix staged at s_M, and the fp8 channel maxima when asked).  When the lights fit one shared-memory
 // tile the caller has staged them already (`staged`); otherwise the light
 // tiles are staged here.  Must be called by every thread of the CTA.
-template <int KC, int PPT, bool SEC, int BLOCK, int VEC>
+template <int KC, int PPT, bool SEC, int BLOCK, int VEC, bool RGB = false>
 __device__ __forceinline__ void shade_tile(const ShadeArgs& a, int64_t tile, float4* s_light, bool staged,
                                            const float* s_M) {
   constexpr int F4 = LightStage<KC, VEC>::F4;
@@ -246,7 +246,21 @@ __device__ __forceinline__ void shade_tile(const ShadeArgs& a, int64_t tile, flo
 #pragma unroll
           for (int c = 0; c < KC; ++c) o[c] = out[c];
         }
-        if (a.xyz) {
+        if constexpr (RGB) {
+          float t[3];
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            float s = 0.0f;
+#pragma unroll
+            for (int c = 0; c < KC; ++c) s = __fmaf_rn(s_M[r * KC + c], out[c], s);
+            t[r] = s;
+          }
+          if (a.xyz) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) a.xyz[3 * p + r] = t[r];
+          }
+          xyz_to_srgb8(t[0], t[1], t[2], a.srgb8 + 3 * p);
+        } else if (a.xyz) {
 #pragma unroll
           for (int r = 0; r < 3; ++r) {
             float s = 0.0f;
@@ -273,7 +287,7 @@ __device__ __forceinline__ void shade_tile(const ShadeArgs& a, int64_t tile, flo
 // fused XYZ epilogue.
 template <int KC, int BLOCK>
 __device__ __forceinline__ void stage_decode_matrix(const ShadeArgs& a, float* s_M) {
-  if (a.xyz)
+  if (a.xyz || a.srgb8)
     for (int i = threadIdx.x; i < 3 * KC; i += BLOCK) s_M[i] = __ldg(a.M + (i / KC) * a.k + a.c0 + (i % KC));
 }
 
@@ -291,7 +305,9 @@ __device__ __forceinline__ void release_queue(unsigned int* queue) {
   }
 }
 
-template <int KC, int PPT, bool SEC, int BLOCK, int VEC>
+// RGB: the epilogue also writes 8-bit sRGB (a separate instantiation, so the
+// kernels without it keep their code).
+template <int KC, int PPT, bool SEC, int BLOCK, int VEC, bool RGB>
 __global__ void __launch_bounds__(BLOCK) shade_codes_kernel(const ShadeArgs a) {
   extern __shared__ float4 s_light[];
   __shared__ float s_M[3 * KC];
@@ -308,22 +324,22 @@ __global__ void __launch_bounds__(BLOCK) shade_codes_kernel(const ShadeArgs a) {
       const int64_t tile = s_next;
       __syncthreads();
       if (tile >= a.tiles) break;
-      shade_tile<KC, PPT, SEC, BLOCK, VEC>(a, tile, s_light, staged, s_M);
+      shade_tile<KC, PPT, SEC, BLOCK, VEC, RGB>(a, tile, s_light, staged, s_M);
     }
     release_queue(a.queue);
   } else {
     for (int64_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x)
-      shade_tile<KC, PPT, SEC, BLOCK, VEC>(a, tile, s_light, staged, s_M);
+      shade_tile<KC, PPT, SEC, BLOCK, VEC, RGB>(a, tile, s_light, staged, s_M);
   }
 }
 
-template <int KC, int PPT, bool SEC, int BLOCK, int VEC>
-hsc_status launch_one(const ShadeArgs& a0, const LaunchCfg& cfg, cudaStream_t stream) {
+template <int KC, int PPT, bool SEC, int BLOCK, int VEC, bool RGB>
+hsc_status launch_one_rgb(const ShadeArgs& a0, const LaunchCfg& cfg, cudaStream_t stream) {
   constexpr int F4 = LightStage<KC, VEC>::F4;
   ShadeArgs a = a0;
   a.tiles = (a.P + (int64_t)BLOCK * PPT - 1) / ((int64_t)BLOCK * PPT);
   const size_t smem = (size_t)min(a.L, kLightTile) * F4 * sizeof(float4);
-  auto kern = shade_codes_kernel<KC, PPT, SEC, BLOCK, VEC>;
+  auto kern = shade_codes_kernel<KC, PPT, SEC, BLOCK, VEC, RGB>;
   static int occ = -1;
   if (occ < 0) {
     int o = 0;
@@ -346,6 +362,12 @@ hsc_status launch_one(const ShadeArgs& a0, const LaunchCfg& cfg, cudaStream_t st
   if (grid < 1) grid = 1;
   kern<<<(unsigned)grid, BLOCK, smem, stream>>>(a);
   return check_launch("shade_codes_kernel");
+}
+
+template <int KC, int PPT, bool SEC, int BLOCK, int VEC>
+hsc_status launch_one(const ShadeArgs& a, const LaunchCfg& cfg, cudaStream_t stream) {
+  return a.srgb8 ? launch_one_rgb<KC, PPT, SEC, BLOCK, VEC, true>(a, cfg, stream)
+                 : launch_one_rgb<KC, PPT, SEC, BLOCK, VEC, false>(a, cfg, stream);
 }
 
 template <int KC, int BLOCK>

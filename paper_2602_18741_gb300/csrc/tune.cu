@@ -96,8 +96,9 @@ hsc_status tuned_cfg(hsc_ctx* ctx, const TuneKey& key, const std::vector<LaunchC
   float best = 1e30f;
   LaunchCfg best_cfg = cands[0];
   char line[256];
-  snprintf(line, sizeof(line), "%s ch=%d sec=%d L<=2^%d P<=2^%d dt=%d:", key.kind == kTuneLatent ? "latent" : "spectral",
-           key.channels, key.sec, key.lbucket, key.pbucket, key.dtype);
+  const char* kind = key.kind == kTuneLatent ? "latent" : (key.kind == kTuneLatentSrgb ? "latent+srgb8" : "spectral");
+  snprintf(line, sizeof(line), "%s ch=%d sec=%d L<=2^%d P<=2^%d dt=%d:", kind, key.channels, key.sec, key.lbucket,
+           key.pbucket, key.dtype);
   std::string rep = line;
   hsc_status st = HSC_OK;
   for (const LaunchCfg& c : cands) {

@@ -10,7 +10,7 @@
 
 namespace hsc {
 
-enum TuneKind { kTuneLatent = 1, kTuneSpectral = 2 };
+enum TuneKind { kTuneLatent = 1, kTuneSpectral = 2, kTuneLatentSrgb = 3 };  // sRGB epilogue: its own class
 
 // Configurations are cached per shape class: kernel, channels per launch,
 // secondary bounce on/off, and the light and pixel counts rounded up to

@@ -51,6 +51,8 @@ class ServeStats:
     wall_s: float = 0.0
     first_arrival_s: float = 0.0
     last_done_ms: float = 0.0
+    max_launch_call_ms: float = 0.0   # longest host time inside one backend.launch
+    max_loop_gap_ms: float = 0.0      # longest host time between two scheduler passes
 
     def summary(self, warmup_s: float = 0.0, arrivals: Optional[Sequence[float]] = None) -> dict:
         lat = np.asarray(self.latencies_ms, dtype=np.float64)
@@ -67,7 +69,8 @@ class ServeStats:
         return {"requests": int(lat.size), "p50_ms": nr(0.50), "p99_ms": nr(0.99), "mean_ms": float(lat.mean()),
                 "max_ms": float(srt[-1]), "launches": self.launches, "max_batch": self.max_batch,
                 "max_inflight_MB": self.max_inflight_bytes / 1e6,
-                "frames_per_s": float(len(self.latencies_ms) / max(self.wall_s, 1e-9))}
+                "frames_per_s": float(len(self.latencies_ms) / max(self.wall_s, 1e-9)),
+                "max_launch_call_ms": self.max_launch_call_ms, "max_loop_gap_ms": self.max_loop_gap_ms}
 
 
 class Scheduler:
@@ -99,8 +102,11 @@ class Scheduler:
         nxt = 0
         done = 0
         t_start = self.b.now_s()
+        prev = t_start
         while done < len(reqs):
             now = self.b.now_s()
+            st.max_loop_gap_ms = max(st.max_loop_gap_ms, 1e3 * (now - prev))
+            prev = now
             while nxt < len(reqs) and reqs[nxt].arrival_s <= now:
                 queue.append(reqs[nxt])
                 nxt += 1
@@ -127,7 +133,9 @@ class Scheduler:
                     batch.append(queue.popleft())
                     nbytes += fp
                 if batch:
+                    t_l = self.b.now_s()
                     h = self.b.launch(batch)
+                    st.max_launch_call_ms = max(st.max_launch_call_ms, 1e3 * (self.b.now_s() - t_l))
                     inflight.append(Inflight(h, batch, nbytes))
                     used += nbytes
                     st.launches += 1
@@ -223,17 +231,25 @@ class GpuBackend:
         self.outputs: Dict[int, object] = {}
         self.ref = torch.cuda.Event(enable_timing=True)
         self.t0 = None
+        # output buffers by pixel count; a buffer returns to its list when the
+        # launch that wrote it has completed (so any stream may reuse it)
+        self.pool: Dict[int, list] = collections.defaultdict(list)
 
-    def reserve(self, requests):
-        """Allocate and release one output of every request size on every
-        stream, so that the caching allocator holds the blocks before the
-        first arrival and no request waits on a device allocation."""
+    def reserve(self, requests, per_size: int = 4):
+        """Allocate `per_size` output buffers of every request size before the
+        first arrival.  A device allocation inside the serving loop can wait
+        for all queued work (the driver may synchronise the device), which
+        would stall every request behind it."""
         import torch
-        sizes = sorted({r.width * r.height for r in requests})
-        for s in self.streams:
-            with torch.cuda.stream(s):
-                held = [torch.empty(px, 3, device=self.sc.dev) for px in sizes]
-                del held
+        for px in sorted({r.width * r.height for r in requests}):
+            while len(self.pool[px]) < per_size:
+                self.pool[px].append(torch.empty(px, 3, device=self.sc.dev))
+        torch.cuda.synchronize(self.sc.dev)
+
+    def _buffer(self, px: int):
+        import torch
+        free = self.pool[px]
+        return free.pop() if free else torch.empty(px, 3, device=self.sc.dev)
 
     def start(self):
         import torch
@@ -258,7 +274,7 @@ class GpuBackend:
                 frames = []
                 for r in requests:
                     g1, lights, zm, zl, M = self.sc.frame_inputs(r)
-                    xyz = torch.empty(r.width * r.height, 3, device=self.sc.dev)
+                    xyz = self._buffer(r.width * r.height)
                     frames.append(self.hsc.BatchFrame(g1, None, zm, lights, zl, M, xyz))
                     outs.append((r.rid, xyz))
                 self.hsc.hsc_shade_frames(self.ctx, frames, stream=stream)
@@ -267,7 +283,7 @@ class GpuBackend:
                     g1 = self.sc.gbuf[(r.scene, r.width, r.height)]
                     lpos, linten = self.sc.lights[r.scene]
                     lights = self.hsc.Lights(lpos[:r.lights], linten[:r.lights])
-                    xyz = torch.empty(r.width * r.height, 3, device=self.sc.dev)
+                    xyz = self._buffer(r.width * r.height)
                     self.hsc.hsc_shade_spectral(self.ctx, g1, None, self.sc.mats[(r.scene, r.n)], lights,
                                                 self.sc.spd[(r.scene, r.n)][:r.lights], self.sc.T[r.n], xyz,
                                                 stream=stream)
@@ -280,9 +296,13 @@ class GpuBackend:
         return (ev, outs)
 
     def done(self, handle) -> Optional[float]:
-        ev, _ = handle
+        ev, outs = handle
         if not ev.query():
             return None
+        if not self.keep:
+            for _, xyz in outs:
+                self.pool[xyz.shape[0]].append(xyz)
+            outs.clear()
         return float(self.ref.elapsed_time(ev))
 
 
@@ -291,9 +311,9 @@ def serve(hsc, ctx, scenes: ResidentScenes, requests, mode="latent", budget_byte
     """Serve `requests` in real time.  Launch-configuration tuning is switched
     off while serving: tuning a new shape class synchronises the stream, which
     would stall the requests behind it (a server tunes ahead of time and
-    loads the result with hsc_tune_load).  Output blocks are reserved per
-    stream before the first arrival and the garbage collector is paused for
-    the loop."""
+    loads the result with hsc_tune_load).  Output buffers come from a pool
+    filled before the first arrival (no device allocation inside the loop),
+    and the garbage collector is paused for the loop."""
     backend = GpuBackend(hsc, ctx, scenes, mode=mode, keep_outputs=keep_outputs)
     sched = Scheduler(backend, budget_bytes, max_inflight=4, max_batch=max_batch)
     was = bool(ctx.autotune) if hasattr(ctx, "autotune") else False

@@ -141,6 +141,44 @@ def test_shade_latent_fused_matches_oracle(env, w, h, grid_spec, L, sec, k):
     assert metrics.rel_xyz_error(xyz.cpu().numpy(), xyz_ref) <= TOL
 
 
+@pytest.mark.parametrize("w,h,grid_spec,L,sec,k", [CASES[0], CASES[2], CASES[3], CASES[5], CASES[7]])
+@pytest.mark.parametrize("mode", ["FUSED", "PASSES"])
+def test_shade_latent_srgb8_equals_decode(env, w, h, grid_spec, L, sec, k, mode):
+    """The 8-bit sRGB written by the shading call (fused into the epilogue for
+    FUSED and k <= 15) equals hsc_decode_xyz of its latent image byte for
+    byte, and its XYZ output is unchanged by asking for the bytes."""
+    hsc, ctx, dev = env
+    import torch
+    f = hi.make_frame(w * 7 + h + L, w, h, grid_spec, n_smooth=20, n_saw=5, lights=L, secondary=sec)
+    if (w, h) == (256, 256):
+        f = hi.frame_config1()
+    E, D = _codec(k, f.n)
+    df = upload(hsc, ctx, f, dev)
+    zm, zl = encode_all(hsc, ctx, df, E)
+    M = torch.empty(3, k, device=dev)
+    hsc.hsc_fold_xyz(ctx, df.T, torch.from_numpy(D).to(dev), M)
+    # scale the decoder so that many pixels land in every part of the transfer curve
+    M *= 4.0
+    md = getattr(hsc, "HSC_" + mode)
+    lat = torch.empty(f.pixels, k, device=dev)
+    xyz = torch.empty(f.pixels, 3, device=dev)
+    rgb = torch.full((f.pixels, 3), 7, dtype=torch.uint8, device=dev)
+    hsc.hsc_shade_latent(ctx, df.g1, df.g2, zm, df.lights, zl, md, lat, xyz_out=xyz, M_xyz=M, srgb8_out=rgb)
+    lat2 = torch.empty(f.pixels, k, device=dev)
+    rgb_only = torch.empty(f.pixels, 3, dtype=torch.uint8, device=dev)
+    hsc.hsc_shade_latent(ctx, df.g1, df.g2, zm, df.lights, zl, md, lat2, M_xyz=M, srgb8_out=rgb_only)
+    xyz_plain = torch.empty(f.pixels, 3, device=dev)
+    hsc.hsc_shade_latent(ctx, df.g1, df.g2, zm, df.lights, zl, md, lat2, xyz_out=xyz_plain, M_xyz=M)
+    xd = torch.empty(f.pixels, 3, device=dev)
+    rd = torch.empty(f.pixels, 3, dtype=torch.uint8, device=dev)
+    hsc.hsc_decode_xyz(ctx, lat, M, xd, srgb8_out=rd)
+    hsc.hsc_sync(ctx)
+    assert torch.equal(rgb, rd) and torch.equal(rgb_only, rd)
+    assert torch.equal(xyz, xd) and torch.equal(xyz_plain, xyz)
+    if f.pixels >= 1000:
+        assert len(np.unique(rd.cpu().numpy())) > 50        # the bytes span the transfer curve
+
+
 @pytest.mark.parametrize("w,h,grid_spec,L,sec,k", [CASES[1], CASES[3], CASES[4], CASES[6], CASES[7]])
 def test_passes_bit_identical_to_fused(env, w, h, grid_spec, L, sec, k):
     hsc, ctx, dev = env

@@ -333,10 +333,12 @@ HSC_API void hsc_batch_destroy(hsc_batch* batch);
 /* One-shot batched launch for continuous batching: shades and decodes to XYZ
  * up to HSC_MAX_FRAMES_PER_CALL frames in one persistent launch on `stream`,
  * asynchronously (descriptors go through a ring of 8 pinned host buffers in
- * the context; a slot is reused once its previous launch has started, which
- * may block the host briefly).  Same results as hsc_batch_shade and as
+ * the context; a call takes a slot whose previous launch has finished and
+ * blocks the host only when all 8 are still in flight).  Same results as hsc_batch_shade and as
  * shading each frame alone.  Tile shape: 2 pixels per thread, 128 threads,
- * unless hsc_force_launch_config overrides it.                              */
+ * unless hsc_force_launch_config overrides it.  The first call allocates the
+ * ring (pinned host and device memory); count = 0 only does that, so a
+ * server can prepare before its first request.                              */
 HSC_API hsc_status hsc_shade_frames(hsc_ctx* ctx, const hsc_frame* frames, int count, void* stream);
 
 /* ------------------------------------------------------ RGB-to-latent upsampling */

@@ -347,24 +347,41 @@ hsc_status hsc_batch_shade(hsc_ctx* ctx, hsc_batch* batch, void* stream) {
 hsc_status hsc_shade_frames(hsc_ctx* ctx, const hsc_frame* frames, int count, void* stream) {
   hsc::clear_error();
   HSC_CHECK_CTX(ctx);
-  HSC_REQUIRE(count <= HSC_MAX_FRAMES_PER_CALL, "at most %d frames per call", HSC_MAX_FRAMES_PER_CALL);
-  HSC_TRY(hsc::validate_frames(frames, count));
+  HSC_REQUIRE(count >= 0 && count <= HSC_MAX_FRAMES_PER_CALL, "0 to %d frames per call", HSC_MAX_FRAMES_PER_CALL);
+  if (count > 0) HSC_TRY(hsc::validate_frames(frames, count));
   HSC_GUARD(ctx);
   cudaStream_t s = hsc::as_stream(stream);
-  // descriptor ring: the slot is reused only after its previous launch has
-  // consumed the descriptors (its event), so host writes never race a copy
-  hsc_ctx::DescSlot& slot = ctx->desc_ring[ctx->desc_next];
-  ctx->desc_next = (ctx->desc_next + 1) % hsc_ctx::kDescSlots;
-  if (!slot.h) {
-    if (cudaMallocHost(&slot.h, sizeof(hsc::FrameDesc) * HSC_MAX_FRAMES_PER_CALL) != cudaSuccess ||
-        cudaMalloc(&slot.d, sizeof(hsc::FrameDesc) * HSC_MAX_FRAMES_PER_CALL + 256) != cudaSuccess ||
-        cudaEventCreateWithFlags(&slot.ev, cudaEventDisableTiming) != cudaSuccess) {
-      cudaGetLastError();
-      return hsc::set_error(HSC_ERR_OOM, "cannot allocate the frame descriptor ring");
+  // the whole descriptor ring is allocated by the first call (pinned host
+  // memory and device memory: allocations that can wait for the device)
+  if (!ctx->desc_ring[0].h) {
+    for (int i = 0; i < hsc_ctx::kDescSlots; ++i) {
+      hsc_ctx::DescSlot& sl = ctx->desc_ring[i];
+      if (cudaMallocHost(&sl.h, sizeof(hsc::FrameDesc) * HSC_MAX_FRAMES_PER_CALL) != cudaSuccess ||
+          cudaMalloc(&sl.d, sizeof(hsc::FrameDesc) * HSC_MAX_FRAMES_PER_CALL + 256) != cudaSuccess ||
+          cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventRecord(sl.ev, s) != cudaSuccess) {
+        cudaGetLastError();
+        return hsc::set_error(HSC_ERR_OOM, "cannot allocate the frame descriptor ring");
+      }
     }
-  } else {
-    HSC_CUDA(cudaEventSynchronize(slot.ev));
   }
+  if (count == 0) return HSC_OK;
+  // descriptor ring: a slot is reused only after its previous launch has
+  // consumed the descriptors (its event), so host writes never race a copy.
+  // Launches on different streams finish out of order, so take the first
+  // slot whose launch is done and wait only when every slot is busy.
+  int pick = -1;
+  for (int i = 0; i < hsc_ctx::kDescSlots && pick < 0; ++i) {
+    const int j = (ctx->desc_next + i) % hsc_ctx::kDescSlots;
+    const cudaError_t q = cudaEventQuery(ctx->desc_ring[j].ev);
+    if (q == cudaSuccess) pick = j;
+    else if (q != cudaErrorNotReady) HSC_CUDA(q);
+  }
+  if (cudaPeekAtLastError() == cudaErrorNotReady) cudaGetLastError();  // a query's "not ready" is no error
+  if (pick < 0) pick = ctx->desc_next;
+  ctx->desc_next = (pick + 1) % hsc_ctx::kDescSlots;
+  hsc_ctx::DescSlot& slot = ctx->desc_ring[pick];
+  HSC_CUDA(cudaEventSynchronize(slot.ev));
   hsc::LaunchCfg c;
   c.sm_count = ctx->sm_count;
   c.ppt = 2;

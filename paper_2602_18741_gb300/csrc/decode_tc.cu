@@ -69,34 +69,63 @@ __device__ __forceinline__ void split3(float z, float (&part)[3]) {
 // kSegB[s] = (hi, mid, hi, lo, mid, hi)[s] of D_{i,c} in B.
 __constant__ int kSegB[6] = {0, 1, 0, 2, 1, 0};
 
-// Latent row p as 8 * KB packed bf16 pairs (K = 16 * KB), zero beyond the
-// used columns (and beyond P).
+// Latent row p in two steps, so that the loads of the next tile are in
+// flight while the current tile's MMA and epilogue run: load_a_raw issues the
+// loads (raw element bits, zero beyond k and beyond P), pack_a_row turns them
+// into 8 * KB packed bf16 pairs (K = 16 * KB): the values themselves (KB = 1)
+// or the six segments of the three-part split (KB = 3).
 template <int KB>
-__device__ __forceinline__ void load_a_row(const TcArgs& a, int64_t p, bool valid, uint32_t (&w)[8 * KB]) {
+struct RawRow {
+  // KB = 1: elements as 16-bit units, two per word (bf16 bits, or an fp8 byte);
+  // KB = 3: the FP32 values of codes 0 .. 7
+  uint32_t v[8];
+};
+
+template <int KB>
+__device__ __forceinline__ void load_a_raw(const TcArgs& a, int64_t p, bool valid, RawRow<KB>& r) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) r.v[j] = 0u;
+  if constexpr (KB == 3) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      if (valid && e < a.k) r.v[e] = __float_as_uint(__ldg(reinterpret_cast<const float*>(a.latent) + p * a.k + e));
+  } else {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      if (valid && e < a.k) {
+        const uint32_t bits = a.dt == HSC_FP8_E4M3
+                                  ? (uint32_t)__ldg(reinterpret_cast<const unsigned char*>(a.latent) + p * a.k + e)
+                                  : (uint32_t)__ldg(reinterpret_cast<const unsigned short*>(a.latent) + p * a.k + e);
+        r.v[e >> 1] |= bits << ((e & 1) * 16);
+      }
+    }
+  }
+}
+
+template <int KB>
+__device__ __forceinline__ void pack_a_row(const TcArgs& a, const RawRow<KB>& r, uint32_t (&w)[8 * KB]) {
 #pragma unroll
   for (int j = 0; j < 8 * KB; ++j) w[j] = 0u;
-  if (!valid) return;
   auto put = [&](int e, float v) {
     const uint32_t bits = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v));
     w[e >> 1] |= bits << ((e & 1) * 16);
   };
   if constexpr (KB == 1) {
+    if (a.dt == HSC_FP8_E4M3) {
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      if (e >= a.k) break;
-      float v;
-      if (a.dt == HSC_FP8_E4M3)
-        v = fp8_e4m3_to_float(__ldg(reinterpret_cast<const unsigned char*>(a.latent) + p * a.k + e));
-      else
-        v = __uint_as_float(((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(a.latent) + p * a.k + e)) << 16);
-      put(e, v);
+      for (int e = 0; e < 16; ++e) {
+        if (e >= a.k) break;
+        put(e, fp8_e4m3_to_float((unsigned char)(r.v[e >> 1] >> ((e & 1) * 16))));
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) w[j] = r.v[j];   // already bf16 pairs
     }
   } else {
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-      if (c >= a.k) break;
       float part[3];
-      split3(__ldg(reinterpret_cast<const float*>(a.latent) + p * a.k + c), part);
+      split3(__uint_as_float(r.v[c]), part);
       // segments of 8 columns: hi, hi, mid, hi, mid, lo
       put(0 + c, part[0]);
       put(8 + c, part[0]);
@@ -161,11 +190,13 @@ __global__ void __launch_bounds__(kTcThreads) decode_spectra_tc_kernel(const TcA
 
   const int64_t tiles = (a.P + kTcRows - 1) / kTcRows;
   uint32_t phase = 0;
-  // this thread's latent row of the first tile, loaded ahead
+  // this thread's latent row of the first tile
   uint32_t wA[8 * KB];
+  RawRow<KB> raw;
   {
     const int64_t p = (int64_t)blockIdx.x * kTcRows + t;
-    load_a_row<KB>(a, p, blockIdx.x < tiles && p < a.P, wA);
+    load_a_raw<KB>(a, p, blockIdx.x < tiles && p < a.P, raw);
+    pack_a_row<KB>(a, raw, wA);
   }
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t p0 = tile * kTcRows;
@@ -194,11 +225,12 @@ __global__ void __launch_bounds__(kTcThreads) decode_spectra_tc_kernel(const TcA
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
     }
-    // next tile's row, in flight while the MMA and this tile's epilogue run
+    // next tile's row: the loads stay in flight through the MMA and this
+    // tile's epilogue and are packed at the end of the iteration
     {
       const int64_t nt = tile + gridDim.x;
       const int64_t p = nt * kTcRows + t;
-      load_a_row<KB>(a, p, nt < tiles && p < a.P, wA);
+      load_a_raw<KB>(a, p, nt < tiles && p < a.P, raw);
     }
     if (t == 0) {
       if (!mbar_wait(bar, phase)) {
@@ -241,6 +273,7 @@ __global__ void __launch_bounds__(kTcThreads) decode_spectra_tc_kernel(const TcA
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       }
     }
+    pack_a_row<KB>(a, raw, wA);
   }
   if (t == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -53,6 +53,7 @@ class ServeStats:
     last_done_ms: float = 0.0
     max_launch_call_ms: float = 0.0   # longest host time inside one backend.launch
     max_loop_gap_ms: float = 0.0      # longest host time between two scheduler passes
+    launch_parts_ms: Dict[str, float] = field(default_factory=dict)  # longest time per part of a launch
 
     def summary(self, warmup_s: float = 0.0, arrivals: Optional[Sequence[float]] = None) -> dict:
         lat = np.asarray(self.latencies_ms, dtype=np.float64)
@@ -70,7 +71,8 @@ class ServeStats:
                 "max_ms": float(srt[-1]), "launches": self.launches, "max_batch": self.max_batch,
                 "max_inflight_MB": self.max_inflight_bytes / 1e6,
                 "frames_per_s": float(len(self.latencies_ms) / max(self.wall_s, 1e-9)),
-                "max_launch_call_ms": self.max_launch_call_ms, "max_loop_gap_ms": self.max_loop_gap_ms}
+                "max_launch_call_ms": self.max_launch_call_ms, "max_loop_gap_ms": self.max_loop_gap_ms,
+                "max_launch_parts_ms": dict(self.launch_parts_ms)}
 
 
 class Scheduler:
@@ -234,17 +236,30 @@ class GpuBackend:
         # output buffers by pixel count; a buffer returns to its list when the
         # launch that wrote it has completed (so any stream may reuse it)
         self.pool: Dict[int, list] = collections.defaultdict(list)
+        self.parts: Dict[str, float] = {}
 
     def reserve(self, requests, per_size: int = 4):
-        """Allocate `per_size` output buffers of every request size before the
-        first arrival.  A device allocation inside the serving loop can wait
-        for all queued work (the driver may synchronise the device), which
-        would stall every request behind it."""
+        """Prepare before the first arrival: allocate `per_size` output buffers
+        of every request size, the descriptor ring, and run one request of
+        every (k, n) so that its kernels are loaded.  A device allocation or
+        the first launch of a kernel inside the serving loop can wait for all
+        queued work, which would stall every request behind it."""
         import torch
         for px in sorted({r.width * r.height for r in requests}):
             while len(self.pool[px]) < per_size:
                 self.pool[px].append(torch.empty(px, 3, device=self.sc.dev))
+        if self.mode == "latent":
+            self.hsc.hsc_shade_frames(self.ctx, [], stream=self.streams[0])   # allocates the descriptor ring
+        # one request of every (k, n) through the real path: the first launch of
+        # a kernel loads its code, which can wait for the device as well
+        firsts = {}
+        for r in requests:
+            firsts.setdefault((r.k, r.n), r)
+        handles = [self.launch([r]) for r in firsts.values()]
         torch.cuda.synchronize(self.sc.dev)
+        for _, outs in handles:
+            self._release(outs)
+        self.outputs.clear()
 
     def _buffer(self, px: int):
         import torch
@@ -264,6 +279,11 @@ class GpuBackend:
     def footprint(self, r: hi.Request) -> int:
         return r.width * r.height * 12 + 4096
 
+    def _part(self, name, t0):
+        t1 = time.perf_counter()
+        self.parts[name] = max(self.parts.get(name, 0.0), 1e3 * (t1 - t0))
+        return t1
+
     def launch(self, requests):
         import torch
         stream = self.streams[self.si]
@@ -272,12 +292,15 @@ class GpuBackend:
         with torch.cuda.stream(stream):
             if self.mode == "latent":
                 frames = []
+                t = time.perf_counter()
                 for r in requests:
                     g1, lights, zm, zl, M = self.sc.frame_inputs(r)
                     xyz = self._buffer(r.width * r.height)
                     frames.append(self.hsc.BatchFrame(g1, None, zm, lights, zl, M, xyz))
                     outs.append((r.rid, xyz))
+                t = self._part("inputs", t)
                 self.hsc.hsc_shade_frames(self.ctx, frames, stream=stream)
+                self._part("shade_frames", t)
             else:
                 for r in requests:
                     g1 = self.sc.gbuf[(r.scene, r.width, r.height)]
@@ -288,21 +311,26 @@ class GpuBackend:
                                                 self.sc.spd[(r.scene, r.n)][:r.lights], self.sc.T[r.n], xyz,
                                                 stream=stream)
                     outs.append((r.rid, xyz))
+            t = time.perf_counter()
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(stream)
+            self._part("event", t)
         if self.keep:
             for rid, xyz in outs:
                 self.outputs[rid] = xyz
         return (ev, outs)
 
+    def _release(self, outs):
+        if not self.keep:
+            for _, xyz in outs:
+                self.pool[xyz.shape[0]].append(xyz)
+        outs.clear()
+
     def done(self, handle) -> Optional[float]:
         ev, outs = handle
         if not ev.query():
             return None
-        if not self.keep:
-            for _, xyz in outs:
-                self.pool[xyz.shape[0]].append(xyz)
-            outs.clear()
+        self._release(outs)
         return float(self.ref.elapsed_time(ev))
 
 
@@ -322,8 +350,10 @@ def serve(hsc, ctx, scenes: ResidentScenes, requests, mode="latent", budget_byte
     gc.disable()                   # no collector pause inside the real-time loop
     try:
         backend.reserve(requests)
+        backend.parts.clear()
         backend.start()
         stats = sched.run(requests)
+        stats.launch_parts_ms = dict(backend.parts)
         hsc.hsc_sync(ctx)
     finally:
         if gc_was:

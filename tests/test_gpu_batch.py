@@ -93,3 +93,21 @@ def test_batch_rejects_unsupported_k(env):
     with pytest.raises(hsc.HscError) as ei:
         hsc.hsc_batch_create(ctx, [bad])
     assert ei.value.status == hsc.HSC_ERR_INVALID_ARG
+
+
+def test_shade_frames_with_no_frames_only_prepares(env):
+    hsc, ctx, dev = env
+    import torch
+    c2 = hsc.Context(0)
+    hsc.hsc_shade_frames(c2, [])          # allocates the descriptor ring, launches nothing
+    hsc.hsc_shade_frames(c2, [])
+    spec = hi.batched_frame_specs(seed=6, count=1, min_side=9, max_side=9, ks=(6,))[0]
+    f, g1, g2, lights, zm, zl, M = _device_frame(hsc, c2, dev, spec, torch.float32)
+    xyz = torch.empty(f.pixels, 3, device=dev)
+    hsc.hsc_shade_frames(c2, [hsc.BatchFrame(g1, g2, zm, lights, zl, M, xyz)])
+    ref = torch.empty(f.pixels, 3, device=dev)
+    lat = torch.empty(f.pixels, 6, device=dev)
+    hsc.hsc_shade_latent(c2, g1, g2, zm, lights, zl, hsc.HSC_FUSED, lat, xyz_out=ref, M_xyz=M)
+    hsc.hsc_sync(c2)
+    assert torch.equal(xyz, ref)
+    c2.close()

@@ -238,7 +238,7 @@ class GpuBackend:
         self.pool: Dict[int, list] = collections.defaultdict(list)
         self.parts: Dict[str, float] = {}
 
-    def reserve(self, requests, per_size: int = 4):
+    def reserve(self, requests, per_size: int = 16):
         """Prepare before the first arrival: allocate `per_size` output buffers
         of every request size, the descriptor ring, and run one request of
         every (k, n) so that its kernels are loaded.  A device allocation or
@@ -286,10 +286,12 @@ class GpuBackend:
 
     def launch(self, requests):
         import torch
+        t_in = time.perf_counter()
         stream = self.streams[self.si]
         self.si = (self.si + 1) % len(self.streams)
         outs = []
         with torch.cuda.stream(stream):
+            self._part("enter", t_in)
             if self.mode == "latent":
                 frames = []
                 t = time.perf_counter()
@@ -314,7 +316,8 @@ class GpuBackend:
             t = time.perf_counter()
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(stream)
-            self._part("event", t)
+            t_exit = self._part("event", t)
+        self._part("exit", t_exit)
         if self.keep:
             for rid, xyz in outs:
                 self.outputs[rid] = xyz

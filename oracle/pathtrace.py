@@ -18,8 +18,8 @@ traces a Cornell-box stand-in (hsc_inputs.cornell_scene):
   blockwise product, then XYZ = T (D z).
 
 Reading where the paper is silent: no Russian roulette and no next-event
-estimation (the paper's path tracer settings are Mitsuba's; this build fixes
-the simplest unbiased estimator); a depth bound D in place of Mitsuba's
+estimation (the paper's path tracer settings are Mitsuba's; the simplest
+unbiased estimator is taken here); a depth bound D in place of Mitsuba's
 maxDepth.
 
 Determinism shared with the CUDA kernel (so both trace identical paths and

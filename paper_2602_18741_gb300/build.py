@@ -4,7 +4,7 @@
 
 Every ``csrc/*.cu`` is compiled to an object in parallel, then linked into
 ``paper_2602_18741_gb300/libhsc.so`` with the CUDA runtime linked statically
-(so the library depends only on the driver).  Objects go to ``_build/<machine>/`` at
+(so the library depends only on the CUDA driver).  Objects go to ``_build/<machine>/`` at
 the repository root.  A translation unit is rebuilt only when it or a header is
 newer than its object.
 """

@@ -116,6 +116,7 @@ CASES = [
     (33, 31, hi.GRID_81, 11, False, 12),
     (64, 17, hi.GRID_81, 7, True, 15),
     (29, 11, hi.GRID_81, 6, True, 18),        # k > 15: fused launch in channel chunks
+    (5, 3, (360.0, 2.5, 128), 7, True, 96),   # the largest code length and sample count
 ]
 
 

@@ -21,31 +21,67 @@ __device__ __forceinline__ float load_lat(const void* base, int64_t i, const flo
 }
 
 // One thread per pixel: XYZ = M z with the sums over c in order, then sRGB.
-template <int DT>
+// KT > 0 fixes k at compile time (the loads of a pixel's codes then issue
+// back to back); KT = 0 takes k at run time.
+template <int DT, int KT>
 __global__ void __launch_bounds__(kDBlock) decode_xyz_kernel(const void* __restrict__ latent,
-                                                             const float* __restrict__ scales, int64_t P, int k,
+                                                             const float* __restrict__ scales, int64_t P, int k_rt,
                                                              const float* __restrict__ M, float* __restrict__ xyz,
                                                              uint8_t* __restrict__ srgb8) {
+  const int k = KT > 0 ? KT : k_rt;
   __shared__ float s_M[3 * HSC_MAX_K];
   __shared__ float s_scale[HSC_MAX_K];
   for (int i = threadIdx.x; i < 3 * k; i += blockDim.x) s_M[i] = M[i];
   if (DT == HSC_FP8_E4M3)
     for (int i = threadIdx.x; i < k; i += blockDim.x) s_scale[i] = scales[i];
   __syncthreads();
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
-    float X = 0.0f, Y = 0.0f, Z = 0.0f;
-    for (int c = 0; c < k; ++c) {
-      const float z = load_lat<DT>(latent, p * k + c, s_scale, c);
-      X = __fmaf_rn(s_M[c], z, X);
-      Y = __fmaf_rn(s_M[k + c], z, Y);
-      Z = __fmaf_rn(s_M[2 * k + c], z, Z);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if constexpr (KT > 0) {
+    // four pixels per pass, all their codes loaded before any is used
+    constexpr int U = 4;
+    for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < P; p0 += U * stride) {
+      float z[U][KT];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t p = p0 + u * stride;
+#pragma unroll
+        for (int c = 0; c < KT; ++c) z[u][c] = p < P ? load_lat<DT>(latent, p * KT + c, s_scale, c) : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t p = p0 + u * stride;
+        if (p >= P) break;
+        float X = 0.0f, Y = 0.0f, Z = 0.0f;
+#pragma unroll
+        for (int c = 0; c < KT; ++c) {
+          X = __fmaf_rn(s_M[c], z[u][c], X);
+          Y = __fmaf_rn(s_M[KT + c], z[u][c], Y);
+          Z = __fmaf_rn(s_M[2 * KT + c], z[u][c], Z);
+        }
+        if (xyz) {
+          xyz[3 * p + 0] = X;
+          xyz[3 * p + 1] = Y;
+          xyz[3 * p + 2] = Z;
+        }
+        if (srgb8) xyz_to_srgb8(X, Y, Z, srgb8 + 3 * p);
+      }
     }
-    if (xyz) {
-      xyz[3 * p + 0] = X;
-      xyz[3 * p + 1] = Y;
-      xyz[3 * p + 2] = Z;
+  } else {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
+      float X = 0.0f, Y = 0.0f, Z = 0.0f;
+      for (int c = 0; c < k; ++c) {
+        const float z = load_lat<DT>(latent, p * k + c, s_scale, c);
+        X = __fmaf_rn(s_M[c], z, X);
+        Y = __fmaf_rn(s_M[k + c], z, Y);
+        Z = __fmaf_rn(s_M[2 * k + c], z, Z);
+      }
+      if (xyz) {
+        xyz[3 * p + 0] = X;
+        xyz[3 * p + 1] = Y;
+        xyz[3 * p + 2] = Z;
+      }
+      if (srgb8) xyz_to_srgb8(X, Y, Z, srgb8 + 3 * p);
     }
-    if (srgb8) xyz_to_srgb8(X, Y, Z, srgb8 + 3 * p);
   }
 }
 
@@ -123,11 +159,20 @@ int64_t stream_grid(int64_t work, int block, int sm_count, int per_sm) {
 hsc_status launch_decode_xyz(const void* latent, int dt, const float* scales, int64_t P, int k, const float* M,
                              float* xyz, uint8_t* srgb8, int sm_count, cudaStream_t s) {
   const int64_t grid = stream_grid(P, kDBlock, sm_count, 8);
+  auto go = [&](auto kern) { kern<<<(unsigned)grid, kDBlock, 0, s>>>(latent, scales, P, k, M, xyz, srgb8); };
   switch (dt) {
-    case HSC_F32: decode_xyz_kernel<HSC_F32><<<(unsigned)grid, kDBlock, 0, s>>>(latent, scales, P, k, M, xyz, srgb8); break;
-    case HSC_BF16: decode_xyz_kernel<HSC_BF16><<<(unsigned)grid, kDBlock, 0, s>>>(latent, scales, P, k, M, xyz, srgb8); break;
-    case HSC_F16: decode_xyz_kernel<HSC_F16><<<(unsigned)grid, kDBlock, 0, s>>>(latent, scales, P, k, M, xyz, srgb8); break;
-    default: decode_xyz_kernel<HSC_FP8_E4M3><<<(unsigned)grid, kDBlock, 0, s>>>(latent, scales, P, k, M, xyz, srgb8); break;
+    case HSC_F32:
+      if (k == 6) go(decode_xyz_kernel<HSC_F32, 6>);
+      else if (k == 9) go(decode_xyz_kernel<HSC_F32, 9>);
+      else if (k == 3) go(decode_xyz_kernel<HSC_F32, 3>);
+      else go(decode_xyz_kernel<HSC_F32, 0>);
+      break;
+    case HSC_BF16: go(decode_xyz_kernel<HSC_BF16, 0>); break;
+    case HSC_F16: go(decode_xyz_kernel<HSC_F16, 0>); break;
+    default:
+      if (k == 6) go(decode_xyz_kernel<HSC_FP8_E4M3, 6>);
+      else go(decode_xyz_kernel<HSC_FP8_E4M3, 0>);
+      break;
   }
   return check_launch("decode_xyz_kernel");
 }

@@ -549,6 +549,21 @@ def test_full_size_1080p_sampled(env, k):
     assert metrics.rel_xyz_error(xs[torch.from_numpy(idx).to(dev)].cpu().numpy(), xs_ref) <= TOL
     # invariants at full size: non-negative latent, finite XYZ
     assert float(lat.min()) >= 0.0 and bool(torch.isfinite(xs).all())
+    # the frame step's call (latent, XYZ and sRGB8 from one fused launch, the
+    # kernel's sRGB variant) gives the same latent and XYZ bits, and the
+    # sRGB8 bytes of the standalone decode
+    lat_r = torch.empty(f.pixels, k, device=dev)
+    x_r = torch.empty(f.pixels, 3, device=dev)
+    rgb = torch.empty(f.pixels, 3, device=dev, dtype=torch.uint8)
+    hsc.hsc_shade_latent(ctx, df.g1, df.g2, zm, df.lights, zl, hsc.HSC_FUSED, lat_r, xyz_out=x_r, M_xyz=M,
+                         srgb8_out=rgb)
+    rgb_d = torch.empty(f.pixels, 3, device=dev, dtype=torch.uint8)
+    hsc.hsc_decode_xyz(ctx, lat, M, None, srgb8_out=rgb_d)
+    hsc.hsc_sync(ctx)
+    assert torch.equal(lat_r, lat) and torch.equal(x_r, xl) and torch.equal(rgb, rgb_d)
+    u8 = cmf.srgb_to_u8(cmf.xyz_to_srgb(x_ref))
+    dd = np.abs(rgb[torch.from_numpy(idx).to(dev)].cpu().numpy().astype(int) - u8.astype(int))
+    assert dd.max() <= 1 and np.mean(dd == 0) > 0.99
 
 
 # ------------------------------------------------ launch configurations

@@ -58,6 +58,9 @@ def parse():
                     help="load tuned launch configurations from this file if it exists, save them there after the run")
     ap.add_argument("--serve-seconds", type=float, default=8.0,
                     help="length of the Poisson request stream served (0 = skip); the first quarter is warm-up")
+    ap.add_argument("--rows-only", default="",
+                    help="comma list of secondary row groups to run: core, batch, chains, upsample, pathtrace, "
+                         "sweep, serve (default: all)")
     ap.add_argument("--sweep-epochs", type=int, default=150,
                     help="epoch cap of the 700-variant codec sweep (0 = skip the sweep row)")
     return ap.parse_args()
@@ -376,6 +379,8 @@ def _traffic_from_profile():
 
 def secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T, Dd, zm, zl, lat, timed, flush):
     import torch
+    if "core" not in wanted_rows(args):
+        return group_rows(args, hsc, ctx, dev, timed)
     P = f.pixels
     evals = f.evals
     K, W = args.steps, args.warmup
@@ -500,13 +505,36 @@ def secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T,
                                           "de2000_p95": float(s[1]), "de94_mean": float(s[2]),
                                           "de76_mean": float(s[3])}
     hsc.hsc_sync(ctx)
-    rows.update(batch_rows(args, hsc, ctx, dev, timed))
-    rows.update(chain_rows(args, hsc, ctx, dev, timed))
-    rows.update(upsample_rows(args, hsc, ctx, dev, timed))
-    rows.update(pathtrace_rows(args, hsc, ctx, dev, timed))
-    if args.sweep_epochs > 0:
+    rows.update(group_rows(args, hsc, ctx, dev, timed))
+    return rows
+
+
+def wanted_rows(args):
+    """The secondary row groups to run (all unless --rows-only names some)."""
+    groups = ("core", "batch", "chains", "upsample", "pathtrace", "sweep", "serve")
+    if not args.rows_only:
+        return set(groups)
+    want = {g.strip() for g in args.rows_only.split(",") if g.strip()}
+    unknown = want - set(groups)
+    if unknown:
+        raise SystemExit(f"--rows-only: unknown groups {sorted(unknown)}; known: {', '.join(groups)}")
+    return want
+
+
+def group_rows(args, hsc, ctx, dev, timed):
+    want = wanted_rows(args)
+    rows = {}
+    if "batch" in want:
+        rows.update(batch_rows(args, hsc, ctx, dev, timed))
+    if "chains" in want:
+        rows.update(chain_rows(args, hsc, ctx, dev, timed))
+    if "upsample" in want:
+        rows.update(upsample_rows(args, hsc, ctx, dev, timed))
+    if "pathtrace" in want:
+        rows.update(pathtrace_rows(args, hsc, ctx, dev, timed))
+    if "sweep" in want and args.sweep_epochs > 0:
         rows.update(codec_sweep_rows(args, hsc, ctx, dev))
-    if args.serve_seconds > 0:
+    if "serve" in want and args.serve_seconds > 0:
         rows.update(serve_rows(args, hsc, ctx, dev))
     return rows
 

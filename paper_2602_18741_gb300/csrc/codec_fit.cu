@@ -83,7 +83,7 @@ __device__ __forceinline__ float batch_l(const FitArgs& a, int p, int i) {
 }
 
 template <int K>
-__global__ void __launch_bounds__(kFitThreads, K <= 6 ? 3 : 2) codec_fit_kernel(const FitArgs a) {
+__global__ void __launch_bounds__(kFitThreads, K <= 6 ? 3 : (K <= 9 ? 2 : 1)) codec_fit_kernel(const FitArgs a) {
   extern __shared__ float sm[];
   constexpr int k = K;
   const int n = a.n, P = a.P, v = blockIdx.x;

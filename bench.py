@@ -288,6 +288,9 @@ def run_hsc(args, rank: int, world: int):
                     "frac": round(achieved / peak, 4), "traffic": _traffic_from_profile(),
                     "kernel": "shade_codes_kernel<6,PPT,true,...,RGB> (fused latent shade + XYZ + sRGB8)",
                     "ops_per_eval": ops_per_eval, "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x {peak_mhz:.0f} MHz"}
+        probe = fp32_probe(hsc, ctx, dev, stream)
+        probe["frac_of_burst"] = round(achieved / probe["burst"], 4)
+        roofline["fp32_probe"] = probe
         e2e = e2e_leg(args, hsc, ctx, f, dev, stream, Ed, M, evals)
         tune = [ln for ln in hsc.hsc_tune_report(ctx).splitlines() if ln.strip()]
         if args.tune_file:
@@ -313,6 +316,38 @@ def run_hsc(args, rank: int, world: int):
         }
     ctx.close()
     return result
+
+
+def fp32_probe(hsc, ctx, dev, stream, iters: int = 2048, sustain_s: float = 1.0):
+    """Measured FP32 FMA issue rate (T lane-ops/s) of the library's
+    register-only FFMA probe: best of 10 single launches (burst) and the mean
+    over back-to-back launches for about `sustain_s` seconds (sustained),
+    CUDA events on the launching stream."""
+    import torch
+    sink = torch.empty(8 * torch.cuda.get_device_properties(dev).multi_processor_count * 256, device=dev)
+    for _ in range(3):
+        ops = hsc.hsc_fp32_peak_probe(ctx, sink, iters, stream=stream)
+    torch.cuda.synchronize()
+    best = math.inf
+    for _ in range(10):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        hsc.hsc_fp32_peak_probe(ctx, sink, iters, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        best = min(best, a.elapsed_time(b) * 1e-3)
+    reps = max(int(sustain_s / best), 1)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        hsc.hsc_fp32_peak_probe(ctx, sink, iters, stream=stream)
+    b.record(stream)
+    b.synchronize()
+    hsc.hsc_sync(ctx)
+    sustained = ops * reps / (a.elapsed_time(b) * 1e-3)
+    return {"burst": round(ops / best / 1e12, 3), "sustained": round(sustained / 1e12, 3), "unit": "T lane-ops/s",
+            "how": f"hsc_fp32_peak_probe: 8 CTAs x 256 threads per SM, 32 register-only FFMAs x {iters} per thread; "
+                   f"best of 10 launches and {reps} launches back to back"}
 
 
 def max_over_ranks(value: float, world: int, device) -> float:

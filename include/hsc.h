@@ -155,6 +155,16 @@ HSC_API hsc_status hsc_tune_load(hsc_ctx* ctx, const char* text);
  * persistent).
  * ppt <= 0 removes the override.                                            */
 HSC_API hsc_status hsc_force_launch_config(hsc_ctx* ctx, int ppt, int block, int waves, int vec, int chunk);
+/* FP32 issue-rate probe (measurement only; the shading kernels are FP32 issue
+ * bound and compared with the ALU peak SMs x 128 lanes x SM clock).  One
+ * launch of `ctas` CTAs of 256 threads (ctas <= 0: 8 per SM), each thread
+ * running `iters` iterations of 32 register-only FFMAs (8 independent chains).
+ *   sink: device, ctas x 256 float32, overwritten with meaningless values;
+ *   lane_ops_out: host, may be null; receives the FMA lane-operations of the
+ *   launch (ctas x 256 x iters x 32), which the caller divides by the time it
+ *   measures on `stream`.  1 <= iters <= 2^24.                              */
+HSC_API hsc_status hsc_fp32_peak_probe(hsc_ctx* ctx, int ctas, int iters, float* sink, int64_t* lane_ops_out,
+                                       void* stream);
 
 /* ----------------------------------------------------- colour projection */
 

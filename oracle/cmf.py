@@ -21,8 +21,10 @@ Pins (tests/test_oracle_cmf.py): equal-energy white chromaticity near (1/3,
 maps D65 to equal RGB and the transfer function is continuous; Lab of the white
 is (100, 0, 0), 18% grey has L* = 49.5, the linear segment has slope 903.3;
 Delta E vanishes on equal colours, is symmetric (2000, 76), reduces to
-|dL|/S_L on neutral pairs.  The chroma/hue terms of Delta E 2000 beyond those
-special cases are parity unpinned (no published test pairs are available).
+|dL|/S_L on neutral pairs, and Delta E 2000 reproduces, in both orders, the
+34 published conformance pairs of Sharma, Wu and Dalal (2005, Table 1;
+tests/golden/ciede2000_sharma2005.json), which exercise the chroma, hue and
+rotation terms and the hue-angle branch points.
 """
 from __future__ import annotations
 

@@ -437,6 +437,43 @@ def test_delta_e_on_shared_inputs(env):
     assert got[6] == f.pixels
 
 
+def test_delta_e2000_published_pairs_on_the_gpu(env):
+    # the published CIEDE2000 conformance pairs (Sharma, Wu and Dalal 2005),
+    # entered as XYZ images whose CIELAB against the kernel's white T @ 1 is
+    # the published Lab; a white pixel fixes Y_ref.  Pairs 9-15 sit on the
+    # hue-angle branch points with b* of +-0.001, which FP32 XYZ cannot carry
+    # exactly (the branch may flip), so they are left to the FP64 oracle pins.
+    hsc, ctx, dev = env
+    import json
+    import os
+    import torch
+    with open(os.path.join(os.path.dirname(__file__), "golden", "ciede2000_sharma2005.json")) as fh:
+        pairs = json.load(fh)["pairs"]
+    keep = [i for i in range(len(pairs)) if not 8 <= i <= 14]
+    T = torch.empty(3, 81, device=dev)
+    hsc.hsc_cmf_weights(ctx, 81, 380.0, 5.0, T)
+    W = T.double().sum(dim=1).cpu().numpy()
+
+    def xyz(lab):
+        lab = np.asarray(lab, dtype=np.float64)
+        fy = (lab[:, 0] + 16.0) / 116.0
+        f = np.stack([fy + lab[:, 1] / 500.0, fy, fy - lab[:, 2] / 200.0], axis=1)
+        d = 6.0 / 29.0
+        t = np.where(f > d, f ** 3, 3 * d * d * (f - 4.0 / 29.0))
+        return t * W[None, :] * W[1]
+
+    a = np.vstack([xyz([pairs[i]["lab1"] for i in keep]), W[None, :]])
+    b = np.vstack([xyz([pairs[i]["lab2"] for i in keep]), W[None, :]])
+    want = np.array([pairs[i]["de00"] for i in keep] + [0.0])
+    st = torch.zeros(8, device=dev, dtype=torch.float64)
+    de = torch.empty(len(want), device=dev)
+    for t_, r_ in ((a, b), (b, a)):
+        hsc.hsc_delta_e(ctx, torch.from_numpy(t_.astype(np.float32)).to(dev),
+                        torch.from_numpy(r_.astype(np.float32)).to(dev), T, st, de_out=de)
+        hsc.hsc_sync(ctx)
+        assert np.max(np.abs(de.cpu().numpy() - want)) < 2e-3
+
+
 def test_delta_e_latent_vs_spectral_end_to_end(env):
     # GPU render + GPU metric vs oracle render + oracle metric, within 0.01
     hsc, ctx, dev = env

@@ -122,3 +122,20 @@ def test_delta_e2000_small_differences_are_below_delta_e76_scale():
     d00 = cmf.delta_e2000(a, b)
     d76 = cmf.delta_e76(a, b)
     assert np.all(d00 <= 1.5 * d76 + 1e-12)
+
+
+SHARMA = os.path.join(os.path.dirname(__file__), "golden", "ciede2000_sharma2005.json")
+
+
+def test_delta_e2000_published_conformance_pairs():
+    # the 34 published CIEDE2000 test pairs (Sharma, Wu and Dalal 2005), in
+    # both orders; they exercise every term, including the hue-angle and
+    # mean-hue branches at 180 degrees
+    with open(SHARMA) as fh:
+        pairs = json.load(fh)["pairs"]
+    a = np.array([p["lab1"] for p in pairs], dtype=np.float64)
+    b = np.array([p["lab2"] for p in pairs], dtype=np.float64)
+    want = np.array([p["de00"] for p in pairs])
+    assert len(pairs) == 34
+    assert np.all(np.abs(cmf.delta_e2000(a, b) - want) < 5e-5)
+    assert np.all(np.abs(cmf.delta_e2000(b, a) - want) < 5e-5)

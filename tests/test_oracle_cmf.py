@@ -139,3 +139,18 @@ def test_delta_e2000_published_conformance_pairs():
     assert len(pairs) == 34
     assert np.all(np.abs(cmf.delta_e2000(a, b) - want) < 5e-5)
     assert np.all(np.abs(cmf.delta_e2000(b, a) - want) < 5e-5)
+
+
+def test_delta_e94_and_76_on_pure_chroma_and_hue_steps():
+    # Delta E 76 is the Euclidean Lab distance: a 3-4-5 triangle
+    assert abs(cmf.delta_e76(np.array([[50.0, 3.0, 4.0]]), np.array([[50.0, 0.0, 0.0]]))[0] - 5.0) < 1e-12
+    ref = np.array([[50.0, 30.0, 0.0], [50.0, 30.0, 0.0], [50.0, 0.0, 30.0]])
+    # a pure chroma step of 10 at C_ref = 30: 10 / (1 + 0.045 * 30)
+    # a 90-degree hue turn at constant C = 30: chord 2 C sin(45 deg) / (1 + 0.015 * 30)
+    # the same turn with the weights taken from the other colour (C_ref = 30 too) is unchanged
+    oth = np.array([[50.0, 40.0, 0.0], [50.0, 0.0, 30.0], [50.0, 30.0, 0.0]])
+    want = [10.0 / 2.35, 60.0 * np.sin(np.pi / 4) / 1.45, 60.0 * np.sin(np.pi / 4) / 1.45]
+    assert np.allclose(cmf.delta_e94(ref, oth), want, rtol=1e-12, atol=0)
+    # CIE94 is asymmetric: the weights come from the reference colour
+    back = cmf.delta_e94(oth[:1], ref[:1])[0]
+    assert abs(back - 10.0 / (1 + 0.045 * 40)) < 1e-12

@@ -512,6 +512,15 @@ def secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T,
         b_ = P4 * (args.k * esz + 81 * 4)
         rows[f"decode_spectra_tc_{tag}_4k"] = {"ms": m_, "GB_per_s": b_ / (m_ * 1e-3) / 1e9,
                                                "Mpx_per_s": P4 / (m_ * 1e-3) / 1e6, "bytes": b_}
+    # context for the decode rows (write-dominated streams): a write-only
+    # fill (torch) of the same output sizes
+    fill = {}
+    for tag, buf in (("1080p", out4[:P]), ("4k", out4)):
+        ms, _ = timed(lambda buf=buf: buf.fill_(0.0), K, W)
+        m_ = statistics.mean(ms)
+        fill[f"GB_per_s_{tag}"] = buf.numel() * 4 / (m_ * 1e-3) / 1e9
+    fill["note"] = "torch fill_ of a P x 81 float32 buffer: write-only bandwidth, context for the decode rows"
+    rows["hbm_write_only_fill"] = fill
     del out4
 
     xyz_only = torch.empty(P, 3, device=dev)

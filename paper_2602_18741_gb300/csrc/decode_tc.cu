@@ -14,10 +14,11 @@
 //   * one elected thread issues tcgen05.mma into a 128-lane x N-column TMEM
 //     accumulator and commits to an mbarrier;
 //   * each warp reads its 32 TMEM lanes (all columns, one wait) with
-//     tcgen05.ld, writes its rows to a [128 x n] FP32 staging tile, and one
-//     thread streams the whole tile (128 * n * 4 contiguous bytes) to global
-//     memory with a bulk async copy (cp.async.bulk), which overlaps the next
-//     tile's MMA.
+//     tcgen05.ld, writes its rows to its quarter of a [128 x n] FP32 staging
+//     tile, and its lane 0 streams those 32 rows (32 * n * 4 contiguous bytes)
+//     to global memory with a bulk async copy (cp.async.bulk), which overlaps
+//     the next tile's MMA; no block barrier stands between a warp's epilogue
+//     and its store.
 // FP32 latents (k <= 8) take the same path with each FP32 value split into
 // three bf16 parts, z = hi + mid + lo (each remainder is exact in FP32), and
 // the six products hi.hi, hi.mid, mid.hi, hi.lo, mid.mid, lo.hi laid side by
@@ -237,8 +238,6 @@ __global__ void __launch_bounds__(kTcThreads) decode_spectra_tc_kernel(const TcA
         *sOk = 0;
         atomicOr(a.err, HSC_DEVERR_TIMEOUT);
       }
-      // the staging tile is free once the previous bulk store has read it
-      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     }
     __syncthreads();
     if (!*sOk) break;
@@ -252,6 +251,9 @@ __global__ void __launch_bounds__(kTcThreads) decode_spectra_tc_kernel(const TcA
     for (int c0 = 0; c0 < NPAD; c0 += 16) TC_LD16(trow + (uint32_t)c0, (v + c0));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     const bool full = rows == kTcRows;
+    // this warp's staging rows are free once its previous store has read them
+    if ((t & 31) == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    __syncwarp();
 #pragma unroll
     for (int c = 0; c < NPAD; ++c) {
       if (c < n) {
@@ -265,17 +267,18 @@ __global__ void __launch_bounds__(kTcThreads) decode_spectra_tc_kernel(const TcA
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     if (full) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (t == 0) {
-        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(a.out + p0 * n),
-                     "r"(smem_u32(sOut)), "r"((uint32_t)(kTcRows * n * 4))
+      __syncwarp();
+      if ((t & 31) == 0) {
+        const int r0 = warp * 32;
+        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(a.out + (p0 + r0) * n),
+                     "r"(smem_u32(sOut + r0 * n)), "r"((uint32_t)(32 * n * 4))
                      : "memory");
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       }
     }
     pack_a_row<KB>(a, raw, wA);
   }
-  if (t == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  if ((t & 31) == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {

@@ -393,7 +393,8 @@ def test_decode_xyz_from_reduced_latents(env):
     assert metrics.rel_xyz_error(xyz.cpu().numpy(), shade.decode_xyz(deq, D.astype(np.float64), Tr)) <= TOL
 
 
-@pytest.mark.parametrize("k,n,P", [(6, 81, 1000), (9, 81, 4097), (6, 31, 63), (96, 128, 70), (3, 1, 5)])
+@pytest.mark.parametrize("k,n,P", [(6, 81, 1000), (9, 81, 4097), (6, 31, 63), (96, 128, 70), (3, 1, 5),
+                                   (6, 81, 160_077), (8, 128, 160_077)])
 def test_decode_spectra_f32(env, k, n, P):
     hsc, ctx, dev = env
     import torch

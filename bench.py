@@ -272,10 +272,19 @@ def run_hsc(args, rank: int, world: int):
     result = None
     if rank == 0:
         rows = {}
+        clk_box = {}
+
+        def stop_clocks():
+            # the nvidia-smi sampler queries the driver every 100 ms; it is
+            # stopped before the serving rows, whose latencies it would disturb
+            if clocks is not None and "clk" not in clk_box:
+                clk_box["clk"] = clocks.stop()
+
         if not args.no_rows:
             rows = secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T, Dd, zm, zl, lat,
-                                  timed, flush)
-        clk = clocks.stop() if clocks else None
+                                  timed, flush, before_serve=stop_clocks)
+        stop_clocks()
+        clk = clk_box.get("clk")
         # roofline of the dominant kernel: the fused shading launch
         sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
         peak_mhz = _peak_sm_mhz()
@@ -412,10 +421,11 @@ def _traffic_from_profile():
         return None
 
 
-def secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T, Dd, zm, zl, lat, timed, flush):
+def secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T, Dd, zm, zl, lat, timed, flush,
+                   before_serve=None):
     import torch
     if "core" not in wanted_rows(args):
-        return group_rows(args, hsc, ctx, dev, timed)
+        return group_rows(args, hsc, ctx, dev, timed, before_serve)
     P = f.pixels
     evals = f.evals
     K, W = args.steps, args.warmup
@@ -549,7 +559,7 @@ def secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T,
                                           "de2000_p95": float(s[1]), "de94_mean": float(s[2]),
                                           "de76_mean": float(s[3])}
     hsc.hsc_sync(ctx)
-    rows.update(group_rows(args, hsc, ctx, dev, timed))
+    rows.update(group_rows(args, hsc, ctx, dev, timed, before_serve))
     return rows
 
 
@@ -565,7 +575,7 @@ def wanted_rows(args):
     return want
 
 
-def group_rows(args, hsc, ctx, dev, timed):
+def group_rows(args, hsc, ctx, dev, timed, before_serve=None):
     want = wanted_rows(args)
     rows = {}
     if "batch" in want:
@@ -579,6 +589,8 @@ def group_rows(args, hsc, ctx, dev, timed):
     if "sweep" in want and args.sweep_epochs > 0:
         rows.update(codec_sweep_rows(args, hsc, ctx, dev))
     if "serve" in want and args.serve_seconds > 0:
+        if before_serve is not None:
+            before_serve()
         rows.update(serve_rows(args, hsc, ctx, dev))
     return rows
 

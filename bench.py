@@ -484,6 +484,19 @@ def secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T,
     rows["latent_fused_k9_xyz"] = {"ms": f9, "evals_per_s": evals / (f9 * 1e-3), "ops_per_eval": 22}
     rows["speedup_latent_fused_k9_vs_spectral"] = spec_ms / f9
 
+    # decode of the k = 9 FP32 latent to spectra (tensor cores, three-part split)
+    spec9 = torch.empty(P, 81, device=dev)
+
+    def dec9():
+        hsc.hsc_decode_spectra(ctx, lat9, D9d, spec9)
+
+    ms, _ = timed(dec9, K, W)
+    m9 = statistics.mean(ms)
+    b9 = P * (9 * 4 + 81 * 4)
+    rows["decode_spectra_f32_k9"] = {"ms": m9, "GB_per_s": b9 / (m9 * 1e-3) / 1e9, "Mpx_per_s": P / (m9 * 1e-3) / 1e6,
+                                     "bytes": b9}
+    del spec9
+
     # decode to spectra (FP32 CUDA cores): P x 81 float32 out
     spec_out = torch.empty(P, 81, device=dev)
 

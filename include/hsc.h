@@ -276,10 +276,11 @@ HSC_API hsc_status hsc_decode_xyz(hsc_ctx* ctx, const void* latent, hsc_dtype dt
                           uint8_t* srgb8_out, void* stream);
 
 /* Decode a latent image to n-sample spectra, s_hat = W_dec z (Eq. 4).
- *   dt = F32, k <= 8: tensor cores with FP32 accuracy: z and D split into
+ *   dt = F32, k <= 10: tensor cores with FP32 accuracy: z and D split into
  *        three bf16 parts each (hi + mid + lo), the six leading products
- *        laid side by side along K (K = 48), FP32 accumulation.
- *   dt = F32, k > 8: FP32 FMAs on CUDA cores, sums over channels in order.
+ *        laid side by side along K (K = 48 for k <= 8, 64 for k = 9, 10),
+ *        FP32 accumulation.
+ *   dt = F32, k > 10: FP32 FMAs on CUDA cores, sums over channels in order.
  *   dt = BF16 or FP8_E4M3 (+ scales): tensor-core contraction
  *        [P x 16 (k zero-padded)] x [16 x n] with BF16 operands (z exact in
  *        bf16 for fp8 codes; D * scale rounded to bf16) and FP32 accumulation.

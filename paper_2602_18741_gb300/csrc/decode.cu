@@ -237,9 +237,9 @@ hsc_status hsc_decode_spectra(hsc_ctx* ctx, const void* latent, hsc_dtype dt, co
   cudaStream_t s = hsc::as_stream(stream);
   if (dt == HSC_F32) {
     HSC_REQUIRE(hsc::aligned(latent, 4), "misaligned latent");
-    // k <= 8: tensor cores on the three-part bf16 split (FP32 accuracy);
+    // k <= 10: tensor cores on the three-part bf16 split (FP32 accuracy);
     // otherwise CUDA cores
-    if (k <= 8) return hsc::launch_decode_spectra_tc(ctx, latent, (int)dt, nullptr, pixels, k, D, n, spectra_out, s);
+    if (k <= 10) return hsc::launch_decode_spectra_tc(ctx, latent, (int)dt, nullptr, pixels, k, D, n, spectra_out, s);
     return hsc::launch_decode_spectra_f32(reinterpret_cast<const float*>(latent), pixels, k, D, n, spectra_out,
                                           ctx->sm_count, s);
   }

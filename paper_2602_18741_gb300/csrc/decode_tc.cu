@@ -19,11 +19,12 @@
 //     to global memory with a bulk async copy (cp.async.bulk), which overlaps
 //     the next tile's MMA; no block barrier stands between a warp's epilogue
 //     and its store.
-// FP32 latents (k <= 8) take the same path with each FP32 value split into
+// FP32 latents (k <= 10) take the same path with each FP32 value split into
 // three bf16 parts, z = hi + mid + lo (each remainder is exact in FP32), and
 // the six products hi.hi, hi.mid, mid.hi, hi.lo, mid.mid, lo.hi laid side by
-// side along K in segments of 8 columns (K = 48: three K = 16 MMAs into one
-// accumulator); every
+// side along K in segments of 8 columns for k <= 8 (K = 48: three K = 16 MMAs
+// into one accumulator) or 10 columns for k = 9, 10 (K = 60 padded to 64:
+// four MMAs); every
 // product is exact in FP32 and the dropped ones are below 2^-24 relative, so
 // the result has FP32 accuracy.
 // Every mbarrier wait is bounded; on expiry the kernel sets an error bit,
@@ -65,30 +66,33 @@ __device__ __forceinline__ void split3(float z, float (&part)[3]) {
   part[2] = to_bf16_value(__fsub_rn(r1, part[1]));
 }
 
-// K segments of the split FP32 form: columns 8s .. 8s+7 hold, for every code
-// c < k, parts (hi, hi, mid, hi, mid, lo)[s] of z_c in A and parts
+// K segments of the split FP32 form: columns SW s .. SW s + SW - 1 (segment
+// width SW = 8 for KB = 3, 10 for KB = 4) hold, for every code c < k, parts
+// (hi, hi, mid, hi, mid, lo)[s] of z_c in A and parts
 // kSegB[s] = (hi, mid, hi, lo, mid, hi)[s] of D_{i,c} in B.
 __constant__ int kSegB[6] = {0, 1, 0, 2, 1, 0};
+template <int KB>
+constexpr int seg_width() { return KB == 4 ? 10 : 8; }
 
 // Latent row p in two steps, so that the loads of the next tile are in
 // flight while the current tile's MMA and epilogue run: load_a_raw issues the
 // loads (raw element bits, zero beyond k and beyond P), pack_a_row turns them
 // into 8 * KB packed bf16 pairs (K = 16 * KB): the values themselves (KB = 1)
-// or the six segments of the three-part split (KB = 3).
+// or the six segments of the three-part split (KB = 3, 4).
 template <int KB>
 struct RawRow {
   // KB = 1: elements as 16-bit units, two per word (bf16 bits, or an fp8 byte);
-  // KB = 3: the FP32 values of codes 0 .. 7
-  uint32_t v[8];
+  // KB = 3, 4: the FP32 values of codes 0 .. SW - 1
+  uint32_t v[KB == 1 ? 8 : seg_width<KB>()];
 };
 
 template <int KB>
 __device__ __forceinline__ void load_a_raw(const TcArgs& a, int64_t p, bool valid, RawRow<KB>& r) {
 #pragma unroll
-  for (int j = 0; j < 8; ++j) r.v[j] = 0u;
-  if constexpr (KB == 3) {
+  for (int j = 0; j < (KB == 1 ? 8 : seg_width<KB>()); ++j) r.v[j] = 0u;
+  if constexpr (KB != 1) {
 #pragma unroll
-    for (int e = 0; e < 8; ++e)
+    for (int e = 0; e < seg_width<KB>(); ++e)
       if (valid && e < a.k) r.v[e] = __float_as_uint(__ldg(reinterpret_cast<const float*>(a.latent) + p * a.k + e));
   } else {
 #pragma unroll
@@ -123,17 +127,18 @@ __device__ __forceinline__ void pack_a_row(const TcArgs& a, const RawRow<KB>& r,
       for (int j = 0; j < 8; ++j) w[j] = r.v[j];   // already bf16 pairs
     }
   } else {
+    constexpr int SW = seg_width<KB>();
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
+    for (int c = 0; c < SW; ++c) {
       float part[3];
       split3(__uint_as_float(r.v[c]), part);
-      // segments of 8 columns: hi, hi, mid, hi, mid, lo
-      put(0 + c, part[0]);
-      put(8 + c, part[0]);
-      put(16 + c, part[1]);
-      put(24 + c, part[0]);
-      put(32 + c, part[1]);
-      put(40 + c, part[2]);
+      // segments of SW columns: hi, hi, mid, hi, mid, lo
+      put(0 * SW + c, part[0]);
+      put(1 * SW + c, part[0]);
+      put(2 * SW + c, part[1]);
+      put(3 * SW + c, part[0]);
+      put(4 * SW + c, part[1]);
+      put(5 * SW + c, part[2]);
     }
   }
 }
@@ -173,8 +178,8 @@ __global__ void __launch_bounds__(kTcThreads) decode_spectra_tc_kernel(const TcA
         v = __ldg(a.D + r * a.k + e);
         if (a.dt == HSC_FP8_E4M3) v = __fmul_rn(v, __ldg(a.scales + e));
       }
-    } else if (r < n && (e & 7) < a.k) {
-      const int seg = e >> 3, c = e & 7;
+    } else if (r < n && e < 6 * seg_width<KB>() && e % seg_width<KB>() < a.k) {
+      const int seg = e / seg_width<KB>(), c = e % seg_width<KB>();
       float part[3];
       split3(__ldg(a.D + r * a.k + c), part);
       v = part[kSegB[seg]];
@@ -335,7 +340,7 @@ hsc_status launch_decode_spectra_tc(hsc_ctx* ctx, const void* latent, int dt, co
   a.npad = (n + 15) / 16 * 16;
   a.out = out;
   a.err = ctx->d_err;
-  if (dt == HSC_F32) return launch_tc_n<3>(a, ctx->sm_count, s);
+  if (dt == HSC_F32) return k <= 8 ? launch_tc_n<3>(a, ctx->sm_count, s) : launch_tc_n<4>(a, ctx->sm_count, s);
   return launch_tc_n<1>(a, ctx->sm_count, s);
 }
 

@@ -127,9 +127,10 @@ class ClockSampler:
 
 def oracle_rate(seconds: float, k: int, threads: int = 1, max_rows: int = 1080):
     """Run the FP64 oracle's latent frame (encode, shading, decode to XYZ) on
-    consecutive 32-row bands of the 1920x1080 frame in a child process with
-    ``threads`` BLAS/OpenMP threads until ``seconds`` elapse (at least one
-    band); returns (evals per second, rows done, seconds)."""
+    consecutive 32-row bands of the 1920x1080 frame (the last one clamped to
+    the frame) in a child process with ``threads`` BLAS/OpenMP threads until
+    ``seconds`` elapse or ``max_rows`` rows are done (at least one band);
+    returns (evals per second, rows done, seconds)."""
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = str(threads)
@@ -142,10 +143,11 @@ def oracle_rate(seconds: float, k: int, threads: int = 1, max_rows: int = 1080):
         f"E, D = hi.load_codec({k}, 81)\n"
         "T = cmf.cmf_weights(*f.grid)\n"
         "W = f.width\n"
-        "band = 32\n"
+        f"top = min({max_rows}, f.height)\n"
         "rows = 0; evals = 0\n"
         "t0 = time.perf_counter()\n"
-        f"while rows < {max_rows} and (rows == 0 or time.perf_counter() - t0 < {seconds}):\n"
+        f"while rows < top and (rows == 0 or time.perf_counter() - t0 < {seconds}):\n"
+        "    band = min(32, top - rows)\n"
         "    idx = np.arange(rows * W, (rows + band) * W)\n"
         "    g1 = hi.GBuffer(f.g1.normal[idx], f.g1.pos[idx], f.g1.mat[idx])\n"
         "    g2 = hi.GBuffer(f.g2.normal[idx], f.g2.pos[idx], f.g2.mat[idx])\n"

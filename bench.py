@@ -25,6 +25,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -124,6 +125,17 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- oracle leg
+
+def host_cpu_info():
+    """Host CPUs seen by the bench: count, the affinity mask's size and the
+    BLAS/OpenMP thread setting the oracle leg overrides (it runs one thread)."""
+    try:
+        aff = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        aff = None
+    return {"cpu_count": os.cpu_count(), "affinity_cpus": aff, "machine": platform.machine(),
+            "omp_num_threads_env": os.environ.get("OMP_NUM_THREADS"), "oracle_threads": 1}
+
 
 def oracle_rate(seconds: float, k: int, threads: int = 1, max_rows: int = 1080):
     """Run the FP64 oracle's latent frame (encode, shading, decode to XYZ) on
@@ -312,7 +324,8 @@ def run_hsc(args, rank: int, world: int):
             rate, nrows, secs = oracle_rate(args.cpu_seconds, k, threads=1)
             cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"FP64 NumPy oracle latent frame (encode, shading, XYZ decode) on the first {nrows} rows "
-                             f"of the same 1920x1080 frame ({secs:.1f} s, one thread)"}
+                             f"of the same 1920x1080 frame ({secs:.1f} s, one thread)",
+                   "host": host_cpu_info()}
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -952,7 +965,8 @@ def run_reference(args, rank: int, world: int):
             "config": {"workload": WORKLOAD, "pixels": 1920 * 1080, "lights": 64, "k": args.k, "n": 81,
                        "sample": "each step: one 32-row band of the frame (61,440 pixels)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncores, "kind": "oracle",
-                             "sample": "32-row band of the 1920x1080 frame per step, FP64 NumPy, one thread"},
+                             "sample": "32-row band of the 1920x1080 frame per step, FP64 NumPy, one thread",
+                             "host": host_cpu_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

@@ -74,7 +74,7 @@ typedef enum {
   HSC_ERR_INVALID_ARG = 1,   /* bad size, null or misaligned pointer, bad enum   */
   HSC_ERR_CUDA = 2,          /* a CUDA runtime call failed (message has details) */
   HSC_ERR_OOM = 3,           /* context scratch could not be allocated           */
-  HSC_ERR_UNSUPPORTED = 4,   /* valid request this build does not implement      */
+  HSC_ERR_UNSUPPORTED = 4,   /* valid request the library does not implement     */
   HSC_ERR_TIMEOUT = 5,       /* a bounded device wait ran out                    */
   HSC_ERR_DEVICE_CHECK = 6   /* a kernel flagged bad input (see hsc_sync)        */
 } hsc_status;

@@ -1,4 +1,5 @@
 """Fit and store the codecs (E, D) used as inputs by the tests and the bench.
+Test infrastructure (input data generation), not part of the product path.
 
 Runs the oracle's projected-gradient fit of Eq. 6 (paper weights, Sec. 3.5)
 on the seeded synthetic training set for k in {6, 9} and n in {31, 81}, and

@@ -1,5 +1,6 @@
 """Fit and store the RGB-to-latent upsampling networks used by the tests and
 the bench.
+Test infrastructure (input data generation), not part of the product path.
 
 Trains the oracle's network (Sec. 4: 3 -> 128 -> 128 -> k, SiLU) on the
 linear RGB colours and codes of the seeded training reflectances under the

@@ -593,7 +593,7 @@ def secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T,
 
 def wanted_rows(args):
     """The secondary row groups to run (all unless --rows-only names some)."""
-    groups = ("core", "batch", "chains", "upsample", "pathtrace", "sweep", "serve")
+    groups = ("core", "small", "batch", "chains", "upsample", "pathtrace", "sweep", "serve")
     if not args.rows_only:
         return set(groups)
     want = {g.strip() for g in args.rows_only.split(",") if g.strip()}
@@ -606,6 +606,8 @@ def wanted_rows(args):
 def group_rows(args, hsc, ctx, dev, timed, before_serve=None):
     want = wanted_rows(args)
     rows = {}
+    if "small" in want:
+        rows.update(small_frame_rows(args, hsc, ctx, dev))
     if "batch" in want:
         rows.update(batch_rows(args, hsc, ctx, dev, timed))
     if "chains" in want:
@@ -621,6 +623,77 @@ def group_rows(args, hsc, ctx, dev, timed, before_serve=None):
             before_serve()
         rows.update(serve_rows(args, hsc, ctx, dev))
     return rows
+
+
+def small_frame_rows(args, hsc, ctx, dev, replays: int = 200):
+    """The 256x256 frame (n = 31, k = 6, 4 lights, direct only): launch
+    bound, so the latent frame (two encodes + fused shade with XYZ), the
+    latent shade alone (assets already encoded) and the spectral frame are
+    each captured once in a CUDA graph and replayed back to back;
+    microseconds per frame (inputs of ~4 MB stay in L2)."""
+    import torch
+    f = hi.frame_config1()
+    E, D = hi.load_codec(6, 31)
+
+    def t(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    g1 = hsc.GBuffer(t(f.g1.normal), t(f.g1.pos), t(f.g1.mat))
+    lights = hsc.Lights(t(f.light_pos), t(f.light_intensity))
+    mats, spd, Ed, Dd = t(f.mat_spectra), t(f.light_spd), t(E), t(D)
+    T = torch.empty(3, 31, device=dev)
+    hsc.hsc_cmf_weights(ctx, 31, f.grid[0], f.grid[1], T)
+    M = torch.empty(3, 6, device=dev)
+    hsc.hsc_fold_xyz(ctx, T, Dd, M)
+    zm = torch.empty(mats.shape[0], 6, device=dev)
+    zl = torch.empty(spd.shape[0], 6, device=dev)
+    lat = torch.empty(f.pixels, 6, device=dev)
+    xyz_l = torch.empty(f.pixels, 3, device=dev)
+    xyz_s = torch.empty(f.pixels, 3, device=dev)
+
+    def latent():
+        hsc.hsc_encode(ctx, Ed, mats, zm)
+        hsc.hsc_encode(ctx, Ed, spd, zl)
+        hsc.hsc_shade_latent(ctx, g1, None, zm, lights, zl, hsc.HSC_FUSED, lat, xyz_out=xyz_l, M_xyz=M)
+
+    def latent_shade():
+        # assets are encoded once per scene (Fig. 2b): the frame is one launch
+        hsc.hsc_shade_latent(ctx, g1, None, zm, lights, zl, hsc.HSC_FUSED, lat, xyz_out=xyz_l, M_xyz=M)
+
+    def spectral():
+        hsc.hsc_shade_spectral(ctx, g1, None, mats, lights, spd, T, xyz_s)
+
+    out = {}
+    side = torch.cuda.Stream(dev)
+    for name, fn in (("latent_k6", latent), ("latent_k6_shade_only", latent_shade), ("spectral_n31", spectral)):
+        for _ in range(3):          # eager warm-up (and the autotuner's first call)
+            fn()
+        torch.cuda.synchronize(dev)
+        hsc.hsc_sync(ctx)
+        g = torch.cuda.CUDAGraph()
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(g, stream=side):
+                fn()
+        torch.cuda.synchronize(dev)
+        for _ in range(3):
+            g.replay()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(replays):
+            g.replay()
+        b.record()
+        b.synchronize()
+        hsc.hsc_sync(ctx)
+        us = a.elapsed_time(b) * 1e3 / replays
+        out[name] = {"us_per_frame": us, "evals_per_s": f.evals / (us * 1e-6)}
+    return {"small_frame_256x256_graph": {"frame": "256x256, n = 31, 4 lights, direct only", "replays": replays,
+                                          "evals": f.evals, **out,
+                                          "speedup_latent_vs_spectral":
+                                              out["spectral_n31"]["us_per_frame"] / out["latent_k6"]["us_per_frame"],
+                                          "speedup_latent_shade_only_vs_spectral":
+                                              out["spectral_n31"]["us_per_frame"]
+                                              / out["latent_k6_shade_only"]["us_per_frame"]}}
 
 
 def upsample_rows(args, hsc, ctx, dev, timed):

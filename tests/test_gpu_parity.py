@@ -13,7 +13,7 @@ import pytest
 import hsc_inputs as hi
 from oracle import cmf, codec, metrics, quant, shade
 
-from helpers import encode_all, rel_err_rows, subset_frame, upload
+from helpers import assert_srgb8, encode_all, rel_err_rows, subset_frame, upload
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -363,9 +363,7 @@ def test_decode_xyz_and_srgb(env, k, P):
     hsc.hsc_sync(ctx)
     ref = shade.decode_xyz(z, D.astype(np.float64), cmf.cmf_weights(*hi.GRID_81))
     assert metrics.rel_xyz_error(xyz.cpu().numpy(), ref) <= TOL
-    u8 = cmf.srgb_to_u8(cmf.xyz_to_srgb(ref))
-    d = np.abs(rgb.cpu().numpy().astype(int) - u8.astype(int))
-    assert d.max() <= 1 and np.mean(d == 0) > 0.99
+    assert_srgb8(rgb.cpu().numpy(), cmf.xyz_to_srgb(ref))
 
 
 def test_decode_xyz_from_reduced_latents(env):
@@ -600,9 +598,7 @@ def test_full_size_1080p_sampled(env, k):
     hsc.hsc_decode_xyz(ctx, lat, M, None, srgb8_out=rgb_d)
     hsc.hsc_sync(ctx)
     assert torch.equal(lat_r, lat) and torch.equal(x_r, xl) and torch.equal(rgb, rgb_d)
-    u8 = cmf.srgb_to_u8(cmf.xyz_to_srgb(x_ref))
-    dd = np.abs(rgb[torch.from_numpy(idx).to(dev)].cpu().numpy().astype(int) - u8.astype(int))
-    assert dd.max() <= 1 and np.mean(dd == 0) > 0.99
+    assert_srgb8(rgb[torch.from_numpy(idx).to(dev)].cpu().numpy(), cmf.xyz_to_srgb(x_ref))
 
 
 # ------------------------------------------------ launch configurations

@@ -17,7 +17,8 @@ here as:
 * sRGB: the IEC 61966-2-1 XYZ -> linear sRGB matrix and transfer function.
 
 Pins (tests/test_oracle_cmf.py): equal-energy white chromaticity near (1/3,
-1/3) and ybar(555) near 1 (catch a dropped or mis-signed lobe); the sRGB matrix
+1/3) and ybar(555) near 1 (catch a dropped or mis-signed lobe); the fit within
+0.012 of the tabulated CIE 1931 observer at five wavelengths; the sRGB matrix
 maps D65 to equal RGB and the transfer function is continuous; Lab of the white
 is (100, 0, 0), 18% grey has L* = 49.5, the linear segment has slope 903.3;
 Delta E vanishes on equal colours, is symmetric (2000, 76), reduces to

@@ -154,3 +154,13 @@ def test_delta_e94_and_76_on_pure_chroma_and_hue_steps():
     # CIE94 is asymmetric: the weights come from the reference colour
     back = cmf.delta_e94(oth[:1], ref[:1])[0]
     assert abs(back - 10.0 / (1 + 0.045 * 40)) < 1e-12
+
+
+def test_cmf_fit_follows_the_cie_1931_table():
+    # the analytic fit against the tabulated observer at five wavelengths; a
+    # dropped, shifted or mis-scaled lobe moves some value by far more
+    g = _golden()["cie1931_2deg"]
+    lam = np.asarray(g["nm"], dtype=np.float64)
+    for name in ("xbar", "ybar", "zbar"):
+        fit = getattr(cmf, name)(lam)
+        assert np.max(np.abs(fit - np.asarray(g[name]))) < 0.012, name

@@ -764,7 +764,7 @@ def pathtrace_rows(args, hsc, ctx, dev, timed):
 
 
 def codec_sweep_rows(args, hsc, ctx, dev):
-    """The hyper-parameter sweep of the codec fit (Sec. 3.5) on the GPU: the
+    """The hyper-parameter sweep of the codec fit (Sec. 4.5) on the GPU: the
     700 loss-weight variants of the k = 6, n = 81 codec, softplus
     parameterisation, Adam (lr 1e-3), mini-batches of 128 of the 4096 training
     pairs (32 per epoch), at most 150 epochs with early stopping (patience 15)
@@ -846,7 +846,7 @@ def serve_rows(args, hsc, ctx, dev):
 
 
 def chain_rows(args, hsc, ctx, dev, timed):
-    """Multi-bounce chains (the codec-selection proxy of Sec. 3.5): 1,048,576
+    """Multi-bounce chains (the codec-selection proxy of Sec. 4.5): 1,048,576
     chains of depth 3 over held-out synthetic reflectances and lights, k = 6,
     n = 81; CIE94 and CIEDE2000 of the latent chain against the spectral chain
     per depth (the paper reports mean CIE94 per depth on its own data)."""

@@ -4,7 +4,7 @@ This module is shared by the CPU oracle, the tests and the benchmark.  It holds
 no arithmetic of the method itself (no encoding, shading, decoding or colour
 science): only seeded random draws and the closed-form spectra that stand in
 for the paper's measured data.  The paper trains and renders with Munsell
-reflectances, LSPDD lamp spectra and Mitsuba scenes (Sec. 3.4, Sec. 5.1), none
+reflectances, LSPDD lamp spectra and Mitsuba scenes (Sec. 4.4, Sec. 6.1), none
 of which is available here; every array below is a synthetic stand-in with the
 shapes and value ranges those data have.
 
@@ -79,7 +79,7 @@ _KB = 1.380649e-23
 
 def blackbody(lam: np.ndarray, temperature_k) -> np.ndarray:
     """Planck radiance at the grid wavelengths, normalised to unit peak on the
-    grid (the paper normalises its lights to unit peak, Sec. 3.4)."""
+    grid (the paper normalises its lights to unit peak, Sec. 4.4)."""
     t = np.atleast_1d(np.asarray(temperature_k, dtype=np.float64))[:, None]
     lm = lam[None, :] * 1e-9
     b = (2.0 * _H * _C ** 2) / (lm ** 5 * np.expm1(_H * _C / (lm * _KB * t)))
@@ -269,7 +269,7 @@ class TrainingSet:
 def training_set(grid_spec, seed: int = MASTER_SEED + 100, n_smooth: int = 1024,
                  n_saw: int = 128, n_bb: int = 256, n_nb: int = 256,
                  pairs: int = 4096) -> TrainingSet:
-    """Seeded stand-in for the paper's training spectra (Sec. 3.4): smooth and
+    """Seeded stand-in for the paper's training spectra (Sec. 4.4): smooth and
     saw-tooth reflectances, blackbody (2000-10000 K) and narrow-band (std 5-20
     nm) unit-peak lights, random reflectance-light pairs with a light scale
     augmentation U[0.5, 1]."""
@@ -288,7 +288,7 @@ def training_set(grid_spec, seed: int = MASTER_SEED + 100, n_smooth: int = 1024,
 
 
 def sweep_weight_grid() -> np.ndarray:
-    """The loss-weight grid of the codec sweep (Sec. 3.5) as (700, 4) float32
+    """The loss-weight grid of the codec sweep (Sec. 4.5) as (700, 4) float32
     rows (lambda_e2e, lambda_rec, lambda_code, lambda_col): e2e 0-2 by 0.5, rec
     0-3 by 0.5, code 0-1 by 0.25, col 0.25-1 by 0.25.  The grid as printed has
     7 x 5 x 5 x 5 = 875 points but is said to give 700 variants; leaving out

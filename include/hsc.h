@@ -3,14 +3,14 @@
  * shading with Hadamard spectral codes ("Compact Hadamard Latent Codes for
  * Efficient Spectral Rendering", arXiv 2602.18741).
  *
- * The method (Sec. 3-5 of the paper): a non-negative linear encoder E (k x n)
+ * The method (Sec. 4-6 of the paper): a non-negative linear encoder E (k x n)
  * and decoder D (n x k) map n-sample spectra to k-codes, k = 3B (Eq. 4);
  * scaling and addition stay exact in code space and the element-wise
  * (Hadamard) product of spectra is replaced by the blockwise product of codes
- * (Eq. 5).  Assets are encoded once, the k-code image is rendered as B RGB
+ * (Eq. 6).  Assets are encoded once, the k-code image is rendered as B RGB
  * passes and reassembled, then decoded once to spectra, XYZ or sRGB (Fig. 2b).
  *
- * Shading model (the paper path-traces in Mitsuba, Sec. 5.1; this library
+ * Shading model (the paper path-traces in Mitsuba, Sec. 6.1; this library
  * shades a G-buffer instead): point lights l at p_l with intensity I_l, Lambert
  * BRDF rho/pi, inverse-square falloff, no visibility, plus an optional
  * indirect bounce through a secondary G-buffer point treated as a virtual
@@ -20,7 +20,7 @@
  *   h          = max(0, n1.d) max(0, -n2.d) / (|d|^2 max(|d|^2, eps)) / pi,  d = x2 - x1
  *   out        = R_m1 (.) (A(x1, n1) + h * (R_m2 (.) A(x2, n2)))
  * with (.) the element-wise product on n samples (spectral) or k channels
- * (latent, Eq. 5).
+ * (latent, Eq. 6).
  *
  * Conventions for every entry point
  * ---------------------------------
@@ -170,7 +170,7 @@ HSC_API hsc_status hsc_fp32_peak_probe(hsc_ctx* ctx, int ctas, int iters, float*
 
 /* Integration weights of the CIE 1931 2-degree observer on the grid
  * lambda_i = lambda0 + i*dlambda, i < n (paper: T_cmf in R^{3 x n}, colour
- * loss of Sec. 3.3).  The CMFs are the analytic multi-lobe Gaussian fit of
+ * loss of Sec. 4.3).  The CMFs are the analytic multi-lobe Gaussian fit of
  * Wyman, Sloan and Shirley (JCGT 2013), evaluated in FP32;
  * T[c][i] = cmf_c(lambda_i) dlambda / sum_j ybar(lambda_j) dlambda with the
  * normalising sum accumulated in FP64, so the unit spectrum has Y = 1.
@@ -214,7 +214,7 @@ HSC_API hsc_status hsc_shade_pass(hsc_ctx* ctx, const hsc_gbuffer* g1, const hsc
 HSC_API hsc_status hsc_reassemble(hsc_ctx* ctx, const float* const* passes, int B, int64_t pixels,
                           float* latent_out, void* stream);
 
-/* Latent shading of a whole frame (Sec. 3-5, Fig. 2b).
+/* Latent shading of a whole frame (Sec. 4-6, Fig. 2b).
  *   mode: HSC_PASSES (B shade passes into context scratch + reassembly) or
  *         HSC_FUSED (one launch for k <= 15; larger k in chunks of 15).
  *   latent_out: device P x k, latent_dt F32 (16-byte aligned) or FP8_E4M3
@@ -292,7 +292,7 @@ HSC_API hsc_status hsc_decode_spectra(hsc_ctx* ctx, const void* latent, hsc_dtyp
 /* --------------------------------------------------------- spectral shade */
 
 /* Naive n-sample spectral shading, the paper's ground truth whose cost is
- * linear in n (Sec. 1, Sec. 5): the shading model above on n samples, with
+ * linear in n (Sec. 1, Sec. 6): the shading model above on n samples, with
  * XYZ = T S fused.
  *   mat_spectra: device n_mat x n;  light_spd: device L x n (unit peak);
  *   T: device 3 x n from hsc_cmf_weights;  xyz_out: device P x 3;
@@ -354,7 +354,7 @@ HSC_API hsc_status hsc_shade_frames(hsc_ctx* ctx, const hsc_frame* frames, int c
 
 /* ------------------------------------------------------ RGB-to-latent upsampling */
 
-/* Latent upsampling from RGB (Sec. 4): per pixel a three-layer perceptron
+/* Latent upsampling from RGB (Sec. 5): per pixel a three-layer perceptron
  *     h1 = silu(W1 c + b1),  h2 = silu(W2 h1 + b2),  z = W3 h2 + b3,
  * silu(x) = x / (1 + exp(-x)), hidden width HSC_UPSAMPLE_HIDDEN (128).
  *   rgb: device P x 3 float32 linear RGB;  W1: device 128 x 3, b1: 128,
@@ -370,14 +370,14 @@ HSC_API hsc_status hsc_upsample_rgb(hsc_ctx* ctx, const float* rgb, int64_t pixe
 
 /* ------------------------------------------------------------- path tracing */
 
-/* Path tracing with per-channel throughput (the renderer of Sec. 5): camera
+/* Path tracing with per-channel throughput (the renderer of Sec. 6): camera
  * rays through jittered pixel positions, Lambertian reflection sampled by the
  * cosine (each reflection multiplies the throughput by the reflectance), a
  * path ends on an emitting rectangle, on leaving the scene or after `depth`
  * reflections; pixel = mean over `spp` samples of emit (.) mat_{m_0} (.) ...
  * With spectra (channels = n, to_xyz = T) this is the naive spectral path
  * tracer; with codes (channels = k, to_xyz = M = T D) the latent one, the
- * per-channel product being the blockwise product of Eq. 5.  The paths do
+ * per-channel product being the blockwise product of Eq. 6.  The paths do
  * not depend on the channels: both modes trace the same paths.
  *   quads: device n_quads x 8 float32 rows (axis 0/1/2, c, u0, u1, v0, v1,
  *     normal sign, material; material -1 = emitter): the rectangle
@@ -398,8 +398,8 @@ HSC_API hsc_status hsc_path_trace(hsc_ctx* ctx, const float* quads, int n_quads,
 
 /* ------------------------------------------------------- codec fitting sweep */
 
-/* One Adam step of the paper's codec parameterisation (Sec. 3.2-3.5):
- * E = softplus(E~), D = softplus(D~) with beta `softplus_beta`, loss Eq. 6
+/* One Adam step of the paper's codec parameterisation (Sec. 4.1-4.5):
+ * E = softplus(E~), D = softplus(D~) with beta `softplus_beta`, loss Eq. 8
  * (weights e2e, rec, code, col per variant) on one mini-batch shared by all
  * `variants`, for every variant at once (one CTA each).
  *   R_all, L_all: device rows of n float32 (training reflectances, lights);
@@ -422,8 +422,8 @@ HSC_API hsc_status hsc_codec_fit_step(hsc_ctx* ctx, int variants, int k, int n, 
                                       float lr, float beta1, float beta2, float eps, float softplus_beta,
                                       const int32_t* active, float* losses_out, float* grad_out, void* stream);
 
-/* The Eq. 6 loss terms of every active variant at its current parameters on
- * one batch (the validation loss of the sweep, Sec. 3.5), without a step;
+/* The Eq. 8 loss terms of every active variant at its current parameters on
+ * one batch (the validation loss of the sweep, Sec. 4.5), without a step;
  * arguments as hsc_codec_fit_step.  E_out: device variants x k x n
  * softplus(E~), D_out: device variants x n x k softplus(D~) (each NULL or
  * written; the decoder and encoder the selection stage evaluates).  At least
@@ -434,7 +434,7 @@ HSC_API hsc_status hsc_codec_fit_eval(hsc_ctx* ctx, int variants, int k, int n, 
                                       const float* Et, const float* Dt, float softplus_beta, const int32_t* active,
                                       float* losses_out, float* E_out, float* D_out, void* stream);
 
-/* Early stopping of the sweep (Sec. 3.5: training stops after `patience`
+/* Early stopping of the sweep (Sec. 4.5: training stops after `patience`
  * epochs without a lower validation loss).  Per variant v with active[v] != 0:
  * if val_loss[v * val_stride] < best_loss[v] the loss becomes best_loss[v],
  * wait[v] = 0 and Et[v], Dt[v] are copied to best_Et[v], best_Dt[v];
@@ -455,10 +455,10 @@ HSC_API hsc_status hsc_codec_fit_track(hsc_ctx* ctx, int variants, int k, int n,
 
 /* --------------------------------------------------------- multi-bounce chains */
 
-/* Multi-bounce chains, the codec-selection proxy of Sec. 3.5: chain c starts
+/* Multi-bounce chains, the codec-selection proxy of Sec. 4.5: chain c starts
  * from light chain_light[c] and multiplies in reflectance chain_refl[c][b] at
  * bounce b (S(b) = R (.) S(b-1)); the latent chain runs the same recurrence on
- * codes with the blockwise product (Eq. 5).  At every depth both are taken to
+ * codes with the blockwise product (Eq. 6).  At every depth both are taken to
  * XYZ (T S and M z with M = T D), scaled by 1 / max(T L) so the light's
  * largest tristimulus value is 1, converted to CIELAB with the equal-energy
  * white T @ 1, and compared by CIE94 (spectral chain as reference) and
@@ -480,8 +480,8 @@ HSC_API hsc_status hsc_chain_eval(hsc_ctx* ctx, const float* refl, int n_refl, c
 /* Colour difference of a test image against a reference image.  Both are
  * divided by Y_ref = max_p Y of the reference, converted to CIELAB with white
  * (T @ 1) (CIE 1976), and compared per pixel by CIEDE2000 (kL = kC = kH = 1),
- * CIE94 (graphic arts; the paper's codec-selection metric, Sec. 3.5) and
- * Delta E 76 (the paper's upsampler loss, Sec. 4.2).
+ * CIE94 (graphic arts; the paper's codec-selection metric, Sec. 4.5) and
+ * Delta E 76 (the paper's upsampler loss, Sec. 5.2).
  *   stats_out: device 8 doubles = {mean dE2000, p95 dE2000 (nearest rank),
  *              mean dE94, mean dE76, Y_ref, max dE2000, pixels, 0}.
  *   de_out: NULL or device P float32 per-pixel dE2000.

@@ -13,9 +13,9 @@ reordering beyond what each definition states, so each function can be checked
 against the paper by eye.  Modules:
 
 * ``cmf``     colour matching functions, integration weights, sRGB, CIELAB,
-              Delta E 76 / 94 / 2000 (Sec. 3.3 colour loss; Sec. 4.2 Lab)
+              Delta E 76 / 94 / 2000 (Sec. 4.3 colour loss; Sec. 5.2 Lab)
 * ``codec``   linear encoder/decoder and the blockwise Hadamard product
-              (Eq. 4-5), the training objective (Eq. 6 and its four terms)
+              (Eq. 4 and 6), the training objective (Eq. 8 and its four terms)
               and a projected-gradient fit of non-negative E, D
 * ``shade``   spectral and latent deferred shading, k/3-pass form with
               reassembly, and a brute-force per-pixel loop form (Fig. 2b)

@@ -1,10 +1,10 @@
 """Multi-bounce chains in spectral and latent space (float64).
 Test infrastructure only.
 
-Sec. 3.5 of the paper selects its codec with a synthetic b-bounce proxy: a
+Sec. 4.5 of the paper selects its codec with a synthetic b-bounce proxy: a
 light L is multiplied by a fresh reflectance at every bounce,
 S(1) = R(1) (.) L, S(b) = R(b) (.) S(b-1), the same recurrence runs in latent
-space with the blockwise product of Eq. 5, and the two are compared per depth
+space with the blockwise product of Eq. 6, and the two are compared per depth
 by CIE94 colour difference.  Here both chains are taken to colour with the
 CMF weights T; the latent chain is decoded with D first (T (D z)).
 

@@ -1,8 +1,8 @@
 """Colorimetry for the oracle (float64).  Test infrastructure only.
 
 The paper projects spectra to colour with the CIE colour matching functions
-(T_cmf in the colour loss, Sec. 3.3) and compares colours in CIELAB with
-Delta E 76 (upsampler loss, Sec. 4.2) and CIE94 (codec selection, Sec. 3.5).
+(T_cmf in the colour loss, Sec. 4.3) and compares colours in CIELAB with
+Delta E 76 (upsampler loss, Sec. 5.2) and CIE94 (codec selection, Sec. 4.5).
 It does not say which CMF tabulation, white point or exposure it uses.  Read
 here as:
 

@@ -1,21 +1,21 @@
 """Linear non-negative Hadamard codec (float64).  Test infrastructure only.
 
-Follows Sec. 3 of the paper:
+Follows Sec. 4 of the paper:
 
 * Eq. 4 (linear codec): z = E(s) = W_enc s with W_enc in R^{k x n};
   s_hat = D(z) = W_dec z with W_dec in R^{n x k}.
-* Eq. 5 (blockwise Hadamard product): codes of length k = 3B are split into B
+* Eq. 6 (blockwise Hadamard product): codes of length k = 3B are split into B
   blocks of three and multiplied block by block, the blocks concatenated.
-* Eq. 6 (total loss) with its four terms L_e2e, L_rec, L_code, L_col
-  (Sec. 3.3) and the selected weights lambda_e2e = 0.5, lambda_rec = 0.75,
-  lambda_code = 1.0, lambda_col = 0.5 (Sec. 3.5).
+* Eq. 8 (total loss) with its four terms L_e2e, L_rec, L_code, L_col
+  (Sec. 4.3) and the selected weights lambda_e2e = 0.5, lambda_rec = 0.75,
+  lambda_code = 1.0, lambda_col = 0.5 (Sec. 4.5).
 
 Readings where the paper is silent:
 
 * MSE is the mean over every element of the batch; the cosine in L_e2e is
   taken per sample along wavelength and averaged over the batch, and L_e2e is
   the product of the two batch means, as the formula is printed.
-* Non-negativity: the paper parameterises W = softplus(W~) (Eq. 5a) and trains
+* Non-negativity: the paper parameterises W = softplus(W~) (Eq. 5) and trains
   with Adam; here E, D are kept non-negative by projection onto the
   non-negative orthant inside a projected-gradient method with Armijo
   backtracking, full batch, float64.  Both give non-negative weights; the fit
@@ -56,7 +56,7 @@ def decode(D, Z):
 
 
 def blockwise_hadamard(zr, zl):
-    """Eq. 5: split both codes into B = k/3 blocks of three, multiply
+    """Eq. 6: split both codes into B = k/3 blocks of three, multiply
     block-by-block and concatenate the blocks."""
     zr = np.asarray(zr, dtype=np.float64)
     zl = np.asarray(zl, dtype=np.float64)
@@ -106,7 +106,7 @@ def _rowcos(a, b):
 
 
 def losses(E, D, batch: Batch, w=PAPER_WEIGHTS):
-    """Eq. 6 and its four terms (Sec. 3.3) on a batch of pairs."""
+    """Eq. 8 and its four terms (Sec. 4.3) on a batch of pairs."""
     R, L, T = batch.R, batch.L, batch.T
     zR, zL = encode(E, R), encode(E, L)
     zRL = blockwise_hadamard(zR, zL)
@@ -125,7 +125,7 @@ def total_loss(E, D, batch, w=PAPER_WEIGHTS):
 
 
 def gradient(E, D, batch: Batch, w=PAPER_WEIGHTS):
-    """Analytic gradient of Eq. 6 with respect to (E, D), by the chain rule
+    """Analytic gradient of Eq. 8 with respect to (E, D), by the chain rule
     through S_hat = D(E R (.) E L) and the four terms."""
     R, L, T = batch.R, batch.L, batch.T
     P, n = R.shape
@@ -188,7 +188,7 @@ class FitResult:
 def projected_gradient_fit(batch: Batch, k: int, iters: int = 5000, w=PAPER_WEIGHTS,
                            tol: float = 1e-8, armijo_c: float = 1e-4, shrink: float = 0.5,
                            E0=None, D0=None, step0: float = 1.0) -> FitResult:
-    """Minimise Eq. 6 over E >= 0, D >= 0 by projected gradient with Armijo
+    """Minimise Eq. 8 over E >= 0, D >= 0 by projected gradient with Armijo
     backtracking along the projection arc.  The trial step of each iteration
     is the Barzilai-Borwein step <s,s>/<s,y> of the last accepted move (first
     iteration: ``step0``); it is halved until
@@ -234,7 +234,7 @@ def projected_gradient_fit(batch: Batch, k: int, iters: int = 5000, w=PAPER_WEIG
 
 
 # ----------------------------------------------------------------------------
-# The paper's parameterisation (Sec. 3.2-3.5): W = softplus_beta(W~) with
+# The paper's parameterisation (Sec. 4.1-4.5): W = softplus_beta(W~) with
 # beta = 10, Adam on mini-batches.  One step, as the batched GPU sweep takes it.
 # ----------------------------------------------------------------------------
 
@@ -276,7 +276,7 @@ def adam_init(Et, Dt) -> AdamState:
 def adam_softplus_step(Et, Dt, st: AdamState, batch: Batch, w=PAPER_WEIGHTS, lr: float = 1e-3,
                        b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8, beta: float = SOFTPLUS_BETA):
     """One Adam step (bias-corrected moments) on the raw parameters (E~, D~)
-    of E = softplus(E~), D = softplus(D~) for the Eq. 6 loss on ``batch``;
+    of E = softplus(E~), D = softplus(D~) for the Eq. 8 loss on ``batch``;
     returns the new (E~, D~, state) and the loss terms at the old parameters."""
     E, D = softplus(Et, beta), softplus(Dt, beta)
     parts = losses(E, D, batch, w)

@@ -1,7 +1,7 @@
 """Fit and store the codecs (E, D) used as inputs by the tests and the bench.
 Test infrastructure (input data generation), not part of the product path.
 
-Runs the oracle's projected-gradient fit of Eq. 6 (paper weights, Sec. 3.5)
+Runs the oracle's projected-gradient fit of Eq. 8 (paper weights, Sec. 4.5)
 on the seeded synthetic training set for k in {6, 9} and n in {31, 81}, and
 writes ``hsc_inputs/codecs/codec_k{k}_n{n}.npz`` holding float32 E (k, n) and
 D (n, k) plus the fit log.  Calls only ``oracle`` and ``hsc_inputs``.

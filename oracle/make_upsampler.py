@@ -2,7 +2,7 @@
 the bench.
 Test infrastructure (input data generation), not part of the product path.
 
-Trains the oracle's network (Sec. 4: 3 -> 128 -> 128 -> k, SiLU) on the
+Trains the oracle's network (Sec. 5: 3 -> 128 -> 128 -> k, SiLU) on the
 linear RGB colours and codes of the seeded training reflectances under the
 stored k = 6 and k = 9 codecs on the 81-sample grid, and writes
 ``hsc_inputs/upsampler/upsampler_k{k}_n{n}.npz`` (float32 W1, b1, W2, b2, W3,

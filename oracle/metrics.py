@@ -7,8 +7,8 @@
   images are divided by Y_ref = max_p Y of the n-sample image, converted to
   CIELAB with white T @ 1, and Delta E 2000 (also 94, 76) is taken per pixel;
   reported as the mean and the nearest-rank 95th percentile (sort ascending,
-  index ceil(0.95 N) - 1).  The paper compares colours by CIE94 (Sec. 3.5) and
-  Delta E 76 (Sec. 4.2); Delta E 2000 is added as the primary statistic.
+  index ceil(0.95 N) - 1).  The paper compares colours by CIE94 (Sec. 4.5) and
+  Delta E 76 (Sec. 5.2); Delta E 2000 is added as the primary statistic.
 
 Pins: the nearest-rank percentile against a hand-sorted list; the statistics
 of identical images are zero.

@@ -1,9 +1,9 @@
 """Path tracing in spectral and in latent code space.  Test infrastructure only.
 
-The paper renders its latent images with a path tracer (Sec. 5.1; multi-bounce
+The paper renders its latent images with a path tracer (Sec. 6.1; multi-bounce
 results, Fig. of 1, 2, 3 and unbounded bounces): every spectrum is replaced by
 its code, the path throughput is multiplied by the material codes with the
-blockwise product (Eq. 5) at each interaction, the emission is added where a
+blockwise product (Eq. 6) at each interaction, the emission is added where a
 path meets a light, and the image is decoded once at the end.  This module
 traces a Cornell-box stand-in (hsc_inputs.cornell_scene):
 

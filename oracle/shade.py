@@ -1,11 +1,11 @@
 """Deferred G-buffer shading in spectral and latent space (float64).
 Test infrastructure only.
 
-The paper renders with an unmodified path tracer (Sec. 5.1): the spectral
+The paper renders with an unmodified path tracer (Sec. 6.1): the spectral
 ground truth propagates all n wavelength samples; the latent render packs the
 k-code into k/3 RGB triplets, renders k/3 passes, reassembles the k-channel
 latent image and decodes it once (Fig. 2b).  Light-material interaction is the
-element-wise product (Sec. 3 item 3), which Eq. 5 replaces by the blockwise
+element-wise product (Sec. 3 item 3), which Eq. 6 replaces by the blockwise
 Hadamard product of codes; light sums and scalings stay exact because the codec
 is linear (Eq. 4).
 
@@ -19,7 +19,7 @@ The paper does not fix a shading model for a G-buffer.  Read here as:
   h12 = max(0, n1.d) max(0, -n2.d) / (|d|^2 max(|d|^2, eps)),  d = x2 - x1;
 * spectral radiance  S = (R_m1/pi) (.) [E_s(x1,n1) + h12 (R_m2/pi) (.) E_s(x2,n2)];
 * latent radiance: the same formula with every spectrum replaced by its code
-  (R -> E R, spd -> E spd) and (.) by the blockwise product of Eq. 5;
+  (R -> E R, spd -> E spd) and (.) by the blockwise product of Eq. 6;
   XYZ_latent = T (D z), decoded unfolded.
 
 Pins (tests/test_oracle_shade.py): k = n identity codec makes latent equal

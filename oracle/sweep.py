@@ -1,7 +1,7 @@
-"""The codec hyper-parameter sweep of Sec. 3.5 (float64).  Test infrastructure
+"""The codec hyper-parameter sweep of Sec. 4.5 (float64).  Test infrastructure
 only.
 
-Sec. 3.5 trains one codec per setting of the four loss weights of Eq. 6, all
+Sec. 4.5 trains one codec per setting of the four loss weights of Eq. 8, all
 with the same data, architecture and optimiser (Adam, lr 1e-3, mini-batches
 of 128 pairs, at most 150 epochs, early stopping with patience 15), scores
 every trained codec with the multi-bounce proxy (CIE94 of the latent chain
@@ -12,7 +12,7 @@ Readings where the paper is silent:
 
 * An epoch is one pass over the training pairs in a seeded shuffled order,
   cut into whole mini-batches; the Adam step counter runs on across epochs.
-* The validation loss of a variant is its own weighted Eq. 6 total on one
+* The validation loss of a variant is its own weighted Eq. 8 total on one
   fixed validation batch, taken after every epoch.  An epoch improves on the
   best so far only when its loss is strictly lower (a NaN never improves);
   after ``patience`` epochs in a row without improvement the variant stops, and

@@ -1,6 +1,6 @@
 """RGB-to-latent upsampling network (float64).  Test infrastructure only.
 
-Sec. 4 of the paper maps a linear RGB colour to a k-dimensional latent code
+Sec. 5 of the paper maps a linear RGB colour to a k-dimensional latent code
 with a per-pixel multilayer perceptron of three fully connected layers, hidden
 width 128 and SiLU activations:
 

@@ -450,7 +450,7 @@ def hsc_shade_frames(ctx: Context, frames: Sequence[BatchFrame], stream=None):
 
 def hsc_upsample_rgb(ctx: Context, rgb: torch.Tensor, W1: torch.Tensor, b1: torch.Tensor, W2: torch.Tensor,
                      b2: torch.Tensor, W3: torch.Tensor, b3: torch.Tensor, z_out: torch.Tensor, stream=None):
-    """RGB-to-latent upsampling network (Sec. 4); see include/hsc.h."""
+    """RGB-to-latent upsampling network (Sec. 5); see include/hsc.h."""
     P = rgb.shape[0]
     k = W3.shape[0]
     if rgb.shape != (P, 3) or W1.shape != (128, 3) or W2.shape != (128, 128) or W3.shape != (k, 128) \
@@ -562,7 +562,7 @@ def hsc_codec_fit_track(ctx: Context, val_loss: torch.Tensor, Et: torch.Tensor, 
 def hsc_chain_eval(ctx: Context, refl: torch.Tensor, lights: torch.Tensor, E: torch.Tensor, D: torch.Tensor,
                    T: torch.Tensor, chain_light: torch.Tensor, chain_refl: torch.Tensor, de94_out: torch.Tensor,
                    de2000_out: torch.Tensor, stats_out: torch.Tensor, stream=None):
-    """Multi-bounce chain errors (Sec. 3.5 proxy); see include/hsc.h."""
+    """Multi-bounce chain errors (Sec. 4.5 proxy); see include/hsc.h."""
     k, n = E.shape
     chains, depth = chain_refl.shape
     if de94_out.shape != (depth, chains) or de2000_out.shape != (depth, chains) or stats_out.numel() < 4 * depth:

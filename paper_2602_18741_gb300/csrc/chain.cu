@@ -1,7 +1,7 @@
-// Multi-bounce chains: the codec-selection proxy of Sec. 3.5.  A light L is
+// Multi-bounce chains: the codec-selection proxy of Sec. 4.5.  A light L is
 // multiplied by a fresh reflectance at every bounce, S(b) = R(b) (.) S(b-1),
 // S(0) = L; the latent chain runs the same recurrence on codes with the
-// blockwise product (Eq. 5), z(b) = E R(b) (.) z(b-1), z(0) = E L.  Per chain
+// blockwise product (Eq. 6), z(b) = E R(b) (.) z(b-1), z(0) = E L.  Per chain
 // and depth both are projected to XYZ (T S(b) and M z(b), M = T D), scaled by
 // 1 / max(T L) so that the light's largest tristimulus value is 1, converted
 // to CIELAB with the equal-energy white T @ 1, and compared by CIE94

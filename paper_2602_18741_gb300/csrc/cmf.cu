@@ -1,7 +1,7 @@
 // CMF integration weights and the decoder fold M = T D.
 //
 // The paper's colour projection T_cmf (3 x n) holds the CIE colour matching
-// functions (colour loss, Sec. 3.3).  Here they are the analytic multi-lobe
+// functions (colour loss, Sec. 4.3).  Here they are the analytic multi-lobe
 // piecewise-Gaussian fit of the CIE 1931 2-degree observer published by
 // Wyman, Sloan and Shirley (JCGT 2(2), 2013): each function is a sum of lobes
 // a * exp(-((lambda - mu) / sigma)^2 / 2) with sigma taking one value below mu

@@ -1,10 +1,10 @@
 // Batched codec fitting: one Adam step of the paper's parameterisation
-// (E = softplus(E~), D = softplus(D~) with beta = 10, Sec. 3.2) on the Eq. 6
+// (E = softplus(E~), D = softplus(D~) with beta = 10, Sec. 4.1) on the Eq. 8
 // loss, for many hyper-parameter variants at once (the selection sweep of
-// Sec. 3.5).  One CTA per variant; all variants share the mini-batch.
+// Sec. 4.5).  One CTA per variant; all variants share the mini-batch.
 //
 // Per variant the loss needs, per pair p of the batch (R_p, L_p, Y_p = R_p (.)
-// L_p): zR = E R_p, zL = E L_p, zRL = zR (.) zL (Eq. 5), S = D zRL, and for
+// L_p): zR = E R_p, zL = E L_p, zRL = zR (.) zL (Eq. 6), S = D zRL, and for
 // the reconstruction term D zR, D zL; the cosine in L_e2e and the batch MSE
 // couple the pairs only through scalars.  So the kernel runs
 //   A. E, D from the raw parameters; zR, zL, E Y for every pair (dot
@@ -19,7 +19,7 @@
 // same kernel in evaluation mode stops after B (validation losses, and E, D
 // for the selection stage); variants whose `active` flag is 0 return at once.
 // hsc_codec_fit_track keeps the early-stopping state of every variant
-// (Sec. 3.5: best validation loss, epochs without improvement, the best
+// (Sec. 4.5: best validation loss, epochs without improvement, the best
 // parameters) and counts the variants still training.
 #include "common.cuh"
 

@@ -1,7 +1,7 @@
 // Colour-difference statistics of a test image against a reference image:
 // mean / nearest-rank p95 of CIEDE2000, means of CIE94 and Delta E 76.
-// The paper compares colours with CIE94 (codec selection, Sec. 3.5) and
-// Delta E 76 after the CIELAB transform (upsampler loss, Sec. 4.2).
+// The paper compares colours with CIE94 (codec selection, Sec. 4.5) and
+// Delta E 76 after the CIELAB transform (upsampler loss, Sec. 5.2).
 //
 // Pipeline, all on the caller's stream, no host round trip:
 //   1. max_p Y of the reference (unsigned max over float bits; Y >= 0).

@@ -1,7 +1,7 @@
 // Path tracing with per-channel throughput: the renderer the paper uses for
-// its latent images (Sec. 5), where every spectrum is replaced by its code and
+// its latent images (Sec. 6), where every spectrum is replaced by its code and
 // each surface interaction multiplies the path throughput by the material's
-// code with the blockwise product (Eq. 5).  With C = n channels and spectra
+// code with the blockwise product (Eq. 6).  With C = n channels and spectra
 // the same kernel is the naive spectral path tracer; with C = k and codes it
 // is the latent one.  The paths do not depend on the channels, so both modes
 // trace the same paths and differ only in the per-channel work, C multiplies

@@ -1,6 +1,6 @@
 // Per-channel fp8 e4m3 quantisation of an FP32 latent image.
 //   scale_c = max_p z_c(p) / 448 (1 for an all-zero channel), codes RNE(z * (1/scale_c)).
-// Latent values are non-negative (non-negative codec and spectra, Sec. 3.3), so
+// Latent values are non-negative (non-negative codec and spectra, Sec. 4.3), so
 // the channel maximum is an unsigned max over the float bit patterns.
 // Both kernels are HBM streams over the P x k image.
 #include "common.cuh"

@@ -4,7 +4,7 @@
 // Per pixel and per light the work is one geometry term g (13 FP32 ops + one
 // MUFU rsqrt) and KC FMAs acc[c] += g * v_l[c], where v_l = (I_l / pi) * E(spd_l)
 // is the light's scaled code.  After the light loop the blockwise Hadamard
-// product with the material codes (Eq. 5, element-wise on R^k) and the
+// product with the material codes (Eq. 6, element-wise on R^k) and the
 // indirect bounce give
 //     z[c] = zR1[c] * (A1[c] + h * (zR2[c] * A2[c])).
 // A pass (KC = 3) and the fused launch (KC = k) run the same template: each

@@ -1,4 +1,4 @@
-// RGB-to-latent upsampling (Sec. 4): per pixel a three-layer perceptron,
+// RGB-to-latent upsampling (Sec. 5): per pixel a three-layer perceptron,
 //     h1 = silu(W1 c + b1),  h2 = silu(W2 h1 + b2),  z = W3 h2 + b3,
 // hidden width 128, on the 5th-generation tensor cores.
 //

@@ -1,6 +1,6 @@
-"""Codec hyper-parameter sweep on the GPU (Sec. 3.5).
+"""Codec hyper-parameter sweep on the GPU (Sec. 4.5).
 
-Every variant (one setting of the four loss weights of Eq. 6) is a codec
+Every variant (one setting of the four loss weights of Eq. 8) is a codec
 E = softplus(E~), D = softplus(D~) trained with Adam on shared mini-batches;
 all variants advance together, one launch per mini-batch
 (hsc_codec_fit_step), are validated after every epoch (hsc_codec_fit_eval)

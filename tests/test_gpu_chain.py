@@ -1,4 +1,4 @@
-"""Multi-bounce chain evaluator (the Sec. 3.5 proxy) against the FP64 oracle."""
+"""Multi-bounce chain evaluator (the Sec. 4.5 proxy) against the FP64 oracle."""
 import numpy as np
 import pytest
 

@@ -1,4 +1,4 @@
-"""Batched codec fitting (softplus parameterisation, Adam; Sec. 3.2-3.5)
+"""Batched codec fitting (softplus parameterisation, Adam; Sec. 4.1-4.5)
 against the FP64 oracle.
 
 The loss terms are FP32 sums over P x n = 10,368 elements (relative error a

@@ -1,4 +1,4 @@
-"""The codec sweep on the GPU (Sec. 3.5) against the oracle: validation
+"""The codec sweep on the GPU (Sec. 4.5) against the oracle: validation
 losses, the early-stopping state, masked steps, a whole small sweep, and the
 selection by the multi-bounce proxy.
 

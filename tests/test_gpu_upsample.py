@@ -1,4 +1,4 @@
-"""RGB-to-latent upsampling network (Sec. 4) on the tensor cores against the
+"""RGB-to-latent upsampling network (Sec. 5) on the tensor cores against the
 FP64 oracle.
 
 Tolerance: the kernel follows the oracle's bf16 contract (forward_bf16) except

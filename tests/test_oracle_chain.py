@@ -1,4 +1,4 @@
-"""Pins of the multi-bounce chain oracle (Sec. 3.5 proxy)."""
+"""Pins of the multi-bounce chain oracle (Sec. 4.5 proxy)."""
 import numpy as np
 
 import hsc_inputs as hi

@@ -1,4 +1,4 @@
-"""Pins of the oracle's codec (Eq. 4-6) against properties the paper fixes."""
+"""Pins of the oracle's codec (Eq. 4-8) against properties the paper fixes."""
 import numpy as np
 
 import hsc_inputs as hi
@@ -12,7 +12,7 @@ def _small_batch(n=31, pairs=48, seed=5):
 
 
 def test_linearity_is_exact():
-    # Eq. 4: a linear codec keeps scaling and addition exact (Sec. 3.1).
+    # Eq. 4: a linear codec keeps scaling and addition exact (Sec. 4.1).
     rng = np.random.default_rng(0)
     E = rng.uniform(0, 1, (9, 81))
     D = rng.uniform(0, 1, (81, 9))
@@ -28,7 +28,7 @@ def test_linearity_is_exact():
 
 
 def test_blockwise_product_is_elementwise():
-    # Eq. 5 concatenates per-block products of 3-vectors: on R^k that is the
+    # Eq. 6 concatenates per-block products of 3-vectors: on R^k that is the
     # element-wise product, so k/3 RGB passes and one k-channel pass agree.
     rng = np.random.default_rng(1)
     a, b = rng.uniform(0, 1, (2, 10, 9))
@@ -49,7 +49,7 @@ def test_band_init_identity_at_k_equals_n():
 
 def test_identity_codec_has_zero_loss_and_is_a_fixed_point():
     # Sec. 3.1: with k = n the coordinate projection (identity) preserves all
-    # three operations exactly, so every term of Eq. 6 vanishes.
+    # three operations exactly, so every term of Eq. 8 vanishes.
     b = _small_batch(n=30)
     E, D = codec.band_init(30, 30)
     parts = codec.losses(E, D, b)

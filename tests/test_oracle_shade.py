@@ -125,7 +125,7 @@ def test_passes_equal_fused():
 
 
 def test_non_negativity():
-    # Sec. 3.3: non-negative weights and spectra keep codes, latent images
+    # Sec. 4.3: non-negative weights and spectra keep codes, latent images
     # and decoded spectra non-negative.
     f = _tiny(15, w=16, h=16)
     rng = np.random.default_rng(2)
@@ -137,7 +137,7 @@ def test_non_negativity():
 
 
 def test_light_sum_is_linear_in_lights():
-    # exact addition (Sec. 3.1): shading with two lights equals the sum of
+    # exact addition (Sec. 4.1): shading with two lights equals the sum of
     # shading with each alone, in latent space too
     f = _tiny(16, lights=2)
     E = np.random.default_rng(3).uniform(0, 0.2, (6, f.n))

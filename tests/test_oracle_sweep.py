@@ -1,4 +1,4 @@
-"""Pins of the codec-sweep oracle (Sec. 3.5): early stopping, training with
+"""Pins of the codec-sweep oracle (Sec. 4.5): early stopping, training with
 validation, selection."""
 import numpy as np
 

@@ -1,4 +1,4 @@
-"""Pins of the RGB-to-latent upsampling oracle (Sec. 4)."""
+"""Pins of the RGB-to-latent upsampling oracle (Sec. 5)."""
 import numpy as np
 
 from oracle import upsample as up

@@ -490,7 +490,9 @@ class PTScene:
              the rectangle {x[axis] = c, u0 <= x[u] <= u1, v0 <= x[v] <= v1}
              with (u, v) the other two axes in increasing order, its normal
              along +/- axis; material -1 marks the emitter.
-    spheres: (S, 5) rows (cx, cy, cz, radius, material).
+    spheres: (S, 5) rows (cx, cy, cz, radius, material); the normal is
+             (hit - centre) / radius, so a negative radius gives a sphere
+             whose normals point inward (a closed room seen from inside).
     refl:    (M, n) reflectances of the materials; emit: (n,) emitted
              radiance of the emitter (SPD times intensity).
     cam:     (4, 3) pinhole origin, image-plane lower-left corner, horizontal
@@ -531,6 +533,25 @@ def cornell_scene(width: int, height: int, grid_spec=GRID_81, light: str = "blac
     cam = np.array([[0.5, 0.5, -1.4], [0.5 - 0.5 * aspect, 0.0, 0.0], [aspect, 0.0, 0.0], [0.0, 1.0, 0.0]],
                    dtype=np.float32)
     return PTScene(quads, spheres, refl, intensity * spd, cam, tuple(grid_spec))
+
+
+def sphere_enclosure_scene(width: int, height: int, z0: float = 0.6, rho: float = 0.8, emission: float = 1.0,
+                           grid_spec=(400.0, 100.0, 4)) -> PTScene:
+    """A closed spherical room seen from inside: the unit sphere with inward
+    normals (a negative radius) of constant reflectance ``rho``, cut by an
+    emitting square in the plane z = z0 that covers the sphere's cross-section
+    there, so the part of the sphere above z0 is hidden behind the emitter.
+    The camera sits at (0, 0, -0.3) and looks down the -z axis at the lower
+    part of the sphere.  Constant spectra (``emission`` everywhere) on a small
+    grid."""
+    lam = grid(*grid_spec)
+    refl = np.full((1, lam.size), float(rho))
+    quads = np.array([[2, z0, -1.25, 1.25, -1.25, 1.25, -1, -1]], dtype=np.float32)
+    spheres = np.array([[0.0, 0.0, 0.0, -1.0, 0]], dtype=np.float32)
+    aspect = width / height
+    cam = np.array([[0.0, 0.0, -0.3], [-0.25 * aspect, -0.25, -0.8], [0.5 * aspect, 0.0, 0.0], [0.0, 0.5, 0.0]],
+                   dtype=np.float32)
+    return PTScene(quads, spheres, refl, np.full(lam.size, float(emission)), cam, tuple(grid_spec))
 
 
 SERVE_SIZES = ((512, 512), (1024, 1024), (1920, 1080), (2048, 2048), (3840, 2160))

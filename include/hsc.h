@@ -65,6 +65,7 @@ extern "C" {
 #define HSC_MAX_MAT (1 << 24)
 #define HSC_NOALLOC_MAX_K 96  /* channel limit of hsc_quantize_fp8_noalloc   */
 #define HSC_MAX_FRAMES_PER_CALL 512  /* frames per hsc_shade_frames call    */
+#define HSC_QUEUE_SLOTS 256  /* streams per context with their own tile counter */
 #define HSC_UPSAMPLE_HIDDEN 128      /* hidden width of the upsampling network */
 
 typedef struct hsc_ctx hsc_ctx;
@@ -226,7 +227,13 @@ HSC_API hsc_status hsc_reassemble(hsc_ctx* ctx, const float* const* passes, int 
  *         XYZ, the same bytes hsc_decode_xyz gives for the FP32 latent (fused
  *         into the shading epilogue for FUSED and k <= 15);
  *   M_xyz: device 3 x k from hsc_fold_xyz (required when either is set).
- * Uses context scratch for PASSES images and for the fp8 path.               */
+ * Uses context scratch for PASSES images and for the fp8 path (such calls on
+ * one context must be ordered on one stream).  A launch on the dynamic tile
+ * queue (a tuned or forced waves = -1) takes its tiles from a counter of its
+ * own stream, so F32 FUSED calls on different streams may overlap; after
+ * HSC_QUEUE_SLOTS distinct streams a context launches on the static
+ * persistent grid instead (same results).  Destroy a stream only once its
+ * launches have finished: a new stream may reuse the handle, and its counter. */
 HSC_API hsc_status hsc_shade_latent(hsc_ctx* ctx, const hsc_gbuffer* g1, const hsc_gbuffer* g2, int64_t pixels,
                             const void* mat_codes, int n_mat, const hsc_lights* lights,
                             const void* light_codes, int k, hsc_dtype code_dt, hsc_mode mode,
@@ -383,7 +390,8 @@ HSC_API hsc_status hsc_upsample_rgb(hsc_ctx* ctx, const float* rgb, int64_t pixe
  *     normal sign, material; material -1 = emitter): the rectangle
  *     x[axis] = c, u0 <= x[u] <= u1, v0 <= x[v] <= v1, (u, v) the other axes
  *     in increasing order;  spheres: device n_spheres x 5 (centre, radius,
- *     material);  camera: device 4 x 3 (origin, image-plane lower-left
+ *     material; the normal is (hit - centre) / radius, so a negative radius
+ *     makes the normals point inward: a closed room seen from inside);  camera: device 4 x 3 (origin, image-plane lower-left
  *     corner, horizontal and vertical spans; pixel index y * width + x with
  *     y up);  materials: device n_mat x channels;  emit: device channels;
  *   to_xyz: device 3 x channels;  xyz_out: device P x 3;  channels_out:

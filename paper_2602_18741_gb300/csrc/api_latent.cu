@@ -65,9 +65,18 @@ static ShadeArgs base_args(hsc_ctx* ctx, const hsc_gbuffer* g1, const hsc_gbuffe
 }
 
 // One shading launch of `kc` channels in the tuned (or default) configuration.
+// A dynamically scheduled launch takes its tiles from the counter pair of its
+// stream; with no pair left it runs as the persistent static grid instead
+// (same bits: the schedule never changes what a pixel computes).
 static hsc_status shade_launch(hsc_ctx* ctx, const ShadeArgs& a, int kc, bool sec, cudaStream_t s) {
   const TuneKey key = make_tune_key(a.srgb8 ? kTuneLatentSrgb : kTuneLatent, kc, sec, a.L, a.P, a.code_dt);
-  auto launch = [&](const LaunchCfg& c) { return launch_shade_codes(a, kc, sec, c, s); };
+  unsigned int* queue = stream_queue(ctx, s);
+  auto launch = [&](const LaunchCfg& c0) {
+    LaunchCfg c = c0;
+    c.queue = queue;
+    if (c.waves < 0 && !queue) c.waves = 1;
+    return launch_shade_codes(a, kc, sec, c, s);
+  };
   LaunchCfg cfg;
   HSC_TRY(tuned_cfg(ctx, key, latent_candidates(ctx), launch, s, &cfg));
   return launch(cfg);

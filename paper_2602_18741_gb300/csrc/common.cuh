@@ -20,7 +20,7 @@
 #define HSC_SMALL_SCRATCH (1u << 20)
 // Offsets inside the fixed scratch block.
 #define HSC_OFF_CHANMAX 0u          // HSC_MAX_K uint32 (fp8 per-channel max)
-#define HSC_OFF_QUEUE 512u          // one uint32 tile counter for dynamically scheduled launches
+#define HSC_OFF_QUEUE (768u << 10)  // HSC_QUEUE_SLOTS pairs of uint32 tile counters, one pair per stream
 #define HSC_OFF_FITTICKET 1024u     // one uint32 arrival ticket of hsc_codec_fit_track
 #define HSC_OFF_REDUCE 4096u        // reduction workspace for hsc_delta_e
 
@@ -65,6 +65,10 @@ struct hsc_ctx {
     cudaEvent_t ev = nullptr;
   } desc_ring[kDescSlots];
   int desc_next = 0;
+  // dynamically scheduled shading launches: the tile-counter pair of each
+  // stream seen so far (index into the HSC_OFF_QUEUE block), so launches on
+  // different streams never share a counter
+  std::map<void*, int> queue_slots;
 };
 
 // Device error flags.
@@ -77,6 +81,9 @@ hsc_status set_error(hsc_status st, const char* fmt, ...);
 hsc_status clear_error();
 hsc_status check_launch(const char* what);
 hsc_status ensure_big(hsc_ctx* ctx, size_t bytes, cudaStream_t stream);
+// The tile-counter pair of `stream` for dynamically scheduled launches, or
+// null once HSC_QUEUE_SLOTS streams have their own (launch statically then).
+unsigned int* stream_queue(hsc_ctx* ctx, cudaStream_t stream);
 
 // Makes ctx->device current for the scope of a call and restores the
 // caller's device afterwards.

@@ -53,6 +53,22 @@ hsc_status ensure_big(hsc_ctx* ctx, size_t bytes, cudaStream_t stream) {
   return HSC_OK;
 }
 
+// Launches on one stream run in order, so the last CTA of one launch resets
+// the pair before the next launch on that stream reads it; launches on two
+// streams may run at the same time and get two pairs.
+unsigned int* stream_queue(hsc_ctx* ctx, cudaStream_t stream) {
+  unsigned int* base = reinterpret_cast<unsigned int*>(ctx->d_small + HSC_OFF_QUEUE);
+  void* key = reinterpret_cast<void*>(stream);
+  auto it = ctx->queue_slots.find(key);
+  if (it != ctx->queue_slots.end()) return base + 2 * it->second;
+  const int slot = (int)ctx->queue_slots.size();
+  if (slot >= HSC_QUEUE_SLOTS) return nullptr;
+  ctx->queue_slots[key] = slot;
+  return base + 2 * slot;
+}
+
+static_assert(HSC_OFF_QUEUE + 2u * 4u * HSC_QUEUE_SLOTS <= HSC_SMALL_SCRATCH, "tile counters outside the scratch block");
+
 }  // namespace hsc
 
 extern "C" {

@@ -135,6 +135,9 @@ namespace hsc {
 // array is part of the library's device code, so every GPU on which the
 // library is loaded holds its 384 bytes until the process exits.
 static __device__ __align__(256) unsigned int g_noalloc_chan_max[HSC_NOALLOC_MAX_K];
+// launch_channel_max stages one word per channel in a shared array of
+// HSC_MAX_K words, which must hold every channel this entry point accepts
+static_assert(HSC_NOALLOC_MAX_K <= HSC_MAX_K, "the channel-max kernel stages at most HSC_MAX_K channels");
 
 namespace {
 

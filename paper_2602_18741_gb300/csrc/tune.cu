@@ -26,7 +26,6 @@ TuneKey make_tune_key(int kind, int channels, bool sec, int lights, int64_t pixe
 std::vector<LaunchCfg> latent_candidates(const hsc_ctx* ctx) {
   std::vector<LaunchCfg> v;
   LaunchCfg d = default_cfg(ctx);
-  d.queue = reinterpret_cast<unsigned int*>(ctx->d_small + HSC_OFF_QUEUE);
   v.push_back(d);
   for (int vec : {1, 2})
     for (int ppt : {1, 2, 4})
@@ -77,7 +76,6 @@ hsc_status tuned_cfg(hsc_ctx* ctx, const TuneKey& key, const std::vector<LaunchC
   if (ctx->forced.ppt > 0) {
     *out = ctx->forced;
     out->sm_count = ctx->sm_count;
-    out->queue = reinterpret_cast<unsigned int*>(ctx->d_small + HSC_OFF_QUEUE);
     return HSC_OK;
   }
   if (!ctx->autotune || cands.size() < 2) return HSC_OK;
@@ -85,7 +83,6 @@ hsc_status tuned_cfg(hsc_ctx* ctx, const TuneKey& key, const std::vector<LaunchC
   if (it != ctx->tuned.end()) {
     *out = it->second;
     out->sm_count = ctx->sm_count;
-    out->queue = reinterpret_cast<unsigned int*>(ctx->d_small + HSC_OFF_QUEUE);
     return HSC_OK;
   }
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;

@@ -35,6 +35,12 @@ import hsc_inputs as hi
 
 # --------------------------------------------------------------------------- scheduler
 
+# Host sleep of a scheduler pass that found nothing to do (seconds).  Polling
+# without a pause keeps one host core busy all the time; under a CPU quota on
+# the container that can use the quota up and get the whole process held for
+# the rest of the quota period.
+IDLE_SLEEP_S = 100e-6
+
 @dataclass
 class Inflight:
     handle: object          # backend completion handle
@@ -54,6 +60,10 @@ class ServeStats:
     max_launch_call_ms: float = 0.0   # longest host time inside one backend.launch
     max_loop_gap_ms: float = 0.0      # longest host time between two scheduler passes
     launch_parts_ms: Dict[str, float] = field(default_factory=dict)  # longest time per part of a launch
+    max_inflight_launches: int = 0    # most launches submitted and not yet complete, seen at a launch
+    batch_hist: Dict[int, int] = field(default_factory=dict)  # requests per launch -> number of launches
+    idle_sleeps: int = 0              # scheduler passes that found nothing to do and slept
+    host: Dict[str, float] = field(default_factory=dict)      # host CPU accounting of the run (host_usage)
 
     def summary(self, warmup_s: float = 0.0, arrivals: Optional[Sequence[float]] = None) -> dict:
         lat = np.asarray(self.latencies_ms, dtype=np.float64)
@@ -72,7 +82,10 @@ class ServeStats:
                 "max_inflight_MB": self.max_inflight_bytes / 1e6,
                 "frames_per_s": float(len(self.latencies_ms) / max(self.wall_s, 1e-9)),
                 "max_launch_call_ms": self.max_launch_call_ms, "max_loop_gap_ms": self.max_loop_gap_ms,
-                "max_launch_parts_ms": dict(self.launch_parts_ms)}
+                "max_launch_parts_ms": dict(self.launch_parts_ms),
+                "max_inflight_launches": self.max_inflight_launches,
+                "batch_hist": {str(b): c for b, c in sorted(self.batch_hist.items())},
+                "idle_sleeps": self.idle_sleeps, "host": dict(self.host)}
 
 
 class Scheduler:
@@ -82,6 +95,7 @@ class Scheduler:
     backend.done(handle) -> Optional[float]  (completion time in ms since start, or None)
     backend.footprint(request) -> bytes
     backend.now_s() -> seconds since start
+    backend.sleep(seconds)  (optional; time.sleep when absent)
     """
 
     def __init__(self, backend, budget_bytes: int, max_inflight: int = 4, max_batch: int = 64):
@@ -91,6 +105,10 @@ class Scheduler:
         self.max_batch = max_batch
 
     def run(self, requests: Sequence[hi.Request], idle_sleep_s: float = 0.0) -> ServeStats:
+        """Serve ``requests`` (arrival times in seconds from the start).  A
+        pass of the loop that admits, retires and launches nothing sleeps for
+        ``idle_sleep_s`` (capped at the time left to the next arrival) instead
+        of polling again at once; 0 polls continuously."""
         reqs = sorted(requests, key=lambda r: r.arrival_s)
         for r in reqs:
             if self.b.footprint(r) > self.budget:
@@ -124,6 +142,7 @@ class Scheduler:
                     done += 1
                 st.last_done_ms = max(st.last_done_ms, t_done)
                 used -= f.nbytes
+            retired = len(inflight) != len(still)
             inflight = still
             # admit in arrival order while the footprint fits, launch as one batch
             if queue and len(inflight) < self.max_inflight:
@@ -142,12 +161,54 @@ class Scheduler:
                     used += nbytes
                     st.launches += 1
                     st.max_batch = max(st.max_batch, len(batch))
+                    st.batch_hist[len(batch)] = st.batch_hist.get(len(batch), 0) + 1
+                    st.max_inflight_launches = max(st.max_inflight_launches, len(inflight))
                     st.max_inflight_bytes = max(st.max_inflight_bytes, used)
                     continue
-            if idle_sleep_s > 0:
-                time.sleep(idle_sleep_s)
+            if idle_sleep_s > 0 and not retired:
+                wait = idle_sleep_s
+                if nxt < len(reqs) and not queue:
+                    wait = min(wait, max(reqs[nxt].arrival_s - now, 0.0))
+                if wait > 0:
+                    st.idle_sleeps += 1
+                    getattr(self.b, "sleep", time.sleep)(wait)
         st.wall_s = self.b.now_s() - t_start
         return st
+
+
+def host_usage() -> Dict[str, float]:
+    """Host CPU accounting of this process and its control group: CPU seconds
+    used, voluntary and involuntary context switches, and the cgroup's CPU
+    quota and throttling counters (cgroup v2 cpu.max / cpu.stat, where
+    readable).  A scheduler pass that stalls for tens of milliseconds without
+    doing work is either descheduled by the kernel (involuntary switches) or
+    held by a CPU quota that the group has used up (nr_throttled)."""
+    import resource
+    ru = resource.getrusage(resource.RUSAGE_SELF)
+    out = {"cpu_s": ru.ru_utime + ru.ru_stime, "nvcsw": float(ru.ru_nvcsw), "nivcsw": float(ru.ru_nivcsw)}
+    try:
+        with open("/sys/fs/cgroup/cpu.stat") as fh:
+            for line in fh:
+                key, _, val = line.partition(" ")
+                if key in ("nr_periods", "nr_throttled", "throttled_usec", "usage_usec"):
+                    out["cg_" + key] = float(val)
+    except OSError:
+        pass
+    try:
+        with open("/sys/fs/cgroup/cpu.max") as fh:
+            quota, _, period = fh.read().strip().partition(" ")
+            out["cg_quota_cpus"] = -1.0 if quota == "max" else float(quota) / float(period)
+    except (OSError, ValueError):
+        pass
+    return out
+
+
+def usage_delta(before: Dict[str, float], after: Dict[str, float]) -> Dict[str, float]:
+    """Counters of host_usage() over an interval (the quota as it stands)."""
+    d = {k: after[k] - before[k] for k in after if k in before and k != "cg_quota_cpus"}
+    if "cg_quota_cpus" in after:
+        d["cg_quota_cpus"] = after["cg_quota_cpus"]
+    return d
 
 
 # --------------------------------------------------------------------------- GPU state
@@ -245,8 +306,11 @@ class GpuBackend:
         the first launch of a kernel inside the serving loop can wait for all
         queued work, which would stall every request behind it."""
         import torch
-        for px in sorted({r.width * r.height for r in requests}):
-            while len(self.pool[px]) < per_size:
+        sizes = collections.Counter(r.width * r.height for r in requests)
+        for px in sorted(sizes):
+            # outputs kept for the caller never return to the pool: one each
+            want = max(per_size, sizes[px] + 1) if self.keep else per_size
+            while len(self.pool[px]) < want:
                 self.pool[px].append(torch.empty(px, 3, device=self.sc.dev))
         if self.mode == "latent":
             self.hsc.hsc_shade_frames(self.ctx, [], stream=self.streams[0])   # allocates the descriptor ring
@@ -276,6 +340,9 @@ class GpuBackend:
     def now_s(self) -> float:
         return time.perf_counter() - self.t0
 
+    def sleep(self, seconds: float):
+        time.sleep(seconds)
+
     def footprint(self, r: hi.Request) -> int:
         return r.width * r.height * 12 + 4096
 
@@ -304,6 +371,7 @@ class GpuBackend:
                 self.hsc.hsc_shade_frames(self.ctx, frames, stream=stream)
                 self._part("shade_frames", t)
             else:
+                t = time.perf_counter()
                 for r in requests:
                     g1 = self.sc.gbuf[(r.scene, r.width, r.height)]
                     lpos, linten = self.sc.lights[r.scene]
@@ -313,6 +381,7 @@ class GpuBackend:
                                                 self.sc.spd[(r.scene, r.n)][:r.lights], self.sc.T[r.n], xyz,
                                                 stream=stream)
                     outs.append((r.rid, xyz))
+                self._part("shade_spectral", t)
             t = time.perf_counter()
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(stream)
@@ -338,15 +407,17 @@ class GpuBackend:
 
 
 def serve(hsc, ctx, scenes: ResidentScenes, requests, mode="latent", budget_bytes=40 * 10**9, max_batch=64,
-          keep_outputs=False):
+          keep_outputs=False, max_inflight=4, idle_sleep_s=IDLE_SLEEP_S):
     """Serve `requests` in real time.  Launch-configuration tuning is switched
     off while serving: tuning a new shape class synchronises the stream, which
     would stall the requests behind it (a server tunes ahead of time and
     loads the result with hsc_tune_load).  Output buffers come from a pool
     filled before the first arrival (no device allocation inside the loop),
-    and the garbage collector is paused for the loop."""
+    and the garbage collector is paused for the loop.  A pass with nothing to
+    do sleeps ``idle_sleep_s`` rather than polling again at once (see
+    IDLE_SLEEP_S)."""
     backend = GpuBackend(hsc, ctx, scenes, mode=mode, keep_outputs=keep_outputs)
-    sched = Scheduler(backend, budget_bytes, max_inflight=4, max_batch=max_batch)
+    sched = Scheduler(backend, budget_bytes, max_inflight=max_inflight, max_batch=max_batch)
     was = bool(ctx.autotune) if hasattr(ctx, "autotune") else False
     hsc.hsc_set_autotune(ctx, False)
     gc_was = gc.isenabled()
@@ -355,7 +426,9 @@ def serve(hsc, ctx, scenes: ResidentScenes, requests, mode="latent", budget_byte
         backend.reserve(requests)
         backend.parts.clear()
         backend.start()
-        stats = sched.run(requests)
+        u0 = host_usage()
+        stats = sched.run(requests, idle_sleep_s=idle_sleep_s)
+        stats.host = usage_delta(u0, host_usage())
         stats.launch_parts_ms = dict(backend.parts)
         hsc.hsc_sync(ctx)
     finally:

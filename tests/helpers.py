@@ -83,3 +83,50 @@ def assert_srgb8(got, srgb_ref, margin: float = 0.2):
     assert int(d.max()) <= 1
     assert np.all(d[clear] == 0), int(np.count_nonzero(d[clear]))
     return float(np.mean(clear))
+
+
+def _oracle_band(args):
+    """Worker: the oracle's XYZ of one band of a frame, n-sample and latent
+    for each codec (runs in a spawned process)."""
+    sf, codecs = args
+    from oracle import cmf, shade
+    T = cmf.cmf_weights(*sf.grid)
+    out = {"spectral": shade.shade_spectral(sf, want_spectra=False)[1]}
+    for k, (E, D) in codecs.items():
+        z = shade.shade_latent(sf, np.asarray(E, dtype=np.float64))
+        out[k] = shade.decode_xyz(z, np.asarray(D, dtype=np.float64), T)
+    return out
+
+
+def oracle_xyz_whole_frame(f: hi.Frame, codecs: dict, band_rows: int = 32, workers: int = 0) -> dict:
+    """The FP64 oracle's XYZ of every pixel of a frame: the n-sample render
+    ("spectral") and the latent render of each codec (key k, value (E, D)),
+    computed band by band of `band_rows` rows in a pool of spawned processes
+    with one BLAS thread each (the host memory per band stays bounded)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+    step = band_rows * f.width
+    bands = [np.arange(p0, min(p0 + step, f.pixels)) for p0 in range(0, f.pixels, step)]
+    workers = workers or max(1, min(16, os.cpu_count() or 1, len(bands)))
+    saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    out = {"spectral": np.empty((f.pixels, 3))}
+    for k in codecs:
+        out[k] = np.empty((f.pixels, 3))
+    # the workers start on the first submission and read the thread setting
+    # from the environment then; this process's BLAS is already set up
+    for v in saved:
+        os.environ[v] = "1"
+    try:
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            jobs = ex.map(_oracle_band, [(subset_frame(f, b), codecs) for b in bands])
+            for idx, res in zip(bands, jobs):
+                for key, xyz in res.items():
+                    out[key][idx] = xyz
+    finally:
+        for v, old in saved.items():
+            if old is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = old
+    return out

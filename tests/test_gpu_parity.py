@@ -737,3 +737,32 @@ def test_autotune_picks_a_config_without_changing_results(env):
     hsc.hsc_sync(tctx)
     assert hsc.hsc_tune_report(tctx) == rep
     tctx.close()
+
+
+def test_dynamic_queue_launches_on_two_streams(env):
+    # the dynamic tile queue (waves = -1) keeps one counter per stream, so
+    # fused launches of one context on two streams may run at the same time
+    # without taking each other's tiles: both images equal a launch alone
+    hsc, ctx, dev = env
+    import torch
+    f = hi.make_frame(34, 1280, 720, hi.GRID_81, n_smooth=40, n_saw=8, lights=64, secondary=True)
+    E, D = _codec(6, 81)
+    df = upload(hsc, ctx, f, dev)
+    zm, zl = encode_all(hsc, ctx, df, E)
+    ref = torch.empty(f.pixels, 6, device=dev)
+    hsc.hsc_force_launch_config(ctx, 2, 128, -1, 1)
+    hsc.hsc_shade_latent(ctx, df.g1, df.g2, zm, df.lights, zl, hsc.HSC_FUSED, ref)
+    hsc.hsc_sync(ctx)
+    streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+    outs = []
+    for rep in range(3):
+        for s in streams:
+            o = torch.full((f.pixels, 6), -1.0, device=dev)
+            s.wait_stream(torch.cuda.current_stream(dev))
+            hsc.hsc_shade_latent(ctx, df.g1, df.g2, zm, df.lights, zl, hsc.HSC_FUSED, o, stream=s)
+            outs.append(o)
+    torch.cuda.synchronize(dev)
+    hsc.hsc_force_launch_config(ctx, 0)
+    hsc.hsc_sync(ctx)
+    for o in outs:
+        assert torch.equal(o, ref)

@@ -85,3 +85,18 @@ def test_limits_and_errors(env):
     with pytest.raises(hsc.HscError) as ei:
         hsc.hsc_sync(ctx)
     assert ei.value.status == hsc.HSC_ERR_DEVICE_CHECK
+
+
+def test_spherical_room_inward_sphere(env):
+    # the closed spherical room (a sphere with a negative radius, normals
+    # inward) whose mean radiance the oracle pins to a closed form: the
+    # kernel traces the same paths and gives the oracle's pixels
+    hsc, ctx, dev = env
+    W, H, spp, depth = 48, 40, 6, 8
+    sc = hi.sphere_enclosure_scene(W, H, z0=0.2, rho=0.7, grid_spec=hi.GRID_31)
+    T = cmf.cmf_weights(*sc.grid)
+    paths = pt.trace(sc, W, H, spp, depth, seed=77)
+    xs_ref = pt.render_spectral(paths, sc, T)
+    xs, ch = _gpu(hsc, ctx, dev, sc, W, H, spp, depth, 77, sc.refl, sc.emit, T)
+    assert metrics.rel_xyz_error(xs, xs_ref) <= TOL
+    assert xs_ref[:, 1].min() > 0.0     # every pixel gathers light from the emitter

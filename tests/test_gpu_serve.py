@@ -1,5 +1,7 @@
 """Continuous-batching server on the GPU: every request's result is the same
-bits as rendering it alone, whatever it was batched with."""
+bits as rendering it alone, whatever it was batched with; requests that
+arrive while others are on the GPU share launches, and several launches are
+in flight at once."""
 import numpy as np
 import pytest
 
@@ -22,6 +24,25 @@ def env():
     ctx.close()
 
 
+@pytest.fixture(scope="module")
+def big_scenes(env):
+    hsc, serve, ctx, dev, _ = env
+    return serve.ResidentScenes(hsc, ctx, dev, scenes=2, sizes=BIG_SIZES, n_mat=64, pool=128)
+
+
+BIG_SIZES = ((1024, 1024), (1536, 1024))
+
+
+def _solo_latent(hsc, ctx, dev, scenes, r):
+    import torch
+    g1, lights, zm, zl, M = scenes.frame_inputs(r)
+    lat = torch.empty(r.width * r.height, r.k, device=dev)
+    xyz = torch.empty(r.width * r.height, 3, device=dev)
+    hsc.hsc_shade_latent(ctx, g1, None, zm, lights, zl, hsc.HSC_FUSED, lat, xyz_out=xyz, M_xyz=M)
+    hsc.hsc_sync(ctx)
+    return xyz
+
+
 def _stream(n=60):
     return hi.request_stream(seed=11, rate_hz=3000.0, duration_s=1.0, sizes=SIZES, min_lights=4, max_lights=40,
                              scenes=2)[:n]
@@ -35,12 +56,30 @@ def test_latent_serving_matches_requests_alone(env):
     s = stats.summary()
     assert s["requests"] == len(reqs) and s["launches"] >= 1
     for r in reqs:
-        g1, lights, zm, zl, M = scenes.frame_inputs(r)
-        lat = torch.empty(r.width * r.height, r.k, device=dev)
-        xyz = torch.empty(r.width * r.height, 3, device=dev)
-        hsc.hsc_shade_latent(ctx, g1, None, zm, lights, zl, hsc.HSC_FUSED, lat, xyz_out=xyz, M_xyz=M)
-        hsc.hsc_sync(ctx)
-        assert torch.equal(backend.outputs[r.rid], xyz), r
+        assert torch.equal(backend.outputs[r.rid], _solo_latent(hsc, ctx, dev, scenes, r)), r
+
+
+def test_latent_burst_shares_launches_that_overlap(env, big_scenes):
+    # 32 requests arrive together (1-1.5 Mpx, 96-128 lights, every k and n):
+    # the scheduler admits them 8 to a launch, and each launch (~1 ms of GPU
+    # work) is still running when the host submits the next, so launches
+    # share requests and are in flight together; every result is still the
+    # bits of rendering the request alone
+    hsc, serve, ctx, dev, _ = env
+    import torch
+    rng = np.random.default_rng(5)
+    reqs = []
+    for i in range(32):
+        w, h = BIG_SIZES[i % 2]
+        reqs.append(hi.Request(i, 0.0, w, h, (6, 9)[(i // 2) % 2], (31, 81)[(i // 4) % 2],
+                               int(rng.integers(96, 129)), int(rng.integers(0, 2)), i))
+    stats, backend = serve.serve(hsc, ctx, big_scenes, reqs, mode="latent", keep_outputs=True, max_batch=8)
+    s = stats.summary()
+    assert s["requests"] == len(reqs)
+    assert s["max_batch"] == 8 and s["launches"] == 4 and s["batch_hist"] == {"8": 4}, s
+    assert s["max_inflight_launches"] >= 2, s
+    for r in reqs:
+        assert torch.equal(backend.outputs[r.rid], _solo_latent(hsc, ctx, dev, big_scenes, r)), r
 
 
 def test_spectral_serving_matches_requests_alone(env):

@@ -119,3 +119,53 @@ def test_shared_float32_constants():
     assert bits(pt.HALF_PI) == 0x3FC90FDB and bits(pt.T_MIN) == 0x38D1B717 and bits(pt.OFFSET) == 0x3A83126F
     assert [bits(v) for v in pt._S] == [0x3E2AAAAB, 0x3C088889, 0x39500D01, 0x3638EF1D, 0x32D7322B]
     assert [bits(v) for v in pt._C] == [0x3F000000, 0x3D2AAAAB, 0x3AB60B61, 0x37D00D01, 0x3493F27E, 0x310F76C7]
+
+
+def _enclosure_expectation(rho, f, depth, E=1.0):
+    """Mean and variance of one path's value in the spherical room: every
+    reflection happens on the sphere, and from any point on a sphere a
+    cosine-weighted direction meets the sphere at a uniformly distributed
+    point (the form factor between two area elements of a sphere's inside is
+    dA / (4 pi R^2) whatever their positions).  The emitter square hides
+    exactly the cap above z0 from the rest of the sphere (a chord from below
+    the plane to the cap crosses the plane inside the sphere), so every
+    bounce ends on the emitter with probability f = cap area / sphere area,
+    independently of where it starts.  A path that makes j reflections and
+    then meets the emitter carries E rho^j, with probability (1 - f)^(j-1) f
+    for j = 1 .. depth (the camera sees only the sphere below z0)."""
+    j = np.arange(1, depth + 1)
+    p = (1.0 - f) ** (j - 1) * f
+    mean = float(np.sum(p * E * rho ** j))
+    second = float(np.sum(p * (E * rho ** j) ** 2))
+    return mean, second - mean * mean
+
+
+def test_spherical_room_matches_the_closed_form():
+    # the estimator's expectation pinned by geometry alone (not by the traced
+    # float32 paths): mean over 128 x 128 pixels x 24 samples of the room's
+    # radiance against E sum_j rho^j (1 - f)^(j-1) f, with f = (1 - z0) / 2,
+    # within five standard errors plus 0.4% for the 1e-3 offset of each new
+    # ray off the sphere (the uniform-hit property holds on the sphere itself)
+    W = H = 128
+    spp = 24
+    for z0, rho, depth in ((0.6, 0.8, 1), (0.6, 0.8, 3), (0.2, 0.7, 8), (0.6, 1.0, 8)):
+        sc = hi.sphere_enclosure_scene(W, H, z0=z0, rho=rho)
+        paths = pt.trace(sc, W, H, spp, depth, seed=21 + depth)
+        assert np.all(paths.end != 0)                   # the camera never sees the emitter
+        vals = pt.path_products(paths, sc.refl, sc.emit)[:, 0]
+        mean, var = _enclosure_expectation(rho, (1.0 - z0) / 2.0, depth)
+        se = np.sqrt(var / vals.size)
+        assert abs(vals.mean() - mean) <= 5 * se + 4e-3 * mean, (z0, rho, depth, vals.mean(), mean)
+        # the first bounce ends on the emitter with probability f
+        f = (1.0 - z0) / 2.0
+        assert abs(np.mean(paths.end == 1) - f) <= 5 * np.sqrt(f * (1 - f) / paths.end.size) + 4e-3 * f
+
+
+def test_spherical_room_rays_stay_inside():
+    # with inward normals every bounce stays in the room: after any number of
+    # reflections a path either met the emitter or is still going at the
+    # depth bound; no path leaves the scene
+    sc = hi.sphere_enclosure_scene(32, 32, z0=-0.2, rho=0.5)
+    paths = pt.trace(sc, 32, 32, 8, 12, seed=4)
+    lost = (paths.end < 0) & (paths.mats[:, -1] < 0)
+    assert not lost.any()

@@ -48,6 +48,10 @@ class FakeBackend:
     def done(self, handle):
         return handle if self.t_ms >= handle else None
 
+    def sleep(self, seconds):
+        self.slept_ms = getattr(self, "slept_ms", 0.0) + 1e3 * seconds
+        self.t_ms += 1e3 * seconds
+
 
 def _requests(n=300, rate=400.0):
     reqs = hi.request_stream(seed=3, rate_hz=rate, duration_s=10.0)[:n]
@@ -87,3 +91,39 @@ def test_summary_statistics():
     st = Scheduler(FakeBackend(), 10**12).run(reqs)
     s = st.summary()
     assert s["requests"] == 50 and s["p50_ms"] <= s["p99_ms"] <= s["max_ms"]
+
+
+def test_burst_is_batched_and_launches_overlap():
+    # every request arrives at once: the first passes take max_batch requests
+    # each, and while the (simulated) GPU works through one launch the next
+    # ones are submitted, so several launches are in flight together
+    reqs = [hi.Request(i, 0.0, 512, 512, 6, 31, 32, 0, i) for i in range(40)]
+    fb = FakeBackend(px_per_ms=2e5)
+    st = Scheduler(fb, 10**12, max_inflight=4, max_batch=8).run(reqs)
+    s = st.summary()
+    assert s["max_batch"] == 8 and s["launches"] == 5
+    assert s["batch_hist"] == {"8": 5}
+    assert s["max_inflight_launches"] == 4
+    assert all(len(g) == 8 for g in fb.launched)
+
+
+def test_idle_passes_sleep_until_the_next_arrival():
+    # sparse arrivals: passes with nothing to do sleep (at most the time left
+    # to the next arrival), so the loop does not poll continuously, and the
+    # latencies stay those of the polling loop within a sleep
+    reqs = _requests(n=60, rate=50.0)
+    busy = Scheduler(FakeBackend(), 10**12).run(reqs)
+    fb = FakeBackend()
+    lazy = Scheduler(fb, 10**12).run(reqs, idle_sleep_s=1e-3)
+    assert lazy.idle_sleeps > 0 and busy.idle_sleeps == 0
+    assert fb.slept_ms > 0
+    for a, b in zip(busy.latencies_ms, lazy.latencies_ms):
+        assert b <= a + 1.0 + 2 * fb.tick
+
+
+def test_host_usage_counters():
+    u0 = _serve.host_usage()
+    sum(i * i for i in range(200000))
+    d = _serve.usage_delta(u0, _serve.host_usage())
+    assert d["cpu_s"] >= 0.0 and d["nivcsw"] >= 0.0 and d["nvcsw"] >= 0.0
+    assert set(u0) >= {"cpu_s", "nvcsw", "nivcsw"}

@@ -59,6 +59,8 @@ def parse():
                     help="load tuned launch configurations from this file if it exists, save them there after the run")
     ap.add_argument("--serve-seconds", type=float, default=8.0,
                     help="length of the Poisson request stream served (0 = skip); the first quarter is warm-up")
+    ap.add_argument("--serve-idle-us", type=float, default=-1.0,
+                    help="host sleep of an idle scheduler pass in microseconds (default: the server's own)")
     ap.add_argument("--rows-only", default="",
                     help="comma list of secondary row groups to run: core, batch, chains, upsample, pathtrace, "
                          "sweep, serve (default: all)")
@@ -832,10 +834,12 @@ def serve_rows(args, hsc, ctx, dev):
     warm = args.serve_seconds / 4.0
     arrivals = [r.arrival_s for r in sorted(reqs, key=lambda r: r.arrival_s)]
     out = {}
+    idle = serve.IDLE_SLEEP_S if args.serve_idle_us < 0 else args.serve_idle_us * 1e-6
     for mode in ("latent", "spectral"):
-        stats, _ = serve.serve(hsc, ctx, scenes, reqs, mode=mode)
+        stats, _ = serve.serve(hsc, ctx, scenes, reqs, mode=mode, idle_sleep_s=idle)
         sm = stats.summary(warmup_s=warm, arrivals=arrivals)
         sm["offered_per_s"] = len(reqs) / args.serve_seconds
+        sm["idle_sleep_us"] = idle * 1e6
         out[f"serve_{mode}"] = sm
     lat, spe = out["serve_latent"], out["serve_spectral"]
     if lat.get("p50_ms") and spe.get("p50_ms"):

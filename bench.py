@@ -845,6 +845,16 @@ def serve_rows(args, hsc, ctx, dev):
     if lat.get("p50_ms") and spe.get("p50_ms"):
         out["serve_latency_ratio_spectral_over_latent"] = {"p50": spe["p50_ms"] / lat["p50_ms"],
                                                            "p99": spe["p99_ms"] / lat["p99_ms"]}
+    # the same kind of stream at 20x the rate for one second: the latent path
+    # keeps up by batching requests into shared launches, the n-sample path
+    # falls behind and its queue (and latency) grows
+    rate_hi = 4000.0
+    reqs_hi = hi.request_stream(seed=hi.MASTER_SEED + 7, rate_hz=rate_hi, duration_s=1.0)
+    for mode in ("latent", "spectral"):
+        stats, _ = serve.serve(hsc, ctx, scenes, reqs_hi, mode=mode, idle_sleep_s=idle, reserve_per_size=64)
+        sm = stats.summary()
+        sm["offered_per_s"] = float(len(reqs_hi))
+        out[f"serve_{mode}_{int(rate_hi)}_per_s"] = sm
     del scenes
     return out
 

@@ -28,7 +28,8 @@
 // product is exact in FP32 and the dropped ones are below 2^-24 relative, so
 // the result has FP32 accuracy.
 // Every mbarrier wait is bounded; on expiry the kernel sets an error bit,
-// drains its bulk copies, frees its TMEM and returns.
+// waits (bounded) for the MMA it issued and for its bulk copies, frees its
+// TMEM and returns.
 #include "common.cuh"
 #include "tcgen05.cuh"
 
@@ -150,8 +151,8 @@ __global__ void __launch_bounds__(kTcThreads) decode_spectra_tc_kernel(const TcA
   unsigned char* sA = base;                                           // KB x [128 x 16] bf16 (4096 B each)
   unsigned char* sB = base + KB * 4096;                               // KB x [NPAD x 16] bf16
   float* sOut = reinterpret_cast<float*>(base + KB * (4096 + NPAD * 32));  // [128 x n] staging tile
-  uint64_t* sBar = reinterpret_cast<uint64_t*>(sOut + kTcRows * a.n + 4);
-  uint32_t* sTmem = reinterpret_cast<uint32_t*>(sBar + 1);
+  uint64_t* sBar = reinterpret_cast<uint64_t*>(sOut + kTcRows * a.n + 4);  // [0] MMA done, [1] drain
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(sBar + 2);
   int* sOk = reinterpret_cast<int*>(sTmem + 1);
 
   const int t = threadIdx.x;
@@ -167,6 +168,7 @@ __global__ void __launch_bounds__(kTcThreads) decode_spectra_tc_kernel(const TcA
   }
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(sBar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(sBar + 1)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *sOk = 1;
   }
@@ -283,6 +285,9 @@ __global__ void __launch_bounds__(kTcThreads) decode_spectra_tc_kernel(const TcA
     }
     pack_a_row<KB>(a, raw, wA);
   }
+  // after an expired wait the MMA may still be running: drain it (bounded)
+  // before TMEM is freed; every warp's bulk stores finish before the exit
+  if (t == 0 && !*sOk) drain_mma(smem_u32(sBar + 1));
   if ((t & 31) == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();

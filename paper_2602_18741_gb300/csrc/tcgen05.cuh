@@ -53,6 +53,18 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
   return false;
 }
 
+// Expiry path of the kernels whose thread 0 issues every tcgen05.mma: one
+// more commit, to `drain_bar` (an mbarrier initialised for one arrival and
+// not used otherwise), makes that barrier track the completion of every
+// asynchronous tcgen05 operation the thread issued before; thread 0 then
+// waits for it, bounded, so that TMEM is freed only after the MMAs that may
+// still write it have finished.  False if this wait expires as well.
+__device__ __forceinline__ bool drain_mma(uint32_t drain_bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(drain_bar)
+               : "memory");
+  return mbar_wait(drain_bar, 0);
+}
+
 #define TC_LD16(taddr, v)                                                                                      \
   asm volatile(                                                                                                \
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];" \

@@ -152,8 +152,8 @@ __global__ void __launch_bounds__(kUpThreads, 1) upsample_tc_kernel(const UpArgs
   float* sB1 = reinterpret_cast<float*>(base + kOffBias);
   float* sB2 = sB1 + kHidden;
   float* sB3 = sB2 + kHidden;
-  uint64_t* sBar = reinterpret_cast<uint64_t*>(base + kOffBar);  // [2]
-  uint32_t* sTmem = reinterpret_cast<uint32_t*>(sBar + 2);
+  uint64_t* sBar = reinterpret_cast<uint64_t*>(base + kOffBar);  // [0], [1] the two slots, [2] drain
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(sBar + 3);
   int* sOk = reinterpret_cast<int*>(sTmem + 1);
 
   const int t = threadIdx.x;
@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(kUpThreads, 1) upsample_tc_kernel(const UpArgs
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(sBar)) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(sBar + 1)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(sBar + 2)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *sOk = 1;
   }
@@ -289,6 +290,9 @@ __global__ void __launch_bounds__(kUpThreads, 1) upsample_tc_kernel(const UpArgs
     out(1, pair);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   }
+  // after an expired wait the other slot's MMAs may still be running: drain
+  // them (bounded) before TMEM is freed
+  if (t == 0 && !*sOk) drain_mma(smem_u32(sBar + 2));
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {

@@ -35,11 +35,14 @@ import hsc_inputs as hi
 
 # --------------------------------------------------------------------------- scheduler
 
-# Host sleep of a scheduler pass that found nothing to do (seconds).  Polling
-# without a pause keeps one host core busy all the time; under a CPU quota on
-# the container that can use the quota up and get the whole process held for
-# the rest of the quota period.
-IDLE_SLEEP_S = 100e-6
+# Longest host sleep of a scheduler pass that finds the GPU idle and no
+# request waiting (seconds), and how long before the next arrival it wakes.
+# Polling without a pause keeps one host core busy all the time, and a thread
+# that never sleeps is the one the kernel preempts when the host is busy;
+# while launches are in flight the loop still polls, so completions are seen
+# at once.
+IDLE_SLEEP_S = 1e-3
+WAKE_MARGIN_S = 100e-6
 
 @dataclass
 class Inflight:
@@ -106,9 +109,10 @@ class Scheduler:
 
     def run(self, requests: Sequence[hi.Request], idle_sleep_s: float = 0.0) -> ServeStats:
         """Serve ``requests`` (arrival times in seconds from the start).  A
-        pass of the loop that admits, retires and launches nothing sleeps for
-        ``idle_sleep_s`` (capped at the time left to the next arrival) instead
-        of polling again at once; 0 polls continuously."""
+        pass of the loop that finds the GPU idle and no request waiting sleeps
+        for up to ``idle_sleep_s``, waking WAKE_MARGIN_S before the next
+        arrival; with launches in flight it polls continuously.  0 never
+        sleeps."""
         reqs = sorted(requests, key=lambda r: r.arrival_s)
         for r in reqs:
             if self.b.footprint(r) > self.budget:
@@ -165,10 +169,14 @@ class Scheduler:
                     st.max_inflight_launches = max(st.max_inflight_launches, len(inflight))
                     st.max_inflight_bytes = max(st.max_inflight_bytes, used)
                     continue
-            if idle_sleep_s > 0 and not retired:
+            if idle_sleep_s > 0 and not retired and not inflight and not queue:
+                # nothing on the GPU and nothing waiting: sleep, but wake a
+                # little before the next arrival (sleeps overshoot by tens of
+                # microseconds); with launches in flight the loop keeps polling
+                # so that completions are seen at once
                 wait = idle_sleep_s
-                if nxt < len(reqs) and not queue:
-                    wait = min(wait, max(reqs[nxt].arrival_s - now, 0.0))
+                if nxt < len(reqs):
+                    wait = min(wait, reqs[nxt].arrival_s - now - WAKE_MARGIN_S)
                 if wait > 0:
                     st.idle_sleeps += 1
                     getattr(self.b, "sleep", time.sleep)(wait)
@@ -407,7 +415,7 @@ class GpuBackend:
 
 
 def serve(hsc, ctx, scenes: ResidentScenes, requests, mode="latent", budget_bytes=40 * 10**9, max_batch=64,
-          keep_outputs=False, max_inflight=4, idle_sleep_s=IDLE_SLEEP_S):
+          keep_outputs=False, max_inflight=4, idle_sleep_s=IDLE_SLEEP_S, reserve_per_size=16):
     """Serve `requests` in real time.  Launch-configuration tuning is switched
     off while serving: tuning a new shape class synchronises the stream, which
     would stall the requests behind it (a server tunes ahead of time and
@@ -415,7 +423,9 @@ def serve(hsc, ctx, scenes: ResidentScenes, requests, mode="latent", budget_byte
     filled before the first arrival (no device allocation inside the loop),
     and the garbage collector is paused for the loop.  A pass with nothing to
     do sleeps ``idle_sleep_s`` rather than polling again at once (see
-    IDLE_SLEEP_S)."""
+    IDLE_SLEEP_S).  ``reserve_per_size`` output buffers of every request size
+    are allocated before the first arrival; a stream that keeps more requests
+    of one size in flight needs more."""
     backend = GpuBackend(hsc, ctx, scenes, mode=mode, keep_outputs=keep_outputs)
     sched = Scheduler(backend, budget_bytes, max_inflight=max_inflight, max_batch=max_batch)
     was = bool(ctx.autotune) if hasattr(ctx, "autotune") else False
@@ -423,7 +433,7 @@ def serve(hsc, ctx, scenes: ResidentScenes, requests, mode="latent", budget_byte
     gc_was = gc.isenabled()
     gc.disable()                   # no collector pause inside the real-time loop
     try:
-        backend.reserve(requests)
+        backend.reserve(requests, per_size=reserve_per_size)
         backend.parts.clear()
         backend.start()
         u0 = host_usage()

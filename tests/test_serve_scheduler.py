@@ -117,8 +117,10 @@ def test_idle_passes_sleep_until_the_next_arrival():
     lazy = Scheduler(fb, 10**12).run(reqs, idle_sleep_s=1e-3)
     assert lazy.idle_sleeps > 0 and busy.idle_sleeps == 0
     assert fb.slept_ms > 0
+    # the loop wakes before each arrival and polls while work is in flight,
+    # so every request completes when it would with continuous polling
     for a, b in zip(busy.latencies_ms, lazy.latencies_ms):
-        assert b <= a + 1.0 + 2 * fb.tick
+        assert abs(b - a) <= 2 * fb.tick
 
 
 def test_host_usage_counters():

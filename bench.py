@@ -62,8 +62,8 @@ def parse():
     ap.add_argument("--serve-idle-us", type=float, default=-1.0,
                     help="host sleep of an idle scheduler pass in microseconds (default: the server's own)")
     ap.add_argument("--rows-only", default="",
-                    help="comma list of secondary row groups to run: core, batch, chains, upsample, pathtrace, "
-                         "sweep, serve (default: all)")
+                    help="comma list of secondary row groups to run: core, precision, small, batch, chains, "
+                         "upsample, pathtrace, sweep, serve (default: all)")
     ap.add_argument("--sweep-epochs", type=int, default=150,
                     help="epoch cap of the 700-variant codec sweep (0 = skip the sweep row)")
     return ap.parse_args()
@@ -501,6 +501,21 @@ def secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T,
     rows["latent_fused_k9_xyz"] = {"ms": f9, "evals_per_s": evals / (f9 * 1e-3), "ops_per_eval": 22}
     rows["speedup_latent_fused_k9_vs_spectral"] = spec_ms / f9
 
+    # k = 9 as three RGB passes and their reassembly (Fig. 2b)
+    lat9p = torch.empty(P, 9, device=dev)
+    xyz9p = torch.empty(P, 3, device=dev)
+    hsc.hsc_reserve(ctx, hsc.hsc_shade_latent_scratch_bytes(P, 9, hsc.HSC_PASSES, hsc.HSC_F32))
+
+    def passes9():
+        hsc.hsc_shade_latent(ctx, g1, g2, zm9, lights, zl9, hsc.HSC_PASSES, lat9p, xyz_out=xyz9p, M_xyz=M9)
+
+    ms, _ = timed(passes9, K, W)
+    p9 = statistics.mean(ms)
+    rows["latent_passes_k9_xyz"] = {"ms": p9, "evals_per_s": evals / (p9 * 1e-3),
+                                    "bit_identical_to_fused": bool(torch.equal(lat9p, lat9))}
+    rows["speedup_latent_passes_k9_vs_spectral"] = spec_ms / p9
+    del lat9p, xyz9p
+
     # decode of the k = 9 FP32 latent to spectra (tensor cores, three-part split)
     spec9 = torch.empty(P, 81, device=dev)
 
@@ -593,9 +608,86 @@ def secondary_rows(args, hsc, ctx, f, dev, stream, g1, g2, lights, mats, spd, T,
     return rows
 
 
+def precision_rows(args, hsc, ctx, dev, timed):
+    """The 3840x2160 frame (n = 81, 64 lights, primary + secondary, k = 6
+    and 9) shaded with the codes stored in FP32, BF16 and FP16 (fused launch
+    with the XYZ epilogue), and with BF16 codes into an FP8 E4M3 latent image
+    with per-channel scales (fused launch writing FP32 to scratch with the
+    channel maxima, then the quantisation pass), followed by the XYZ decode of
+    the FP8 image.  Accuracy beside each row: relative XYZ error and Delta E
+    2000 (mean, p95) against the FP32 render of the same frame, which matches
+    the FP64 oracle to ~1e-6 (the oracle itself is compared in the precision
+    tests)."""
+    import torch
+    f = hi.frame_config3()
+    P = f.pixels
+    evals = f.evals
+
+    def t(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    g1 = hsc.GBuffer(t(f.g1.normal), t(f.g1.pos), t(f.g1.mat))
+    g2 = hsc.GBuffer(t(f.g2.normal), t(f.g2.pos), t(f.g2.mat))
+    lights = hsc.Lights(t(f.light_pos), t(f.light_intensity))
+    mats, spd = t(f.mat_spectra), t(f.light_spd)
+    T = torch.empty(3, 81, device=dev)
+    hsc.hsc_cmf_weights(ctx, 81, f.grid[0], f.grid[1], T)
+    out = {"frame": "3840x2160, n = 81, 64 lights, primary + secondary", "evals": evals}
+    st = torch.zeros(8, device=dev, dtype=torch.float64)
+    for k in (6, 9):
+        E, D = hi.load_codec(k, 81)
+        Ed, Dd = t(E), t(D)
+        M = _M(hsc, ctx, T, Dd)
+        hsc.hsc_reserve(ctx, hsc.hsc_shade_latent_scratch_bytes(P, k, hsc.HSC_FUSED, hsc.HSC_FP8_E4M3))
+        xyz_ref = torch.empty(P, 3, device=dev)
+        xyz = torch.empty(P, 3, device=dev)
+        lat = torch.empty(P, k, device=dev)
+        codes = torch.empty(P, k, device=dev, dtype=torch.uint8)
+        scales = torch.empty(k, device=dev)
+        rows_k = {}
+        for name, dt in (("f32_codes", torch.float32), ("bf16_codes", torch.bfloat16), ("f16_codes", torch.float16),
+                         ("bf16_codes_fp8_latent", torch.bfloat16)):
+            zm = torch.empty(mats.shape[0], k, device=dev, dtype=dt)
+            zl = torch.empty(spd.shape[0], k, device=dev, dtype=dt)
+            hsc.hsc_encode(ctx, Ed, mats, zm)
+            hsc.hsc_encode(ctx, Ed, spd, zl)
+            if name.endswith("fp8_latent"):
+                def shade():
+                    hsc.hsc_shade_latent(ctx, g1, g2, zm, lights, zl, hsc.HSC_FUSED, codes, latent_scales=scales)
+
+                def dec():
+                    hsc.hsc_decode_xyz(ctx, codes, M, xyz, scales=scales)
+            else:
+                def shade():
+                    hsc.hsc_shade_latent(ctx, g1, g2, zm, lights, zl, hsc.HSC_FUSED, lat,
+                                         xyz_out=(xyz_ref if name == "f32_codes" else xyz), M_xyz=M)
+                dec = None
+            ms, _ = timed(shade, args.steps, args.warmup)
+            m_ = statistics.mean(ms)
+            row = {"ms": m_, "evals_per_s": evals / (m_ * 1e-3), "frac_alu": evals * (13 + k) / (m_ * 1e-3) /
+                   (torch.cuda.get_device_properties(dev).multi_processor_count * 128 * _peak_sm_mhz() * 1e6)}
+            if dec is not None:
+                ms, _ = timed(dec, args.steps, args.warmup)
+                row["xyz_decode_ms"] = statistics.mean(ms)
+                row["ms_with_decode"] = m_ + row["xyz_decode_ms"]
+            if name != "f32_codes":
+                hsc.hsc_delta_e(ctx, xyz, xyz_ref, T, st)
+                hsc.hsc_sync(ctx)
+                s_ = st.cpu().numpy()
+                ref = xyz_ref.abs().amax(dim=1)
+                den = torch.clamp(ref, min=1e-3 * float(ref.max()))
+                row["rel_xyz_vs_f32"] = float(((xyz - xyz_ref).abs().amax(dim=1) / den).max())
+                row["de2000_vs_f32_mean"] = float(s_[0])
+                row["de2000_vs_f32_p95"] = float(s_[1])
+            rows_k[name] = row
+        out[f"k{k}"] = rows_k
+        del xyz_ref, xyz, lat, codes
+    return {"precision_3840x2160": out}
+
+
 def wanted_rows(args):
     """The secondary row groups to run (all unless --rows-only names some)."""
-    groups = ("core", "small", "batch", "chains", "upsample", "pathtrace", "sweep", "serve")
+    groups = ("core", "precision", "small", "batch", "chains", "upsample", "pathtrace", "sweep", "serve")
     if not args.rows_only:
         return set(groups)
     want = {g.strip() for g in args.rows_only.split(",") if g.strip()}
@@ -608,6 +700,8 @@ def wanted_rows(args):
 def group_rows(args, hsc, ctx, dev, timed, before_serve=None):
     want = wanted_rows(args)
     rows = {}
+    if "precision" in want:
+        rows.update(precision_rows(args, hsc, ctx, dev, timed))
     if "small" in want:
         rows.update(small_frame_rows(args, hsc, ctx, dev))
     if "batch" in want:

@@ -62,6 +62,29 @@ __device__ __forceinline__ void stage_light_codes(const ShadeArgs& a, float4* s_
   }
 }
 
+// Material code tables of at most kMatStage values (n_mat x KC) are staged
+// once per CTA in shared memory as FP32 (the same values the global path
+// converts per row), so the epilogue's material reads are shared-memory
+// loads; larger tables are read from global memory.
+constexpr int kMatStage = 4096;
+
+template <int KC>
+__host__ __device__ __forceinline__ bool mat_staged(int n_mat) { return (int64_t)n_mat * KC <= kMatStage; }
+
+template <int KC, int BLOCK>
+__device__ __forceinline__ void stage_material_codes(const ShadeArgs& a, float* s_mat) {
+  for (int i = threadIdx.x; i < a.n_mat * KC; i += BLOCK) {
+    const int row = i / KC, c = i - row * KC;
+    s_mat[i] = load_code(a.mat_codes, a.code_dt, (int64_t)row * a.k + a.c0 + c);
+  }
+}
+
+// Resident CTAs per SM asked of the compiler: the 128-thread scalar form with
+// at most two pixels per thread and six channels runs best at 7 CTAs per SM
+// (72 registers); the others keep the compiler's choice.
+template <int KC, int PPT, int BLOCK, int VEC>
+constexpr int latent_min_blocks() { return (KC <= 6 && PPT <= 2 && BLOCK == 128 && VEC == 1) ? 7 : 1; }
+
 // The KC code channels c0 .. c0+KC-1 of row `row` of a code table in its
 // storage format; one format test per row instead of per channel.
 template <int KC>
@@ -94,7 +117,7 @@ __device__ __forceinline__ void load_code_row(const ShadeArgs& a, int row, float
 // tiles are staged here.  Must be called by every thread of the CTA.
 template <int KC, int PPT, bool SEC, int BLOCK, int VEC, bool RGB = false>
 __device__ __forceinline__ void shade_tile(const ShadeArgs& a, int64_t tile, float4* s_light, bool staged,
-                                           const float* s_M) {
+                                           const float* s_M, const float* s_mat = nullptr) {
   constexpr int F4 = LightStage<KC, VEC>::F4;
   constexpr int NPT = PPT * (SEC ? 2 : 1);
   static_assert(VEC == 1 || NPT % 2 == 0, "paired points need an even point count");
@@ -103,12 +126,16 @@ __device__ __forceinline__ void shade_tile(const ShadeArgs& a, int64_t tile, flo
   auto stage = [&](int l0, int nl) { stage_light_codes<KC, VEC, BLOCK>(a, s_light, l0, nl); };
   {
     float px[NPT], py[NPT], pz[NPT], nx[NPT], ny[NPT], nz[NPT];
+    float hb[PPT];          // bounce term of each pixel (SEC)
+    int mi1[PPT], mi2[PPT];  // material indices
     int64_t pix[PPT];
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
       const int64_t p = tile * (BLOCK * PPT) + (int64_t)j * BLOCK + tid;
       pix[j] = p;
       const int64_t pc = p < a.P ? p : a.P - 1;
+      mi1[j] = __ldg(a.m1 + pc);
+      mi2[j] = SEC ? __ldg(a.m2 + pc) : 0;
       px[j] = __ldg(a.x1 + 3 * pc + 0);
       py[j] = __ldg(a.x1 + 3 * pc + 1);
       pz[j] = __ldg(a.x1 + 3 * pc + 2);
@@ -123,6 +150,16 @@ __device__ __forceinline__ void shade_tile(const ShadeArgs& a, int64_t tile, flo
         ny[PPT + j] = __ldg(a.n2 + 3 * pc + 1);
         nz[PPT + j] = __ldg(a.n2 + 3 * pc + 2);
       }
+    }
+    // the bounce term needs only the G-buffer: computed here, its latency
+    // overlaps the light loop instead of the epilogue
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+      if constexpr (SEC)
+        hb[j] = bounce_term(px[j], py[j], pz[j], nx[j], ny[j], nz[j], px[PPT + j], py[PPT + j], pz[PPT + j],
+                            nx[PPT + j], ny[PPT + j], nz[PPT + j]);
+      else
+        hb[j] = 0.0f;
     }
     float acc[NPT][KC];
 #pragma unroll
@@ -215,21 +252,27 @@ __device__ __forceinline__ void shade_tile(const ShadeArgs& a, int64_t tile, flo
     for (int j = 0; j < PPT; ++j) {
       const int64_t p = pix[j];
       const bool valid = p < a.P;
-      const int64_t pc = valid ? p : a.P - 1;
       // an out-of-range material index (primary or secondary) gives the
       // pixel zero radiance and flags the error word
-      const int m1 = __ldg(a.m1 + pc);
+      const int m1 = mi1[j];
       bool bad = (unsigned)m1 >= (unsigned)a.n_mat;
       float zr1[KC], out[KC];
-      load_code_row<KC>(a, bad ? 0 : m1, zr1);
+      auto code_row = [&](int row, float (&z)[KC]) {
+        if (s_mat) {
+#pragma unroll
+          for (int c = 0; c < KC; ++c) z[c] = s_mat[row * KC + c];
+        } else {
+          load_code_row<KC>(a, row, z);
+        }
+      };
+      code_row(bad ? 0 : m1, zr1);
       if (SEC) {
-        const int m2 = __ldg(a.m2 + pc);
+        const int m2 = mi2[j];
         const bool bad2 = (unsigned)m2 >= (unsigned)a.n_mat;
         bad = bad || bad2;
         float zr2[KC];
-        load_code_row<KC>(a, bad2 ? 0 : m2, zr2);
-        const float h = bounce_term(px[j], py[j], pz[j], nx[j], ny[j], nz[j], px[PPT + j], py[PPT + j],
-                                    pz[PPT + j], nx[PPT + j], ny[PPT + j], nz[PPT + j]);
+        code_row(bad2 ? 0 : m2, zr2);
+        const float h = hb[j];
 #pragma unroll
         for (int c = 0; c < KC; ++c)
           out[c] = __fmul_rn(zr1[c], __fmaf_rn(h, __fmul_rn(zr2[c], acc[PPT + j][c]), acc[j][c]));
@@ -308,11 +351,17 @@ __device__ __forceinline__ void release_queue(unsigned int* queue) {
 // RGB: the epilogue also writes 8-bit sRGB (a separate instantiation, so the
 // kernels without it keep their code).
 template <int KC, int PPT, bool SEC, int BLOCK, int VEC, bool RGB>
-__global__ void __launch_bounds__(BLOCK) shade_codes_kernel(const ShadeArgs a) {
+__global__ void __launch_bounds__(BLOCK, (latent_min_blocks<KC, PPT, BLOCK, VEC>()))
+    shade_codes_kernel(const ShadeArgs a) {
+  // dynamic shared memory: the light tile, then the material table if it fits
   extern __shared__ float4 s_light[];
   __shared__ float s_M[3 * KC];
   const bool staged = a.L <= kLightTile;
+  float* s_mat = mat_staged<KC>(a.n_mat)
+                     ? reinterpret_cast<float*>(s_light + min(a.L, kLightTile) * LightStage<KC, VEC>::F4)
+                     : nullptr;
   if (staged) stage_light_codes<KC, VEC, BLOCK>(a, s_light, 0, a.L);
+  if (s_mat) stage_material_codes<KC, BLOCK>(a, s_mat);
   stage_decode_matrix<KC, BLOCK>(a, s_M);
   __syncthreads();
   if (a.queue) {
@@ -324,12 +373,12 @@ __global__ void __launch_bounds__(BLOCK) shade_codes_kernel(const ShadeArgs a) {
       const int64_t tile = s_next;
       __syncthreads();
       if (tile >= a.tiles) break;
-      shade_tile<KC, PPT, SEC, BLOCK, VEC, RGB>(a, tile, s_light, staged, s_M);
+      shade_tile<KC, PPT, SEC, BLOCK, VEC, RGB>(a, tile, s_light, staged, s_M, s_mat);
     }
     release_queue(a.queue);
   } else {
     for (int64_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x)
-      shade_tile<KC, PPT, SEC, BLOCK, VEC, RGB>(a, tile, s_light, staged, s_M);
+      shade_tile<KC, PPT, SEC, BLOCK, VEC, RGB>(a, tile, s_light, staged, s_M, s_mat);
   }
 }
 
@@ -338,12 +387,20 @@ hsc_status launch_one_rgb(const ShadeArgs& a0, const LaunchCfg& cfg, cudaStream_
   constexpr int F4 = LightStage<KC, VEC>::F4;
   ShadeArgs a = a0;
   a.tiles = (a.P + (int64_t)BLOCK * PPT - 1) / ((int64_t)BLOCK * PPT);
-  const size_t smem = (size_t)min(a.L, kLightTile) * F4 * sizeof(float4);
+  const size_t smem = (size_t)min(a.L, kLightTile) * F4 * sizeof(float4) +
+                      (mat_staged<KC>(a.n_mat) ? (size_t)a.n_mat * KC * sizeof(float) : 0);
   auto kern = shade_codes_kernel<KC, PPT, SEC, BLOCK, VEC, RGB>;
   static int occ = -1;
   if (occ < 0) {
+    // resident CTAs with the largest light tile and material table (which may
+    // pass the 48 KB a launch gets without opting in)
+    const int smem_max = (int)(kLightTile * F4 * sizeof(float4) + kMatStage * sizeof(float));
+    if (smem_max > 48 * 1024 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess)
+      return set_error(HSC_ERR_CUDA, "shared memory attribute of the latent shading kernel");
     int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, BLOCK, kLightTile * F4 * sizeof(float4)) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, BLOCK,
+                                                      kLightTile * F4 * sizeof(float4) + kMatStage * sizeof(float)) !=
+        cudaSuccess)
       o = 1;
     occ = o > 0 ? o : 1;
   }

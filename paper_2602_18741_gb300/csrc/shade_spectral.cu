@@ -383,13 +383,16 @@ __global__ void __launch_bounds__(128, TL <= 12 ? 4 : 2) shade_spectral_lanes_ke
   const float* tw = s_T + grp * VS;
   const float* vrem = SH::INPAD ? vr + SH::ROFF : s_V + SH::ROFF;
   const float* trem = SH::INPAD ? tw + SH::ROFF : s_T + SH::ROFF;
-  const int64_t tiles = (a.P + PX - 1) / PX;
-  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const int64_t pix0 = tile * PX + (int64_t)pg * QP;   // first pixel of this lane group
+  // pixel indices fit 32 bits: the host splits frames whose P x max(n, 3)
+  // would not (each launch then covers a slice of the frame)
+  const int P = (int)a.P;
+  const int tiles = (P + PX - 1) / PX;
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int pix0 = tile * PX + pg * QP;      // first pixel of this lane group
     // this lane's shading point; lanes grp < QP also hold pixel grp's record
     const bool second = SEC && grp >= 4;
-    const int64_t mypix = pix0 + (SEC ? (grp & 3) : grp);
-    const int64_t pc = mypix < a.P ? mypix : a.P - 1;
+    const int mypix = pix0 + (SEC ? (grp & 3) : grp);
+    const int pc = mypix < P ? mypix : P - 1;
     const Pt pt = second ? load_pt(a.x2, a.n2, pc) : load_pt(a.x1, a.n1, pc);
     int m1 = __ldg(a.m1 + pc), m2 = 0;
     bool bad = m1 < 0 || m1 >= a.n_mat;
@@ -405,7 +408,7 @@ __global__ void __launch_bounds__(128, TL <= 12 ? 4 : 2) shade_spectral_lanes_ke
       const float sny = __shfl_down_sync(0xffffffffu, pt.ny, 4, 8), snz = __shfl_down_sync(0xffffffffu, pt.nz, 4, 8);
       if (grp < 4) h = bounce_term(pt.x, pt.y, pt.z, pt.nx, pt.ny, pt.nz, sx, sy, sz, snx, sny, snz);
     }
-    if (bad && grp < QP && mypix < a.P) atomicOr(a.err, HSC_DEVERR_MATERIAL);
+    if (bad && grp < QP && mypix < P) atomicOr(a.err, HSC_DEVERR_MATERIAL);
     float acc[8][TL];
     float accr[RN];                            // this lane's point, the last R samples
 #pragma unroll
@@ -414,13 +417,8 @@ __global__ void __launch_bounds__(128, TL <= 12 ? 4 : 2) shade_spectral_lanes_ke
       for (int i = 0; i < TL; ++i) acc[q][i] = 0.0f;
 #pragma unroll
     for (int r = 0; r < RN; ++r) accr[r] = 0.0f;
-    for (int l0 = 0; l0 < a.L; l0 += kLT) {
-      const int nl = min(kLT, a.L - l0);
-      if (!one_stage) {
-        __syncthreads();
-        stage_lane_lights<TL, R, BLOCK>(a, s_V, s_pos, l0, nl);
-        __syncthreads();
-      }
+    // lights lb .. lb + nl - 1 of the staged tile, kLB at a time
+    auto sweep_stage = [&](int nl) {
       for (int lb = 0; lb < nl; lb += kLB) {
         float gown[kLB];
         __syncwarp();
@@ -466,6 +464,18 @@ __global__ void __launch_bounds__(128, TL <= 12 ? 4 : 2) shade_spectral_lanes_ke
           }
         }
       }
+    };
+    if (one_stage) {
+      // every light is staged: one sweep, no block barrier in the tile loop
+      sweep_stage(a.L);
+    } else {
+      for (int l0 = 0; l0 < a.L; l0 += kLT) {
+        const int nl = min(kLT, a.L - l0);
+        __syncthreads();
+        stage_lane_lights<TL, R, BLOCK>(a, s_V, s_pos, l0, nl);
+        __syncthreads();
+        sweep_stage(nl);
+      }
     }
     // the last R samples of this lane's pixel (lanes grp < QP); added below to
     // the lane's own partial sums of that pixel
@@ -485,7 +495,7 @@ __global__ void __launch_bounds__(128, TL <= 12 ? 4 : 2) shade_spectral_lanes_ke
         rX = __fmaf_rn(trem[r], S, rX);
         rY = __fmaf_rn(trem[VROW + r], S, rY);
         rZ = __fmaf_rn(trem[2 * VROW + r], S, rZ);
-        if (WS && grp < QP && mypix < a.P) a.spectra[mypix * a.n + lam] = S;
+        if (WS && grp < QP && mypix < P) a.spectra[mypix * a.n + lam] = S;
       }
     }
     // radiance of the group's pixels over this lane's wavelengths; XYZ by butterfly
@@ -494,7 +504,7 @@ __global__ void __launch_bounds__(128, TL <= 12 ? 4 : 2) shade_spectral_lanes_ke
       const int jm1 = __shfl_sync(0xffffffffu, bad ? -1 : m1, j, 8);
       const int jm2 = __shfl_sync(0xffffffffu, bad ? 0 : m2, j, 8);
       const float jh = __shfl_sync(0xffffffffu, h, j, 8);
-      const int64_t pix = pix0 + j;
+      const int pix = pix0 + j;
       const bool jbad = jm1 < 0;
       const float* r1 = a.mats + (int64_t)(jbad ? 0 : jm1) * a.n + grp * TL;
       const float* r2 = a.mats + (int64_t)jm2 * a.n + grp * TL;
@@ -508,7 +518,7 @@ __global__ void __launch_bounds__(128, TL <= 12 ? 4 : 2) shade_spectral_lanes_ke
           X = __fmaf_rn(tw[i], S, X);
           Y = __fmaf_rn(tw[VROW + i], S, Y);
           Z = __fmaf_rn(tw[2 * VROW + i], S, Z);
-          if (WS && pix < a.P) a.spectra[pix * a.n + grp * TL + i] = S;
+          if (WS && pix < P) a.spectra[pix * a.n + grp * TL + i] = S;
         }
       }
       if (R > 0 && grp == j) {
@@ -522,7 +532,7 @@ __global__ void __launch_bounds__(128, TL <= 12 ? 4 : 2) shade_spectral_lanes_ke
         Y = __fadd_rn(Y, __shfl_xor_sync(0xffffffffu, Y, o, 8));
         Z = __fadd_rn(Z, __shfl_xor_sync(0xffffffffu, Z, o, 8));
       }
-      if (grp == j && pix < a.P) {
+      if (grp == j && pix < P) {
         a.xyz[3 * pix] = X;
         a.xyz[3 * pix + 1] = Y;
         a.xyz[3 * pix + 2] = Z;
@@ -546,12 +556,31 @@ hsc_status launch_lanes_t(const SpecArgs& a, const LaunchCfg& cfg, cudaStream_t 
     occ = o > 0 ? o : 1;
   }
   constexpr int PX = 16 * (SEC ? 4 : 8);
-  const int64_t tiles = (a.P + PX - 1) / PX;
-  int64_t grid = cfg.waves > 0 ? (int64_t)cfg.sm_count * occ * cfg.waves : tiles;
-  if (grid > tiles) grid = tiles;
-  if (grid < 1) grid = 1;
-  kern<<<(unsigned)grid, 128, smem, s>>>(a);
-  return check_launch("shade_spectral_lanes_kernel");
+  // the kernel indexes pixels, 3 x pixels and pixels x n in 32 bits: a frame
+  // beyond that is shaded in slices (every pixel is independent)
+  const int64_t width = a.n > 3 ? a.n : 3;
+  const int64_t slice = (INT32_MAX / width) / PX * PX;
+  for (int64_t p0 = 0; p0 < a.P; p0 += slice) {
+    SpecArgs c = a;
+    c.P = a.P - p0 < slice ? a.P - p0 : slice;
+    c.n1 = a.n1 + 3 * p0;
+    c.x1 = a.x1 + 3 * p0;
+    c.m1 = a.m1 + p0;
+    if (SEC) {
+      c.n2 = a.n2 + 3 * p0;
+      c.x2 = a.x2 + 3 * p0;
+      c.m2 = a.m2 + p0;
+    }
+    c.xyz = a.xyz + 3 * p0;
+    if (WS) c.spectra = a.spectra + p0 * a.n;
+    const int64_t tiles = (c.P + PX - 1) / PX;
+    int64_t grid = cfg.waves > 0 ? (int64_t)cfg.sm_count * occ * cfg.waves : tiles;
+    if (grid > tiles) grid = tiles;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, 128, smem, s>>>(c);
+    HSC_TRY(check_launch("shade_spectral_lanes_kernel"));
+  }
+  return HSC_OK;
 }
 
 template <int TL, int R, bool EXACT>

@@ -34,7 +34,7 @@ def test_row_groups_and_host_info():
     import pytest
     bench = _bench()
     every = bench.wanted_rows(argparse.Namespace(rows_only=""))
-    assert {"core", "small", "batch", "chains", "upsample", "pathtrace", "sweep", "serve"} == every
+    assert {"core", "precision", "small", "batch", "chains", "upsample", "pathtrace", "sweep", "serve"} == every
     assert bench.wanted_rows(argparse.Namespace(rows_only="small, serve")) == {"small", "serve"}
     with pytest.raises(SystemExit):
         bench.wanted_rows(argparse.Namespace(rows_only="nope"))

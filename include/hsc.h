@@ -66,6 +66,8 @@ extern "C" {
 #define HSC_NOALLOC_MAX_K 96  /* channel limit of hsc_quantize_fp8_noalloc   */
 #define HSC_MAX_FRAMES_PER_CALL 512  /* frames per hsc_shade_frames call    */
 #define HSC_QUEUE_SLOTS 256  /* streams per context with their own tile counter */
+#define HSC_ASSETS_MAX_CODES 4096  /* n_mat x k limit of hsc_shade_latent_assets */
+#define HSC_ASSETS_MAX_LIGHTS 256  /* light limit of hsc_shade_latent_assets       */
 #define HSC_UPSAMPLE_HIDDEN 128      /* hidden width of the upsampling network */
 
 typedef struct hsc_ctx hsc_ctx;
@@ -239,6 +241,28 @@ HSC_API hsc_status hsc_shade_latent(hsc_ctx* ctx, const hsc_gbuffer* g1, const h
                             const void* light_codes, int k, hsc_dtype code_dt, hsc_mode mode,
                             void* latent_out, hsc_dtype latent_dt, float* latent_scales,
                             float* xyz_out, uint8_t* srgb8_out, const float* M_xyz, void* stream);
+
+/* A latent frame straight from spectral assets, in one launch (Eq. 4 and 6,
+ * Fig. 2b).  The paper encodes materials and lights once per scene; for a
+ * small frame the encode launches cost more than the encode, so here every
+ * CTA of the fused shading launch first encodes the materials and lights into
+ * shared memory, each code value summed exactly as hsc_encode sums it.  The
+ * latent image, XYZ and sRGB8 are therefore the bits of hsc_encode (FP32
+ * codes) followed by hsc_shade_latent (HSC_FUSED) with the same outputs.
+ *   E: device k x n (W_enc);  mat_spectra: device n_mat x n;  light_spd:
+ *   device L x n (unit-peak SPDs, scaled by the lights' intensities as in
+ *   hsc_shade_latent);  latent_out: device P x k float32;  xyz_out, srgb8_out,
+ *   M_xyz: as in hsc_shade_latent (nullable outputs).
+ * Limits (HSC_ERR_INVALID_ARG beyond them): k in {3, 6, 9}, 1 <= n <=
+ * HSC_MAX_N, n_mat x k <= HSC_ASSETS_MAX_CODES, L <= HSC_ASSETS_MAX_LIGHTS.
+ * Every CTA repeats the encode (n_mat + L) x k dot products of length n, so
+ * large frames or large asset sets are better served by hsc_encode once and
+ * hsc_shade_latent per frame.  No scratch memory.                          */
+HSC_API hsc_status hsc_shade_latent_assets(hsc_ctx* ctx, const hsc_gbuffer* g1, const hsc_gbuffer* g2,
+                                           int64_t pixels, const float* E, int k, int n, const float* mat_spectra,
+                                           int n_mat, const hsc_lights* lights, const float* light_spd,
+                                           float* latent_out, float* xyz_out, uint8_t* srgb8_out,
+                                           const float* M_xyz, void* stream);
 
 /* Per-channel fp8 quantisation of an FP32 latent image: scale_c = max_p z_c / 448
  * (1 for an all-zero channel), code = RNE_e4m3(z * (1/scale_c)) saturating.

@@ -32,6 +32,9 @@ HSC_MAX_K = 96
 HSC_NOALLOC_MAX_K = 96
 HSC_MAX_FRAMES_PER_CALL = 512
 HSC_MAX_N = 128
+HSC_QUEUE_SLOTS = 256
+HSC_ASSETS_MAX_CODES = 4096
+HSC_ASSETS_MAX_LIGHTS = 256
 
 STATUS_NAMES = {0: "HSC_OK", 1: "HSC_ERR_INVALID_ARG", 2: "HSC_ERR_CUDA", 3: "HSC_ERR_OOM",
                 4: "HSC_ERR_UNSUPPORTED", 5: "HSC_ERR_TIMEOUT", 6: "HSC_ERR_DEVICE_CHECK"}
@@ -88,6 +91,8 @@ _SIGS = {
     "hsc_reassemble": ([_vp, ctypes.POINTER(_vp), _i32, _i64, _vp, _vp], _i32),
     "hsc_shade_latent": ([_vp, _GB, _GB, _i64, _vp, _i32, _LI, _vp, _i32, _i32, _i32, _vp, _i32, _vp, _vp, _vp,
                           _vp, _vp], _i32),
+    "hsc_shade_latent_assets": ([_vp, _GB, _GB, _i64, _vp, _i32, _i32, _vp, _i32, _LI, _vp, _vp, _vp, _vp, _vp,
+                                 _vp], _i32),
     "hsc_quantize_fp8": ([_vp, _vp, _i64, _i32, _vp, _vp, _vp], _i32),
     "hsc_quantize_fp8_noalloc": ([_vp, _i64, _i32, _vp, _vp, _vp], _i32),
     "hsc_decode_xyz": ([_vp, _vp, _i32, _vp, _i64, _i32, _vp, _vp, _vp, _vp], _i32),
@@ -320,6 +325,28 @@ def hsc_shade_latent(ctx: Context, g1: GBuffer, g2: Optional[GBuffer], mat_codes
                                  ctypes.byref(lights._s), _ptr(light_codes), int(k), _dt(mat_codes), int(mode),
                                  _ptr(latent_out), _dt(latent_out), _ptr(latent_scales), _ptr(xyz_out),
                                  _ptr(srgb8_out), _ptr(M_xyz), _stream(stream)))
+
+
+def hsc_shade_latent_assets(ctx: Context, g1: GBuffer, g2: Optional[GBuffer], E: torch.Tensor,
+                            mat_spectra: torch.Tensor, lights: Lights, light_spd: torch.Tensor,
+                            latent_out: torch.Tensor, xyz_out: Optional[torch.Tensor] = None,
+                            M_xyz: Optional[torch.Tensor] = None, srgb8_out: Optional[torch.Tensor] = None,
+                            stream=None):
+    """One-launch latent frame from spectral assets (the encode in the shading
+    prologue); see include/hsc.h."""
+    k, n = E.shape
+    if E.dtype != torch.float32 or mat_spectra.dtype != torch.float32 or light_spd.dtype != torch.float32:
+        raise ValueError("E and the spectra must be float32")
+    if mat_spectra.shape[1] != n or light_spd.shape != (lights.count, n):
+        raise ValueError("spectra must be (n_mat, n) and (L, n)")
+    if latent_out.shape != (g1.pixels, k) or latent_out.dtype != torch.float32:
+        raise ValueError("latent_out must be (P, k) float32")
+    if srgb8_out is not None and (srgb8_out.shape != (g1.pixels, 3) or srgb8_out.dtype != torch.uint8):
+        raise ValueError("srgb8_out must be (P,3) uint8")
+    _check(_lib.hsc_shade_latent_assets(ctx.handle, _gb(g1), _gb(g2), g1.pixels, _ptr(E), int(k), int(n),
+                                        _ptr(mat_spectra), int(mat_spectra.shape[0]), ctypes.byref(lights._s),
+                                        _ptr(light_spd), _ptr(latent_out), _ptr(xyz_out), _ptr(srgb8_out),
+                                        _ptr(M_xyz), _stream(stream)))
 
 
 def hsc_quantize_fp8(ctx: Context, latent: torch.Tensor, codes_out: torch.Tensor, scales_out: torch.Tensor,

@@ -766,3 +766,57 @@ def test_dynamic_queue_launches_on_two_streams(env):
     hsc.hsc_sync(ctx)
     for o in outs:
         assert torch.equal(o, ref)
+
+
+
+@pytest.mark.parametrize("w,h,grid_spec,lights,sec,k,n_mat,rgb", [
+    (256, 256, hi.GRID_31, 4, False, 6, 16, True),     # the 256x256 n = 31 four-light frame
+    (97, 61, hi.GRID_81, 37, True, 9, 45, True),       # ragged tiles, bounce, k = 9
+    (33, 7, hi.GRID_81, 256, True, 3, 30, False),      # the most lights, XYZ only
+    (1, 1, hi.GRID_31, 1, False, 6, 1, True),          # one pixel, one light, one material
+])
+def test_shade_latent_assets_equals_encode_then_shade(env, w, h, grid_spec, lights, sec, k, n_mat, rgb):
+    # the one-launch asset path encodes in the shading prologue with the
+    # summation of hsc_encode: latent, XYZ and sRGB8 are the bits of
+    # hsc_encode (FP32) + hsc_shade_latent (FUSED), and match the oracle
+    hsc, ctx, dev = env
+    import torch
+    n_saw = n_mat // 5
+    f = hi.make_frame(50 + k, w, h, grid_spec, n_smooth=n_mat - n_saw, n_saw=n_saw, lights=lights, secondary=sec)
+    E, D = _codec(k, grid_spec[2])
+    df = upload(hsc, ctx, f, dev)
+    Ed = torch.from_numpy(np.ascontiguousarray(E)).to(dev)
+    M = torch.empty(3, k, device=dev)
+    hsc.hsc_fold_xyz(ctx, df.T, torch.from_numpy(np.ascontiguousarray(D)).to(dev), M)
+    zm, zl = encode_all(hsc, ctx, df, E)
+    ref = [torch.empty(f.pixels, k, device=dev), torch.empty(f.pixels, 3, device=dev),
+           torch.empty(f.pixels, 3, device=dev, dtype=torch.uint8) if rgb else None]
+    got = [torch.full((f.pixels, k), -1.0, device=dev), torch.full((f.pixels, 3), -1.0, device=dev),
+           torch.zeros(f.pixels, 3, device=dev, dtype=torch.uint8) if rgb else None]
+    hsc.hsc_shade_latent(ctx, df.g1, df.g2, zm, df.lights, zl, hsc.HSC_FUSED, ref[0], xyz_out=ref[1], M_xyz=M,
+                         srgb8_out=ref[2])
+    hsc.hsc_shade_latent_assets(ctx, df.g1, df.g2, Ed, df.mats, df.lights, df.spd, got[0], xyz_out=got[1], M_xyz=M,
+                                srgb8_out=got[2])
+    hsc.hsc_sync(ctx)
+    assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1])
+    if rgb:
+        assert torch.equal(got[2], ref[2])
+    z_ref, x_ref = _oracle_latent(f, E, D)
+    assert rel_err_rows(got[0].cpu().numpy(), z_ref) <= TOL
+    assert metrics.rel_xyz_error(got[1].cpu().numpy(), x_ref) <= TOL
+
+
+def test_shade_latent_assets_limits(env):
+    hsc, ctx, dev = env
+    import torch
+    f = hi.make_frame(3, 8, 8, hi.GRID_31, n_smooth=4, n_saw=0, lights=3, secondary=False)
+    df = upload(hsc, ctx, f, dev)
+    lat = torch.empty(f.pixels, 12, device=dev)
+    with pytest.raises(hsc.HscError) as ei:         # k = 12 is not built for the one-launch path
+        hsc.hsc_shade_latent_assets(ctx, df.g1, None, torch.zeros(12, 31, device=dev), df.mats, df.lights, df.spd, lat)
+    assert ei.value.status == hsc.HSC_ERR_INVALID_ARG
+    big = torch.zeros(hsc.HSC_ASSETS_MAX_CODES // 6 + 1, 31, device=dev)
+    with pytest.raises(hsc.HscError) as ei:         # more material codes than a CTA stages
+        hsc.hsc_shade_latent_assets(ctx, df.g1, None, torch.zeros(6, 31, device=dev), big, df.lights, df.spd,
+                                    torch.empty(f.pixels, 6, device=dev))
+    assert ei.value.status == hsc.HSC_ERR_INVALID_ARG

@@ -4,7 +4,7 @@
 // frame is small (a 256 x 256 G-buffer with a handful of lights shades in a
 // few microseconds) the launches of a separate encode cost more than the
 // encode itself, so each CTA encodes what it stages into shared memory.  Every
-// code value is summed by one warp exactly as hsc_encode sums it (lane-strided
+// code value is summed in exactly the order hsc_encode sums it (lane-strided
 // partial sums, then a butterfly), so the codes -- and the latent image, XYZ
 // and sRGB8 -- are the bits of hsc_encode (FP32 codes) followed by
 // hsc_shade_latent (FUSED).
@@ -32,15 +32,27 @@ struct AssetArgs {
   const float* spd;   // L x n
 };
 
-// One code value z_c = sum_i E[c][i] s[i] by one warp: lane t sums the
-// products i = t, t + 32, ... in order, then a butterfly adds the 32 partial
-// sums (the order of hsc_encode's kernel).
-__device__ __forceinline__ float warp_code(const float* e, const float* s, int n, int lane) {
-  float acc = 0.0f;
-  for (int i = lane; i < n; i += 32) acc = __fmaf_rn(__ldg(e + i), __ldg(s + i), acc);
+// One code value z_c = sum_i E[c][i] s[i] by one thread, summed in the order
+// of hsc_encode's warp: partial sum t (t < 32) accumulates the products
+// i = t, t + 32, ... with FMAs, then the 32 partials are added as the
+// xor-butterfly adds them for lane 0 (halves of 16, 8, 4, 2, 1; floating
+// addition is commutative, so the operand order of each pair does not
+// matter).  The loads of all products are independent, so a thread waits
+// for memory once per code instead of once per shuffle step.
+__device__ __forceinline__ float thread_code(const float* __restrict__ e, const float* __restrict__ s, int n) {
+  float v[32];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
-  return acc;
+  for (int t = 0; t < 32; ++t) v[t] = 0.0f;
+  for (int i0 = 0; i0 < n; i0 += 32) {
+#pragma unroll
+    for (int t = 0; t < 32; ++t)
+      if (i0 + t < n) v[t] = __fmaf_rn(__ldg(e + i0 + t), __ldg(s + i0 + t), v[t]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int t = 0; t < o; ++t) v[t] = __fadd_rn(v[t], v[t + o]);
+  return v[0];
 }
 
 template <int KC, bool SEC, bool RGB>
@@ -51,23 +63,22 @@ __global__ void __launch_bounds__(kAssetBlock) shade_assets_kernel(const AssetAr
   const ShadeArgs& a = A.a;
   float* sl = reinterpret_cast<float*>(s_light);
   float* s_mat = reinterpret_cast<float*>(s_light + a.L * F4);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int kWarps = kAssetBlock / 32;
   // light records in the scalar staging layout: position, codes x (I / pi), zeros
   for (int i = threadIdx.x; i < a.L * F4 * 4; i += kAssetBlock) {
     const int l = i / (F4 * 4), j = i - l * (F4 * 4);
     if (j < 3) sl[i] = __ldg(a.lpos + 3 * l + j);
     else if (j >= 3 + KC) sl[i] = 0.0f;
   }
-  for (int w = warp; w < a.L * KC; w += kWarps) {
-    const int l = w / KC, c = w - l * KC;
-    const float z = warp_code(A.E + (int64_t)c * A.n, A.spd + (int64_t)l * A.n, A.n, lane);
-    if (lane == 0) sl[l * F4 * 4 + 3 + c] = __fmul_rn(z, __fmul_rn(__ldg(a.linten + l), kInvPi));
-  }
-  for (int w = warp; w < a.n_mat * KC; w += kWarps) {
-    const int m = w / KC, c = w - m * KC;
-    const float z = warp_code(A.E + (int64_t)c * A.n, A.mats + (int64_t)m * A.n, A.n, lane);
-    if (lane == 0) s_mat[m * KC + c] = z;
+  // one code value per thread: the light codes, then the material codes
+  for (int w = threadIdx.x; w < (a.L + a.n_mat) * KC; w += kAssetBlock) {
+    const int row = w / KC, c = w - row * KC;
+    if (row < a.L) {
+      const float z = thread_code(A.E + (int64_t)c * A.n, A.spd + (int64_t)row * A.n, A.n);
+      sl[row * F4 * 4 + 3 + c] = __fmul_rn(z, __fmul_rn(__ldg(a.linten + row), kInvPi));
+    } else {
+      const int m = row - a.L;
+      s_mat[m * KC + c] = thread_code(A.E + (int64_t)c * A.n, A.mats + (int64_t)m * A.n, A.n);
+    }
   }
   stage_decode_matrix<KC, kAssetBlock>(a, s_M);
   __syncthreads();

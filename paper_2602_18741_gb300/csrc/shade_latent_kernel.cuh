@@ -117,7 +117,8 @@ __device__ __forceinline__ void load_code_row(const ShadeArgs& a, int row, float
 // tiles are staged here.  Must be called by every thread of the CTA.
 template <int KC, int PPT, bool SEC, int BLOCK, int VEC, bool RGB = false>
 __device__ __forceinline__ void shade_tile(const ShadeArgs& a, int64_t tile, float4* s_light, bool staged,
-                                           const float* s_M, const float* s_mat = nullptr) {
+                                           const float* s_M, const float* s_mat = nullptr,
+                                           unsigned int* cmax = nullptr) {
   constexpr int F4 = LightStage<KC, VEC>::F4;
   constexpr int NPT = PPT * (SEC ? 2 : 1);
   static_assert(VEC == 1 || NPT % 2 == 0, "paired points need an even point count");
@@ -313,13 +314,14 @@ __device__ __forceinline__ void shade_tile(const ShadeArgs& a, int64_t tile, flo
           }
         }
       }
-      if (a.chan_max) {
-        // non-negative floats order like their bit patterns
+      if (cmax) {
+        // non-negative floats order like their bit patterns; one atomic per
+        // warp and channel into the CTA's maxima (shared memory)
 #pragma unroll
         for (int c = 0; c < KC; ++c) {
           const unsigned int bits = valid ? __float_as_uint(fmaxf(out[c], 0.0f)) : 0u;
           const unsigned int mx = __reduce_max_sync(0xffffffffu, bits);
-          if ((tid & 31) == 0 && mx) atomicMax(a.chan_max + a.c0 + c, mx);
+          if ((tid & 31) == 0 && mx) atomicMax(cmax + c, mx);
         }
       }
     }
@@ -356,7 +358,10 @@ __global__ void __launch_bounds__(BLOCK, (latent_min_blocks<KC, PPT, BLOCK, VEC>
   // dynamic shared memory: the light tile, then the material table if it fits
   extern __shared__ float4 s_light[];
   __shared__ float s_M[3 * KC];
+  __shared__ unsigned int s_cmax[KC];  // the CTA's channel maxima (fp8 path)
   const bool staged = a.L <= kLightTile;
+  unsigned int* cmax = a.chan_max ? s_cmax : nullptr;
+  if (threadIdx.x < KC) s_cmax[threadIdx.x] = 0u;
   float* s_mat = mat_staged<KC>(a.n_mat)
                      ? reinterpret_cast<float*>(s_light + min(a.L, kLightTile) * LightStage<KC, VEC>::F4)
                      : nullptr;
@@ -373,12 +378,17 @@ __global__ void __launch_bounds__(BLOCK, (latent_min_blocks<KC, PPT, BLOCK, VEC>
       const int64_t tile = s_next;
       __syncthreads();
       if (tile >= a.tiles) break;
-      shade_tile<KC, PPT, SEC, BLOCK, VEC, RGB>(a, tile, s_light, staged, s_M, s_mat);
+      shade_tile<KC, PPT, SEC, BLOCK, VEC, RGB>(a, tile, s_light, staged, s_M, s_mat, cmax);
     }
     release_queue(a.queue);
   } else {
     for (int64_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x)
-      shade_tile<KC, PPT, SEC, BLOCK, VEC, RGB>(a, tile, s_light, staged, s_M, s_mat);
+      shade_tile<KC, PPT, SEC, BLOCK, VEC, RGB>(a, tile, s_light, staged, s_M, s_mat, cmax);
+  }
+  if (cmax) {
+    // one global atomic per CTA and channel
+    __syncthreads();
+    if (threadIdx.x < KC && s_cmax[threadIdx.x]) atomicMax(a.chan_max + a.c0 + threadIdx.x, s_cmax[threadIdx.x]);
   }
 }
 

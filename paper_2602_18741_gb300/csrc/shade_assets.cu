@@ -55,6 +55,8 @@ __device__ __forceinline__ float thread_code(const float* __restrict__ e, const 
   return v[0];
 }
 
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
 template <int KC, bool SEC, bool RGB>
 __global__ void __launch_bounds__(kAssetBlock) shade_assets_kernel(const AssetArgs A) {
   constexpr int F4 = LightStage<KC, 1>::F4;
@@ -63,6 +65,22 @@ __global__ void __launch_bounds__(kAssetBlock) shade_assets_kernel(const AssetAr
   const ShadeArgs& a = A.a;
   float* sl = reinterpret_cast<float*>(s_light);
   float* s_mat = reinterpret_cast<float*>(s_light + a.L * F4);
+  // the tile's G-buffer lines into L1 now, so that the shading's loads after
+  // the encode find them there (the encode's own loads run meanwhile)
+#pragma unroll
+  for (int j = 0; j < kAssetPPT; ++j) {
+    const int64_t p = (int64_t)blockIdx.x * (kAssetBlock * kAssetPPT) + (int64_t)j * kAssetBlock + threadIdx.x;
+    if (p < a.P) {
+      prefetch_l1(a.x1 + 3 * p);
+      prefetch_l1(a.n1 + 3 * p);
+      prefetch_l1(a.m1 + p);
+      if (SEC) {
+        prefetch_l1(a.x2 + 3 * p);
+        prefetch_l1(a.n2 + 3 * p);
+        prefetch_l1(a.m2 + p);
+      }
+    }
+  }
   // light records in the scalar staging layout: position, codes x (I / pi), zeros
   for (int i = threadIdx.x; i < a.L * F4 * 4; i += kAssetBlock) {
     const int l = i / (F4 * 4), j = i - l * (F4 * 4);

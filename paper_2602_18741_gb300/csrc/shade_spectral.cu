@@ -354,8 +354,11 @@ __device__ __forceinline__ void stage_lane_lights(const SpecArgs& a, float* s_V,
                       : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
 }
 
-// EXACT: n = 8 TL + R (no sample index reaches n); WS: spectra are written.
-template <int TL, int R, bool SEC, bool EXACT, bool WS>
+// EXACT: n = 8 TL + R (no sample index reaches n); WS: spectra are written;
+// ONE: every light fits one stage (L <= kLT), so the tile loop has no block
+// barrier and no restaging (a separate instantiation: the compiler allocates
+// its registers better without the restaging path).
+template <int TL, int R, bool SEC, bool EXACT, bool WS, bool ONE>
 __global__ void __launch_bounds__(128, TL <= 12 ? 4 : 2) shade_spectral_lanes_kernel(const SpecArgs a) {
   using SH = LaneShape<TL, R>;
   constexpr int BLOCK = 128;
@@ -375,8 +378,7 @@ __global__ void __launch_bounds__(128, TL <= 12 ? 4 : 2) shade_spectral_lanes_ke
     const int c = i / VROW, r = i - c * VROW, lam = lane_row_sample<TL, R>(r, a.n);
     s_T[i] = lam >= 0 ? __ldg(a.T + c * a.n + lam) : 0.0f;
   }
-  const bool one_stage = a.L <= kLT;
-  if (one_stage) stage_lane_lights<TL, R, BLOCK>(a, s_V, s_pos, 0, a.L);
+  if (ONE) stage_lane_lights<TL, R, BLOCK>(a, s_V, s_pos, 0, a.L);
   __syncthreads();
   float* gx = s_gx + (tid >> 5) * (kLB * 32);
   const float* vr = s_V + grp * VS;            // this lane's group row of light 0
@@ -408,7 +410,6 @@ __global__ void __launch_bounds__(128, TL <= 12 ? 4 : 2) shade_spectral_lanes_ke
       const float sny = __shfl_down_sync(0xffffffffu, pt.ny, 4, 8), snz = __shfl_down_sync(0xffffffffu, pt.nz, 4, 8);
       if (grp < 4) h = bounce_term(pt.x, pt.y, pt.z, pt.nx, pt.ny, pt.nz, sx, sy, sz, snx, sny, snz);
     }
-    if (bad && grp < QP && mypix < P) atomicOr(a.err, HSC_DEVERR_MATERIAL);
     float acc[8][TL];
     float accr[RN];                            // this lane's point, the last R samples
 #pragma unroll
@@ -465,7 +466,7 @@ __global__ void __launch_bounds__(128, TL <= 12 ? 4 : 2) shade_spectral_lanes_ke
         }
       }
     };
-    if (one_stage) {
+    if constexpr (ONE) {
       // every light is staged: one sweep, no block barrier in the tile loop
       sweep_stage(a.L);
     } else {
@@ -506,6 +507,7 @@ __global__ void __launch_bounds__(128, TL <= 12 ? 4 : 2) shade_spectral_lanes_ke
       const float jh = __shfl_sync(0xffffffffu, h, j, 8);
       const int pix = pix0 + j;
       const bool jbad = jm1 < 0;
+      if (jbad && grp == j && pix < P) atomicOr(a.err, HSC_DEVERR_MATERIAL);
       const float* r1 = a.mats + (int64_t)(jbad ? 0 : jm1) * a.n + grp * TL;
       const float* r2 = a.mats + (int64_t)jm2 * a.n + grp * TL;
       float X = 0.0f, Y = 0.0f, Z = 0.0f;
@@ -541,9 +543,9 @@ __global__ void __launch_bounds__(128, TL <= 12 ? 4 : 2) shade_spectral_lanes_ke
   }
 }
 
-template <int TL, int R, bool SEC, bool EXACT, bool WS>
+template <int TL, int R, bool SEC, bool EXACT, bool WS, bool ONE>
 hsc_status launch_lanes_t(const SpecArgs& a, const LaunchCfg& cfg, cudaStream_t s) {
-  auto kern = shade_spectral_lanes_kernel<TL, R, SEC, EXACT, WS>;
+  auto kern = shade_spectral_lanes_kernel<TL, R, SEC, EXACT, WS, ONE>;
   constexpr int VROW = LaneShape<TL, R>::VROW;
   static_assert(kLT % kLB == 0, "light stages hold whole exchange batches");
   const size_t smem = sizeof(float) * ((size_t)kLT * VROW + 4 * kLT + 3 * VROW + 4 * kLB * 32);
@@ -583,12 +585,18 @@ hsc_status launch_lanes_t(const SpecArgs& a, const LaunchCfg& cfg, cudaStream_t 
   return HSC_OK;
 }
 
+template <int TL, int R, bool SEC, bool EXACT, bool WS>
+hsc_status launch_lanes_one(const SpecArgs& a, const LaunchCfg& cfg, cudaStream_t s) {
+  return a.L <= kLT ? launch_lanes_t<TL, R, SEC, EXACT, WS, true>(a, cfg, s)
+                    : launch_lanes_t<TL, R, SEC, EXACT, WS, false>(a, cfg, s);
+}
+
 template <int TL, int R, bool EXACT>
 hsc_status launch_lanes_n(const SpecArgs& a, bool sec, const LaunchCfg& cfg, cudaStream_t s) {
   const bool ws = a.spectra != nullptr;
   if (sec)
-    return ws ? launch_lanes_t<TL, R, true, EXACT, true>(a, cfg, s) : launch_lanes_t<TL, R, true, EXACT, false>(a, cfg, s);
-  return ws ? launch_lanes_t<TL, R, false, EXACT, true>(a, cfg, s) : launch_lanes_t<TL, R, false, EXACT, false>(a, cfg, s);
+    return ws ? launch_lanes_one<TL, R, true, EXACT, true>(a, cfg, s) : launch_lanes_one<TL, R, true, EXACT, false>(a, cfg, s);
+  return ws ? launch_lanes_one<TL, R, false, EXACT, true>(a, cfg, s) : launch_lanes_one<TL, R, false, EXACT, false>(a, cfg, s);
 }
 
 // n = 81 and n = 31 split exactly (8 x 10 + 1, 8 x 3 + 7); other n round up

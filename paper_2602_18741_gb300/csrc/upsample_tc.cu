@@ -2,26 +2,31 @@
 //     h1 = silu(W1 c + b1),  h2 = silu(W2 h1 + b2),  z = W3 h2 + b3,
 // hidden width 128, on the 5th-generation tensor cores.
 //
-// A CTA of 512 threads takes tiles of 128 pixels.  Per tile three BF16 MMAs
-// with FP32 accumulation run in sequence, each issued by one thread and
-// committed to an mbarrier:
+// A CTA takes tiles of 128 pixels; 16 epilogue warps and one MMA warp.  Per
+// tile three BF16 MMAs with FP32 accumulation run in sequence, each issued by
+// the MMA warp's first lane and committed to the slot's "done" mbarrier:
 //   layer 1: [128 x 16] x [16 x 128]   (the colour in K columns 0..2),
 //   layer 2: [128 x 128] x [128 x 128] (eight K = 16 steps),
 //   layer 3: [128 x 128] x [128 x 16]  (k <= 16 outputs, zero-padded).
-// Between them the epilogue runs on all 16 warps: pixel row r is TMEM lane r,
-// read by the four warps of lane quadrant r / 32, each for 32 of the 128
-// hidden columns (tcgen05.ld); a thread adds the bias, applies SiLU as
-// x/2 (1 + tanh(x/2)) with the hardware tanh approximation, rounds to bf16
-// and writes its 32 values into the next layer's A operand in shared memory
-// (no-swizzle K-major layout).  The weights are converted to bf16 and staged
-// once per CTA.  One CTA per SM works on two tiles at once (two A buffers,
-// two 256-column TMEM regions, one mbarrier each) in the order
+// Between them the epilogue runs on the 16 epilogue warps: pixel row r is
+// TMEM lane r, read by the four warps of lane quadrant r / 32, each for 32 of
+// the 128 hidden columns (tcgen05.ld); a thread adds the bias, applies SiLU
+// and rounds to bf16, writing its 32 values into the next layer's A operand
+// in shared memory (no-swizzle K-major layout).  The weights and biases of
+// the hidden layers are staged at half scale (exact in bf16 and FP32), so the
+// accumulator plus bias is already x/2 and SiLU(x) = x/2 (1 + tanh(x/2)) is
+// one FMA around the hardware tanh.  One CTA per SM works on two tiles at
+// once (two A buffers, two 256-column TMEM regions); the hand-offs are
+// mbarriers, not block barriers: every epilogue thread arrives on the slot's
+// "operand ready" barrier once its shared-memory writes and TMEM reads are
+// done and goes on with the other slot, and the MMA lane waits for all 512
+// arrivals before it issues, in the order
 //   MMA1(a) MMA1(b) | epi1(a) MMA2(a) | epi1(b) MMA2(b) | epi2(a) MMA3(a) |
 //   epi2(b) MMA3(b) | out(a) out(b),
-// so each tile's tensor-core work runs while the other tile's epilogue runs;
-// the next pair's colours are loaded while the first layer runs.  Every
-// mbarrier wait is bounded; on expiry the kernel sets the timeout bit, frees
-// its TMEM and returns.
+// so one tile's tensor-core work runs while the other tile's epilogue runs.
+// Every mbarrier wait is bounded; on expiry the kernel sets the timeout bit,
+// the MMA lane drains its MMAs (bounded), and TMEM is freed after a final
+// block barrier.
 #include "common.cuh"
 #include "tcgen05.cuh"
 
@@ -31,7 +36,8 @@ namespace {
 
 using namespace tc;
 
-constexpr int kUpThreads = 512;
+constexpr int kUpThreads = 512;             // epilogue threads (16 warps)
+constexpr int kUpBlock = kUpThreads + 32;    // + the MMA warp
 constexpr int kUpRows = 128;            // MMA M, pixels per tile
 constexpr int kHidden = HSC_UPSAMPLE_HIDDEN;
 constexpr int kKBlocks = kHidden / 16;  // K = 16 steps of the hidden layers
@@ -60,7 +66,7 @@ constexpr int kOffA1 = kOffW3 + kKBlocks * 512;            // 2 slots x [128 x 1
 constexpr int kOffH = kOffA1 + 2 * kBlockBytes;            // 2 slots x 8 x [128 x 16]
 constexpr int kSlotH = kKBlocks * kBlockBytes;
 constexpr int kOffBias = kOffH + 2 * kSlotH;               // b1, b2 (128 each), b3 (16)
-constexpr int kOffBar = kOffBias + (2 * kHidden + 16) * 4; // two mbarriers, TMEM address, status
+constexpr int kOffBar = kOffBias + (2 * kHidden + 16) * 4; // five mbarriers, TMEM address, status
 constexpr int kUpSmem = kOffBar + 64 + 1024;               // + alignment slack
 
 __device__ __forceinline__ float tanh_approx(float x) {
@@ -69,10 +75,8 @@ __device__ __forceinline__ float tanh_approx(float x) {
   return y;
 }
 
-__device__ __forceinline__ float silu_tc(float x) {
-  const float h = __fmul_rn(0.5f, x);
-  return __fmaf_rn(h, tanh_approx(h), h);
-}
+// SiLU of x given h = x / 2: x/2 (1 + tanh(x/2)) = h + h tanh(h).
+__device__ __forceinline__ float silu_half(float h) { return __fmaf_rn(h, tanh_approx(h), h); }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x = lo (low half)
@@ -93,7 +97,7 @@ __device__ __forceinline__ void commit(uint32_t bar) {
 }
 
 // Hand the shared-memory writes of every thread to the tensor core and order
-// them before the MMA issued after the barrier.
+// them before the MMA issued after the barrier (set-up only).
 __device__ __forceinline__ void smem_to_mma_barrier() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -101,16 +105,27 @@ __device__ __forceinline__ void smem_to_mma_barrier() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// Thread 0 waits for the committed MMAs; everyone learns whether they ended.
-__device__ __forceinline__ bool wait_mma(uint32_t bar, uint32_t& phase, int* sOk, unsigned int* err) {
-  if (threadIdx.x == 0 && !mbar_wait(bar, phase)) {
+// An epilogue thread's shared-memory writes (the next A operand) and its
+// finished TMEM reads are handed to the MMA warp: proxy and tcgen05 fences,
+// then one arrival on the slot's "operand ready" barrier (512 per phase).
+__device__ __forceinline__ void operand_ready(uint32_t bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Bounded wait for a phase of an mbarrier; on expiry the status word and the
+// device error word record it.  False also when another thread has already
+// recorded an expiry, so every thread leaves the tile loop.
+__device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t& phase, volatile int* sOk, unsigned int* err) {
+  const bool ok = mbar_wait(bar, phase);
+  phase ^= 1u;
+  if (!ok) {
     *sOk = 0;
     atomicOr(err, HSC_DEVERR_TIMEOUT);
   }
-  __syncthreads();
-  phase ^= 1u;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  return *sOk != 0;
+  return ok && *sOk != 0;
 }
 
 // Reads accumulator columns c0 .. c0+31 of this thread's TMEM lane, applies
@@ -130,8 +145,8 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t trow, int c0, const flo
     uint32_t w[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const float x0 = silu_tc(__fadd_rn(__uint_as_float(v[8 * h + 2 * q]), bb[2 * q]));
-      const float x1 = silu_tc(__fadd_rn(__uint_as_float(v[8 * h + 2 * q + 1]), bb[2 * q + 1]));
+      const float x0 = silu_half(__fadd_rn(__uint_as_float(v[8 * h + 2 * q]), bb[2 * q]));
+      const float x1 = silu_half(__fadd_rn(__uint_as_float(v[8 * h + 2 * q + 1]), bb[2 * q + 1]));
       w[q] = pack_bf16x2(x0, x1);
     }
     const int col = c0 + 8 * h;
@@ -140,7 +155,7 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t trow, int c0, const flo
   }
 }
 
-__global__ void __launch_bounds__(kUpThreads, 1) upsample_tc_kernel(const UpArgs a) {
+__global__ void __launch_bounds__(kUpBlock, 1) upsample_tc_kernel(const UpArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -152,12 +167,15 @@ __global__ void __launch_bounds__(kUpThreads, 1) upsample_tc_kernel(const UpArgs
   float* sB1 = reinterpret_cast<float*>(base + kOffBias);
   float* sB2 = sB1 + kHidden;
   float* sB3 = sB2 + kHidden;
-  uint64_t* sBar = reinterpret_cast<uint64_t*>(base + kOffBar);  // [0], [1] the two slots, [2] drain
-  uint32_t* sTmem = reinterpret_cast<uint32_t*>(sBar + 3);
-  int* sOk = reinterpret_cast<int*>(sTmem + 1);
+  // mbarriers: [0], [1] MMA done per slot (1 arrival: the commit), [2], [3]
+  // operand ready per slot (512 arrivals), [4] drain
+  uint64_t* sBar = reinterpret_cast<uint64_t*>(base + kOffBar);
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(sBar + 5);
+  volatile int* sOk = reinterpret_cast<volatile int*>(sTmem + 1);
 
   const int t = threadIdx.x;
   const int warp = t >> 5;
+  const bool mma_warp = warp == kUpThreads / 32;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(sTmem)),
@@ -166,45 +184,46 @@ __global__ void __launch_bounds__(kUpThreads, 1) upsample_tc_kernel(const UpArgs
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(sBar)) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(sBar + 1)) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(sBar + 2)) : "memory");
+    for (int i = 0; i < 2; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(sBar + i)) : "memory");
+    for (int i = 2; i < 4; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(sBar + i)), "r"(kUpThreads) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(sBar + 4)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *sOk = 1;
   }
-  // weights as bf16 B operands ([N x K], K-major), biases as FP32
-  for (int idx = t; idx < kHidden * 16; idx += kUpThreads) {
+  // weights as bf16 B operands ([N x K], K-major), biases as FP32; the hidden
+  // layers' weights and biases at half scale (exact), so that accumulator +
+  // bias is x / 2 for the SiLU
+  for (int idx = t; idx < kHidden * 16; idx += kUpBlock) {
     const int r = idx >> 4, e = idx & 15;
     const float v = e < 3 ? __ldg(a.W1 + r * 3 + e) : 0.0f;
-    *reinterpret_cast<__nv_bfloat16*>(sW1 + kmajor_off(r, e)) = __float2bfloat16_rn(v);
+    *reinterpret_cast<__nv_bfloat16*>(sW1 + kmajor_off(r, e)) = __float2bfloat16_rn(__fmul_rn(0.5f, v));
   }
-  for (int idx = t; idx < kHidden * kHidden; idx += kUpThreads) {
+  for (int idx = t; idx < kHidden * kHidden; idx += kUpBlock) {
     const int r = idx / kHidden, i = idx - r * kHidden;
     *reinterpret_cast<__nv_bfloat16*>(sW2 + (i >> 4) * kBlockBytes + kmajor_off(r, i & 15)) =
-        __float2bfloat16_rn(__ldg(a.W2 + idx));
+        __float2bfloat16_rn(__fmul_rn(0.5f, __ldg(a.W2 + idx)));
   }
-  for (int idx = t; idx < 16 * kHidden; idx += kUpThreads) {
+  for (int idx = t; idx < 16 * kHidden; idx += kUpBlock) {
     const int r = idx / kHidden, i = idx - r * kHidden;
     const float v = r < a.k ? __ldg(a.W3 + r * kHidden + i) : 0.0f;
     *reinterpret_cast<__nv_bfloat16*>(sW3 + (i >> 4) * 512 + kmajor_off(r, i & 15)) = __float2bfloat16_rn(v);
   }
-  for (int idx = t; idx < kHidden; idx += kUpThreads) {
-    sB1[idx] = __ldg(a.b1 + idx);
-    sB2[idx] = __ldg(a.b2 + idx);
+  for (int idx = t; idx < kHidden; idx += kUpBlock) {
+    sB1[idx] = __fmul_rn(0.5f, __ldg(a.b1 + idx));
+    sB2[idx] = __fmul_rn(0.5f, __ldg(a.b2 + idx));
   }
   if (t < 16) sB3[t] = t < a.k ? __ldg(a.b3 + t) : 0.0f;
 
   const int quad = warp & 3;                 // TMEM lane quadrant of this warp
   const int row = quad * 32 + (t & 31);      // pixel row = TMEM lane
   const int c0 = (warp >> 2) * 32;           // this thread's 32 hidden columns
-  const uint32_t id_hidden = instr_desc_bf16(kUpRows, kHidden);
-  const uint32_t id_out = instr_desc_bf16(kUpRows, 16);
-  uint32_t phase[2] = {0u, 0u};
+  const int64_t tiles = (a.P + kUpRows - 1) / kUpRows;
+  const int64_t pairs = (tiles + 1) / 2;
 
   // Threads 0..255 feed the colours: thread t loads row t & 127 of slot t >> 7.
   const int feed_slot = t >> 7, feed_row = t & 127;
-  const int64_t tiles = (a.P + kUpRows - 1) / kUpRows;
-  const int64_t pairs = (tiles + 1) / 2;
   float cr = 0.0f, cg = 0.0f, cb = 0.0f;
   auto load_colour = [&](int64_t pair) {
     const int64_t p = (2 * pair + feed_slot) * kUpRows + feed_row;
@@ -219,80 +238,84 @@ __global__ void __launch_bounds__(kUpThreads, 1) upsample_tc_kernel(const UpArgs
   smem_to_mma_barrier();
   const uint32_t tm = *sTmem;  // TMEM base address, published by the barrier above
 
-  auto trow = [&](int slot) { return tm + (uint32_t)(256 * slot) + ((uint32_t)(quad * 32) << 16); };
-  auto wait = [&](int slot) { return wait_mma(smem_u32(sBar + slot), phase[slot], sOk, a.err); };
-  auto mma_hidden = [&](int slot, int layer) {  // layer 1 or 2 into the slot's first 128 columns
-    const uint32_t d = tm + (uint32_t)(256 * slot);
-    if (layer == 1) {
-      issue_mma(d, smem_desc(smem_u32(sA1 + slot * kBlockBytes), 128, 256), smem_desc(smem_u32(sW1), 128, 256),
-                id_hidden, 0);
-    } else {
-#pragma unroll
-      for (int kb = 0; kb < kKBlocks; ++kb)
-        issue_mma(d, smem_desc(smem_u32(sH + slot * kSlotH + kb * kBlockBytes), 128, 256),
-                  smem_desc(smem_u32(sW2 + kb * kBlockBytes), 128, 256), id_hidden, kb > 0);
-    }
-    commit(smem_u32(sBar + slot));
-  };
-  auto mma_out = [&](int slot) {
-    const uint32_t d = tm + (uint32_t)(256 * slot + 128);
-#pragma unroll
-    for (int kb = 0; kb < kKBlocks; ++kb)
-      issue_mma(d, smem_desc(smem_u32(sH + slot * kSlotH + kb * kBlockBytes), 128, 256),
-                smem_desc(smem_u32(sW3 + kb * 512), 128, 256), id_out, kb > 0);
-    commit(smem_u32(sBar + slot));
-  };
-  auto out = [&](int slot, int64_t pair) {
-    if (warp < 4) {  // the layer-3 columns, one warp per lane quadrant
-      uint32_t v[16];
-      TC_LD16(trow(slot) + 128u, v);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      const int64_t p = (2 * pair + slot) * kUpRows + row;
-      if (p < a.P) {
-        float* zo = a.z + p * a.k;
-#pragma unroll
-        for (int o = 0; o < 16; ++o)
-          if (o < a.k) zo[o] = __fadd_rn(__uint_as_float(v[o]), sB3[o]);
+  if (mma_warp) {
+    if ((t & 31) == 0) {
+      const uint32_t id_hidden = instr_desc_bf16(kUpRows, kHidden);
+      const uint32_t id_out = instr_desc_bf16(kUpRows, 16);
+      uint32_t rphase[2] = {0u, 0u};
+      bool ok = true;
+      for (int64_t pair = blockIdx.x; ok && pair < pairs; pair += gridDim.x) {
+        for (int layer = 1; ok && layer <= 3; ++layer) {
+          for (int slot = 0; slot < 2; ++slot) {
+            if (!wait_phase(smem_u32(sBar + 2 + slot), rphase[slot], sOk, a.err)) {
+              ok = false;
+              break;
+            }
+            const uint32_t d = tm + (uint32_t)(256 * slot) + (layer == 3 ? 128u : 0u);
+            if (layer == 1) {
+              issue_mma(d, smem_desc(smem_u32(sA1 + slot * kBlockBytes), 128, 256), smem_desc(smem_u32(sW1), 128, 256),
+                        id_hidden, 0);
+            } else {
+              const unsigned char* B = layer == 2 ? sW2 : sW3;
+              const uint32_t bstride = layer == 2 ? (uint32_t)kBlockBytes : 512u;
+#pragma unroll 1
+              for (int kb = 0; kb < kKBlocks; ++kb)
+                issue_mma(d, smem_desc(smem_u32(sH + slot * kSlotH + kb * kBlockBytes), 128, 256),
+                          smem_desc(smem_u32(B + kb * bstride), 128, 256), layer == 2 ? id_hidden : id_out, kb > 0);
+            }
+            commit(smem_u32(sBar + slot));
+          }
+        }
       }
+      // after an expired wait MMAs may still be running: drain them (bounded)
+      // before TMEM is freed
+      if (!ok) drain_mma(smem_u32(sBar + 4));
     }
-  };
-
-  for (int64_t pair = blockIdx.x; pair < pairs; pair += gridDim.x) {
-    // layer 1 A rows of both slots: the colours in bf16, K columns 0..2
-    if (t < 2 * kUpRows)
-      *reinterpret_cast<uint4*>(sA1 + feed_slot * kBlockBytes + kmajor_off(feed_row, 0)) =
-          make_uint4(pack_bf16x2(cr, cg), pack_bf16x2(cb, 0.0f), 0u, 0u);
-    smem_to_mma_barrier();
-    if (t == 0) {
-      mma_hidden(0, 1);
-      mma_hidden(1, 1);
+  } else {
+    auto trow = [&](int slot) { return tm + (uint32_t)(256 * slot) + ((uint32_t)(quad * 32) << 16); };
+    auto ready = [&](int slot) { operand_ready(smem_u32(sBar + 2 + slot)); };
+    uint32_t dphase[2] = {0u, 0u};
+    auto done = [&](int slot) { return wait_phase(smem_u32(sBar + slot), dphase[slot], sOk, a.err); };
+    auto out = [&](int slot, int64_t pair) {
+      if (warp < 4) {  // the layer-3 columns, one warp per lane quadrant
+        uint32_t v[16];
+        TC_LD16(trow(slot) + 128u, v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int64_t p = (2 * pair + slot) * kUpRows + row;
+        if (p < a.P) {
+          float* zo = a.z + p * a.k;
+#pragma unroll
+          for (int o = 0; o < 16; ++o)
+            if (o < a.k) zo[o] = __fadd_rn(__uint_as_float(v[o]), sB3[o]);
+        }
+      }
+    };
+    for (int64_t pair = blockIdx.x; pair < pairs; pair += gridDim.x) {
+      // layer 1 A rows of both slots: the colours in bf16, K columns 0..2
+      if (t < 2 * kUpRows)
+        *reinterpret_cast<uint4*>(sA1 + feed_slot * kBlockBytes + kmajor_off(feed_row, 0)) =
+            make_uint4(pack_bf16x2(cr, cg), pack_bf16x2(cb, 0.0f), 0u, 0u);
+      ready(0);
+      ready(1);
+      load_colour(pair + gridDim.x);  // the next pair's colours, in flight from here on
+      if (!done(0)) break;
+      hidden_epilogue(trow(0), c0, sB1, sH, row);
+      ready(0);
+      if (!done(1)) break;
+      hidden_epilogue(trow(1), c0, sB1, sH + kSlotH, row);
+      ready(1);
+      if (!done(0)) break;
+      hidden_epilogue(trow(0), c0, sB2, sH, row);  // h2 replaces h1 (layer 2 has finished reading it)
+      ready(0);
+      if (!done(1)) break;
+      hidden_epilogue(trow(1), c0, sB2, sH + kSlotH, row);
+      ready(1);
+      if (!done(0)) break;
+      out(0, pair);
+      if (!done(1)) break;
+      out(1, pair);
     }
-    load_colour(pair + gridDim.x);  // the next pair's colours, in flight from here on
-    if (!wait(0)) break;
-    hidden_epilogue(trow(0), c0, sB1, sH, row);
-    smem_to_mma_barrier();
-    if (t == 0) mma_hidden(0, 2);
-    if (!wait(1)) break;
-    hidden_epilogue(trow(1), c0, sB1, sH + kSlotH, row);
-    smem_to_mma_barrier();
-    if (t == 0) mma_hidden(1, 2);
-    if (!wait(0)) break;
-    hidden_epilogue(trow(0), c0, sB2, sH, row);  // h2 replaces h1 (layer 2 has finished reading it)
-    smem_to_mma_barrier();
-    if (t == 0) mma_out(0);
-    if (!wait(1)) break;
-    hidden_epilogue(trow(1), c0, sB2, sH + kSlotH, row);
-    smem_to_mma_barrier();
-    if (t == 0) mma_out(1);
-    if (!wait(0)) break;
-    out(0, pair);
-    if (!wait(1)) break;
-    out(1, pair);
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   }
-  // after an expired wait the other slot's MMAs may still be running: drain
-  // them (bounded) before TMEM is freed
-  if (t == 0 && !*sOk) drain_mma(smem_u32(sBar + 2));
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
@@ -338,6 +361,6 @@ extern "C" hsc_status hsc_upsample_rgb(hsc_ctx* ctx, const float* rgb, int64_t p
   const int64_t pairs = (tiles + 1) / 2;
   int64_t grid = ctx->sm_count;  // one CTA per SM (all 512 TMEM columns)
   if (grid > pairs) grid = pairs;
-  kern<<<(unsigned)grid, hsc::kUpThreads, hsc::kUpSmem, s>>>(a);
+  kern<<<(unsigned)grid, hsc::kUpBlock, hsc::kUpSmem, s>>>(a);
   return hsc::check_launch("upsample_tc_kernel");
 }

@@ -15,15 +15,18 @@
 // in shared memory (no-swizzle K-major layout).  The weights and biases of
 // the hidden layers are staged at half scale (exact in bf16 and FP32), so the
 // accumulator plus bias is already x/2 and SiLU(x) = x/2 (1 + tanh(x/2)) is
-// one FMA around the hardware tanh.  One CTA per SM works on two tiles at
-// once (two A buffers, two 256-column TMEM regions); the hand-offs are
+// one FMA around the hardware tanh.  One CTA per SM works on four tiles at
+// once (four A buffers, four 128-column TMEM regions; layer 3 reuses the
+// first 16 columns of its tile's region once layer 2 has been read); the
+// hand-offs are
 // mbarriers, not block barriers: every epilogue thread arrives on the slot's
 // "operand ready" barrier once its shared-memory writes and TMEM reads are
-// done and goes on with the other slot, and the MMA lane waits for all 512
-// arrivals before it issues, in the order
-//   MMA1(a) MMA1(b) | epi1(a) MMA2(a) | epi1(b) MMA2(b) | epi2(a) MMA3(a) |
-//   epi2(b) MMA3(b) | out(a) out(b),
-// so one tile's tensor-core work runs while the other tile's epilogue runs.
+// done and goes on with the next slot, and the MMA lane waits for all 512
+// arrivals before it issues; per layer the slots are taken in turn,
+//   MMA1(a..d) | epi1(a) MMA2(a) | epi1(b) MMA2(b) | ... | epi2(d) MMA3(d) |
+//   out(a..d),
+// so each tile's tensor-core work runs while the epilogue works on the other
+// three.
 // Every mbarrier wait is bounded; on expiry the kernel sets the timeout bit,
 // the MMA lane drains its MMAs (bounded), and TMEM is freed after a final
 // block barrier.
@@ -41,7 +44,8 @@ constexpr int kUpBlock = kUpThreads + 32;    // + the MMA warp
 constexpr int kUpRows = 128;            // MMA M, pixels per tile
 constexpr int kHidden = HSC_UPSAMPLE_HIDDEN;
 constexpr int kKBlocks = kHidden / 16;  // K = 16 steps of the hidden layers
-constexpr unsigned kUpTmemCols = 512;   // per tile slot s: [256 s, +128) layers 1-2, [256 s + 128, +16) layer 3
+constexpr int kSlots = 4;              // tiles in flight per CTA
+constexpr unsigned kUpTmemCols = 512;   // slot s: columns [128 s, +128) for every layer (layer 3 in the first 16)
 constexpr int kBlockBytes = kUpRows * 16 * 2;  // one [128 x 16] bf16 K-block
 
 struct UpArgs {
@@ -62,12 +66,14 @@ struct UpArgs {
 constexpr int kOffW1 = 0;                                  // [128 x 16] bf16
 constexpr int kOffW2 = kOffW1 + kBlockBytes;               // 8 x [128 x 16]
 constexpr int kOffW3 = kOffW2 + kKBlocks * kBlockBytes;    // 8 x [16 x 16]
-constexpr int kOffA1 = kOffW3 + kKBlocks * 512;            // 2 slots x [128 x 16]
-constexpr int kOffH = kOffA1 + 2 * kBlockBytes;            // 2 slots x 8 x [128 x 16]
+constexpr int kOffA1 = kOffW3 + kKBlocks * 512;            // kSlots x [128 x 16]
+constexpr int kOffH = kOffA1 + kSlots * kBlockBytes;       // kSlots x 8 x [128 x 16]
 constexpr int kSlotH = kKBlocks * kBlockBytes;
-constexpr int kOffBias = kOffH + 2 * kSlotH;               // b1, b2 (128 each), b3 (16)
-constexpr int kOffBar = kOffBias + (2 * kHidden + 16) * 4; // five mbarriers, TMEM address, status
-constexpr int kUpSmem = kOffBar + 64 + 1024;               // + alignment slack
+constexpr int kOffBias = kOffH + kSlots * kSlotH;          // b1, b2 (128 each), b3 (16)
+constexpr int kOffBar = kOffBias + (2 * kHidden + 16) * 4; // 2 kSlots + 1 mbarriers, TMEM address, status
+constexpr int kUpSmem = kOffBar + 128 + 1024;              // + alignment slack
+static_assert(kSlots * kUpRows == kUpThreads, "every epilogue thread feeds one colour row");
+static_assert(kSlots * 128 <= 512, "the slots' accumulators fit the TMEM");
 
 __device__ __forceinline__ float tanh_approx(float x) {
   float y;
@@ -167,10 +173,10 @@ __global__ void __launch_bounds__(kUpBlock, 1) upsample_tc_kernel(const UpArgs a
   float* sB1 = reinterpret_cast<float*>(base + kOffBias);
   float* sB2 = sB1 + kHidden;
   float* sB3 = sB2 + kHidden;
-  // mbarriers: [0], [1] MMA done per slot (1 arrival: the commit), [2], [3]
-  // operand ready per slot (512 arrivals), [4] drain
+  // mbarriers: [s] MMA done of slot s (1 arrival: the commit), [kSlots + s]
+  // operand ready of slot s (512 arrivals), [2 kSlots] drain
   uint64_t* sBar = reinterpret_cast<uint64_t*>(base + kOffBar);
-  uint32_t* sTmem = reinterpret_cast<uint32_t*>(sBar + 5);
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(sBar + 2 * kSlots + 1);
   volatile int* sOk = reinterpret_cast<volatile int*>(sTmem + 1);
 
   const int t = threadIdx.x;
@@ -184,11 +190,12 @@ __global__ void __launch_bounds__(kUpBlock, 1) upsample_tc_kernel(const UpArgs a
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (t == 0) {
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < kSlots; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(sBar + i)) : "memory");
-    for (int i = 2; i < 4; ++i)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(sBar + i)), "r"(kUpThreads) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(sBar + 4)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(sBar + kSlots + i)), "r"(kUpThreads)
+                   : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(sBar + 2 * kSlots)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *sOk = 1;
   }
@@ -220,20 +227,20 @@ __global__ void __launch_bounds__(kUpBlock, 1) upsample_tc_kernel(const UpArgs a
   const int row = quad * 32 + (t & 31);      // pixel row = TMEM lane
   const int c0 = (warp >> 2) * 32;           // this thread's 32 hidden columns
   const int64_t tiles = (a.P + kUpRows - 1) / kUpRows;
-  const int64_t pairs = (tiles + 1) / 2;
+  const int64_t groups = (tiles + kSlots - 1) / kSlots;   // kSlots tiles per group
 
-  // Threads 0..255 feed the colours: thread t loads row t & 127 of slot t >> 7.
+  // Epilogue thread t feeds the colour of row t & 127 of slot t >> 7.
   const int feed_slot = t >> 7, feed_row = t & 127;
   float cr = 0.0f, cg = 0.0f, cb = 0.0f;
-  auto load_colour = [&](int64_t pair) {
-    const int64_t p = (2 * pair + feed_slot) * kUpRows + feed_row;
-    const bool ok = t < 2 * kUpRows && pair < pairs && p < a.P;
+  auto load_colour = [&](int64_t group) {
+    const int64_t p = (kSlots * group + feed_slot) * kUpRows + feed_row;
+    const bool ok = t < kUpThreads && group < groups && p < a.P;
     cr = ok ? __ldg(a.rgb + 3 * p) : 0.0f;
     cg = ok ? __ldg(a.rgb + 3 * p + 1) : 0.0f;
     cb = ok ? __ldg(a.rgb + 3 * p + 2) : 0.0f;
   };
   load_colour(blockIdx.x);
-  if (t < 2 * kUpRows)  // the A1 rows' K columns 8..15 stay zero
+  if (t < kUpThreads)  // the A1 rows' K columns 8..15 stay zero
     *reinterpret_cast<uint4*>(sA1 + feed_slot * kBlockBytes + kmajor_off(feed_row, 8)) = make_uint4(0u, 0u, 0u, 0u);
   smem_to_mma_barrier();
   const uint32_t tm = *sTmem;  // TMEM base address, published by the barrier above
@@ -242,16 +249,16 @@ __global__ void __launch_bounds__(kUpBlock, 1) upsample_tc_kernel(const UpArgs a
     if ((t & 31) == 0) {
       const uint32_t id_hidden = instr_desc_bf16(kUpRows, kHidden);
       const uint32_t id_out = instr_desc_bf16(kUpRows, 16);
-      uint32_t rphase[2] = {0u, 0u};
+      uint32_t rphase[kSlots] = {};
       bool ok = true;
-      for (int64_t pair = blockIdx.x; ok && pair < pairs; pair += gridDim.x) {
+      for (int64_t group = blockIdx.x; ok && group < groups; group += gridDim.x) {
         for (int layer = 1; ok && layer <= 3; ++layer) {
-          for (int slot = 0; slot < 2; ++slot) {
-            if (!wait_phase(smem_u32(sBar + 2 + slot), rphase[slot], sOk, a.err)) {
+          for (int slot = 0; slot < kSlots; ++slot) {
+            if (!wait_phase(smem_u32(sBar + kSlots + slot), rphase[slot], sOk, a.err)) {
               ok = false;
               break;
             }
-            const uint32_t d = tm + (uint32_t)(256 * slot) + (layer == 3 ? 128u : 0u);
+            const uint32_t d = tm + (uint32_t)(128 * slot);
             if (layer == 1) {
               issue_mma(d, smem_desc(smem_u32(sA1 + slot * kBlockBytes), 128, 256), smem_desc(smem_u32(sW1), 128, 256),
                         id_hidden, 0);
@@ -269,19 +276,19 @@ __global__ void __launch_bounds__(kUpBlock, 1) upsample_tc_kernel(const UpArgs a
       }
       // after an expired wait MMAs may still be running: drain them (bounded)
       // before TMEM is freed
-      if (!ok) drain_mma(smem_u32(sBar + 4));
+      if (!ok) drain_mma(smem_u32(sBar + 2 * kSlots));
     }
   } else {
-    auto trow = [&](int slot) { return tm + (uint32_t)(256 * slot) + ((uint32_t)(quad * 32) << 16); };
-    auto ready = [&](int slot) { operand_ready(smem_u32(sBar + 2 + slot)); };
-    uint32_t dphase[2] = {0u, 0u};
+    auto trow = [&](int slot) { return tm + (uint32_t)(128 * slot) + ((uint32_t)(quad * 32) << 16); };
+    auto ready = [&](int slot) { operand_ready(smem_u32(sBar + kSlots + slot)); };
+    uint32_t dphase[kSlots] = {};
     auto done = [&](int slot) { return wait_phase(smem_u32(sBar + slot), dphase[slot], sOk, a.err); };
-    auto out = [&](int slot, int64_t pair) {
+    auto out = [&](int slot, int64_t group) {
       if (warp < 4) {  // the layer-3 columns, one warp per lane quadrant
         uint32_t v[16];
-        TC_LD16(trow(slot) + 128u, v);
+        TC_LD16(trow(slot), v);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const int64_t p = (2 * pair + slot) * kUpRows + row;
+        const int64_t p = (kSlots * group + slot) * kUpRows + row;
         if (p < a.P) {
           float* zo = a.z + p * a.k;
 #pragma unroll
@@ -290,30 +297,38 @@ __global__ void __launch_bounds__(kUpBlock, 1) upsample_tc_kernel(const UpArgs a
         }
       }
     };
-    for (int64_t pair = blockIdx.x; pair < pairs; pair += gridDim.x) {
-      // layer 1 A rows of both slots: the colours in bf16, K columns 0..2
-      if (t < 2 * kUpRows)
-        *reinterpret_cast<uint4*>(sA1 + feed_slot * kBlockBytes + kmajor_off(feed_row, 0)) =
-            make_uint4(pack_bf16x2(cr, cg), pack_bf16x2(cb, 0.0f), 0u, 0u);
-      ready(0);
-      ready(1);
-      load_colour(pair + gridDim.x);  // the next pair's colours, in flight from here on
-      if (!done(0)) break;
-      hidden_epilogue(trow(0), c0, sB1, sH, row);
-      ready(0);
-      if (!done(1)) break;
-      hidden_epilogue(trow(1), c0, sB1, sH + kSlotH, row);
-      ready(1);
-      if (!done(0)) break;
-      hidden_epilogue(trow(0), c0, sB2, sH, row);  // h2 replaces h1 (layer 2 has finished reading it)
-      ready(0);
-      if (!done(1)) break;
-      hidden_epilogue(trow(1), c0, sB2, sH + kSlotH, row);
-      ready(1);
-      if (!done(0)) break;
-      out(0, pair);
-      if (!done(1)) break;
-      out(1, pair);
+    bool ok = true;
+    for (int64_t group = blockIdx.x; ok && group < groups; group += gridDim.x) {
+      // layer 1 A rows of every slot: the colours in bf16, K columns 0..2
+      *reinterpret_cast<uint4*>(sA1 + feed_slot * kBlockBytes + kmajor_off(feed_row, 0)) =
+          make_uint4(pack_bf16x2(cr, cg), pack_bf16x2(cb, 0.0f), 0u, 0u);
+#pragma unroll 1
+      for (int slot = 0; slot < kSlots; ++slot) ready(slot);
+      load_colour(group + gridDim.x);  // the next group's colours, in flight from here on
+      // the two hidden layers: while the tensor core runs one slot's MMA, the
+      // epilogue works on the other slots
+#pragma unroll 1
+      for (int layer = 0; ok && layer < 2; ++layer) {
+        const float* bias = layer == 0 ? sB1 : sB2;
+#pragma unroll 1
+        for (int slot = 0; slot < kSlots; ++slot) {
+          if (!done(slot)) {
+            ok = false;
+            break;
+          }
+          // h2 replaces h1 in the slot's buffer: layer 2 has finished reading it
+          hidden_epilogue(trow(slot), c0, bias, sH + slot * kSlotH, row);
+          ready(slot);
+        }
+      }
+#pragma unroll 1
+      for (int slot = 0; ok && slot < kSlots; ++slot) {
+        if (!done(slot)) {
+          ok = false;
+          break;
+        }
+        out(slot, group);
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -358,9 +373,9 @@ extern "C" hsc_status hsc_upsample_rgb(hsc_ctx* ctx, const float* rgb, int64_t p
   auto kern = hsc::upsample_tc_kernel;
   HSC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, hsc::kUpSmem));
   const int64_t tiles = (pixels + hsc::kUpRows - 1) / hsc::kUpRows;
-  const int64_t pairs = (tiles + 1) / 2;
+  const int64_t groups = (tiles + hsc::kSlots - 1) / hsc::kSlots;
   int64_t grid = ctx->sm_count;  // one CTA per SM (all 512 TMEM columns)
-  if (grid > pairs) grid = pairs;
+  if (grid > groups) grid = groups;
   kern<<<(unsigned)grid, hsc::kUpBlock, hsc::kUpSmem, s>>>(a);
   return hsc::check_launch("upsample_tc_kernel");
 }

@@ -821,9 +821,36 @@ def upsample_rows(args, hsc, ctx, dev, timed):
     flops = P * 2 * (3 * 128 + 128 * 128 + 128 * 6)          # algorithmic
     mma_flops = P * 2 * (16 * 128 + 128 * 128 + 128 * 16)    # as issued (K and N padded to 16)
     del rgb, z
+    # the epilogue's bound: one hardware tanh per hidden value (2 x 128 per
+    # pixel) at the MUFU rate measured by the library's tanh probe (best of 10)
+    sink = torch.empty(8 * torch.cuda.get_device_properties(dev).multi_processor_count * 256, device=dev)
+    best = 0.0
+    for _ in range(11):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ops = hsc.hsc_tanh_peak_probe(ctx, sink, 4096)
+        b.record()
+        b.synchronize()
+        best = max(best, ops / (a.elapsed_time(b) * 1e-3))
+    hsc.hsc_sync(ctx)
+    mufu_ms = 2 * 128 * P / best * 1e3
+    bf16_peak = _measured_peak("bf16_tflops", 1900.0)
     return {"upsample_rgb_4k": {"ms": m, "Mpx_per_s": P / (m * 1e-3) / 1e6,
                                 "TFLOP_per_s": flops / (m * 1e-3) / 1e12,
-                                "tensor_TFLOP_per_s_issued": mma_flops / (m * 1e-3) / 1e12}}
+                                "tensor_TFLOP_per_s_issued": mma_flops / (m * 1e-3) / 1e12,
+                                "frac_of_bf16_peak": flops / (m * 1e-3) / 1e12 / bf16_peak,
+                                "tanh_probe_G_per_s": best / 1e9, "mufu_bound_ms": mufu_ms,
+                                "frac_of_mufu_bound": mufu_ms / m}}
+
+
+def _measured_peak(key: str, fallback: float) -> float:
+    """A peak from MEASURED_PEAKS.json (written on the GPU machine before the
+    run), else the stated fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)[key])
+    except (OSError, ValueError, KeyError):
+        return fallback
 
 
 def pathtrace_rows(args, hsc, ctx, dev, timed):

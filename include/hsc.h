@@ -168,6 +168,16 @@ HSC_API hsc_status hsc_force_launch_config(hsc_ctx* ctx, int ppt, int block, int
  *   measures on `stream`.  1 <= iters <= 2^24.                              */
 HSC_API hsc_status hsc_fp32_peak_probe(hsc_ctx* ctx, int ctas, int iters, float* sink, int64_t* lane_ops_out,
                                        void* stream);
+/* MUFU tanh rate probe (measurement only; the upsampling network's SiLU is
+ * one hardware tanh per hidden value, so the MUFU rate bounds its epilogue).
+ * One launch of `ctas` CTAs of 256 threads (ctas <= 0: 8 per SM), each thread
+ * running `iters` iterations of 32 register-only tanh.approx operations (8
+ * independent recurrences a <- tanh(a + 1/4)).
+ *   sink: device float32, at least ctas x 256 values (each thread's sum).
+ *   tanh_ops_out: host, may be null; receives ctas x 256 x iters x 32.
+ *   1 <= iters <= 2^24.                                                      */
+HSC_API hsc_status hsc_tanh_peak_probe(hsc_ctx* ctx, int ctas, int iters, float* sink, int64_t* tanh_ops_out,
+                                       void* stream);
 
 /* ----------------------------------------------------- colour projection */
 

@@ -28,6 +28,30 @@ __global__ void __launch_bounds__(kProbeThreads) fp32_probe_kernel(int iters, fl
   sink[(size_t)blockIdx.x * kProbeThreads + threadIdx.x] = t;
 }
 
+// MUFU tanh rate probe: the SiLU epilogue of the upsampling network is one
+// hardware tanh per hidden value, so its throughput bound is the MUFU rate.
+// Each thread runs kProbeChains independent recurrences a <- tanh(a + s).
+__global__ void __launch_bounds__(kProbeThreads) tanh_probe_kernel(int iters, float s, float* sink) {
+  float a[kProbeChains];
+#pragma unroll
+  for (int c = 0; c < kProbeChains; ++c) a[c] = threadIdx.x * 1e-3f + c * 0.1f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < kProbeUnroll; ++u) {
+#pragma unroll
+      for (int c = 0; c < kProbeChains; ++c) {
+        float y;
+        asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(a[c] + s));
+        a[c] = y;
+      }
+    }
+  }
+  float t = 0.0f;
+#pragma unroll
+  for (int c = 0; c < kProbeChains; ++c) t += a[c];
+  sink[(size_t)blockIdx.x * kProbeThreads + threadIdx.x] = t;
+}
+
 }  // namespace
 
 extern "C" {
@@ -44,6 +68,20 @@ hsc_status hsc_fp32_peak_probe(hsc_ctx* ctx, int ctas, int iters, float* sink, i
     *lane_ops_out = (int64_t)ctas * kProbeThreads * iters * (kProbeChains * kProbeUnroll);
   fp32_probe_kernel<<<ctas, kProbeThreads, 0, hsc::as_stream(stream)>>>(iters, 0.999f, 1e-3f, sink);
   return hsc::check_launch("fp32_probe_kernel");
+}
+
+hsc_status hsc_tanh_peak_probe(hsc_ctx* ctx, int ctas, int iters, float* sink, int64_t* tanh_ops_out, void* stream) {
+  hsc::clear_error();
+  HSC_CHECK_CTX(ctx);
+  if (ctas <= 0) ctas = 8 * ctx->sm_count;
+  HSC_REQUIRE(ctas <= (1 << 20), "ctas=%d too large", ctas);
+  HSC_REQUIRE(iters >= 1 && iters <= (1 << 24), "iters=%d out of range [1, 2^24]", iters);
+  HSC_REQUIRE(sink && hsc::aligned(sink, 4), "sink is null or misaligned");
+  HSC_GUARD(ctx);
+  if (tanh_ops_out)
+    *tanh_ops_out = (int64_t)ctas * kProbeThreads * iters * (kProbeChains * kProbeUnroll);
+  tanh_probe_kernel<<<ctas, kProbeThreads, 0, hsc::as_stream(stream)>>>(iters, 0.25f, sink);
+  return hsc::check_launch("tanh_probe_kernel");
 }
 
 }  // extern "C"

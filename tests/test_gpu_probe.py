@@ -38,3 +38,24 @@ def test_probe_rejects_bad_arguments():
     with pytest.raises(Exception):
         hsc.hsc_fp32_peak_probe(ctx, sink, 4, ctas=2)    # sink too small
     ctx.close()
+
+
+def test_tanh_probe_counts_and_values():
+    # each of the 8 recurrences a <- tanh(a + 1/4) (hardware tanh, about
+    # 2^-11 relative) stays within 1e-3 of the FP64 recurrence: tanh is a
+    # contraction, so the per-step errors do not grow
+    import paper_2602_18741_gb300 as hsc
+    ctx = hsc.Context(0)
+    dev = torch.device("cuda:0")
+    ctas, iters = 2, 3
+    sink = torch.full((ctas * 256,), float("nan"), device=dev)
+    ops = hsc.hsc_tanh_peak_probe(ctx, sink, iters, ctas=ctas)
+    hsc.hsc_sync(ctx)
+    assert ops == ctas * 256 * iters * 32
+    tid = np.tile(np.arange(256), ctas)
+    a = (np.float32(tid * 1e-3)[:, None] + np.float32(np.arange(8) * 0.1)[None, :]).astype(np.float64)
+    for _ in range(4 * iters):
+        a = np.tanh(a + 0.25)
+    got = sink.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - a.sum(axis=1))) < 8e-3
+    ctx.close()

@@ -172,12 +172,14 @@ HSC_API hsc_status hsc_fp32_peak_probe(hsc_ctx* ctx, int ctas, int iters, float*
  * one hardware tanh per hidden value, so the MUFU rate bounds its epilogue).
  * One launch of `ctas` CTAs of 256 threads (ctas <= 0: 8 per SM), each thread
  * running `iters` iterations of 32 register-only tanh.approx operations (8
- * independent recurrences a <- tanh(a + 1/4)).
+ * independent recurrences a <- tanh(a + 1/4)): packed = 0 in FP32
+ * (tanh.approx.f32), packed = 1 on f16 pairs (tanh.approx.f16x2, the form the
+ * upsampler uses; two results per operation).
  *   sink: device float32, at least ctas x 256 values (each thread's sum).
- *   tanh_ops_out: host, may be null; receives ctas x 256 x iters x 32.
- *   1 <= iters <= 2^24.                                                      */
-HSC_API hsc_status hsc_tanh_peak_probe(hsc_ctx* ctx, int ctas, int iters, float* sink, int64_t* tanh_ops_out,
-                                       void* stream);
+ *   tanh_ops_out: host, may be null; receives the tanh results of the launch,
+ *   ctas x 256 x iters x 32 (x 2 when packed).  1 <= iters <= 2^24.        */
+HSC_API hsc_status hsc_tanh_peak_probe(hsc_ctx* ctx, int ctas, int iters, int packed, float* sink,
+                                       int64_t* tanh_ops_out, void* stream);
 
 /* ----------------------------------------------------- colour projection */
 
@@ -402,8 +404,13 @@ HSC_API hsc_status hsc_shade_frames(hsc_ctx* ctx, const hsc_frame* frames, int c
  *   W2: device 128 x 128 (row = output unit), b2: 128, W3: device k x 128,
  *   b3: k, all float32;  z_out: device P x k float32;  1 <= k <= 16.
  * Precision: the colour, the weights and both hidden activations are rounded
- * to bf16 for the tensor cores, products accumulate in FP32, biases are FP32,
- * and SiLU uses the hardware tanh approximation (silu(x) = x/2 (1 + tanh(x/2))).
+ * to f16 for the tensor cores and products accumulate in FP32; each bias b
+ * enters its layer's product as the f16 pair hi = f16(b), lo = f16(b - hi)
+ * (b to about 2^-22 relative); SiLU is FP32 through the hardware tanh
+ * approximation (silu(x) = x/2 (1 + tanh(x/2))), its result rounded to f16.
+ * Range: f16 holds magnitudes below 65504, so colours, weights, biases and
+ * hidden activations must stay below that; beyond it they overflow to
+ * infinity.
  * No scratch memory; asynchronous on `stream`.                              */
 HSC_API hsc_status hsc_upsample_rgb(hsc_ctx* ctx, const float* rgb, int64_t pixels, const float* W1,
                                     const float* b1, const float* W2, const float* b2, const float* W3,

@@ -84,7 +84,7 @@ _SIGS = {
     "hsc_tune_load": ([_vp, ctypes.c_char_p], _i32),
     "hsc_force_launch_config": ([_vp, _i32, _i32, _i32, _i32, _i32], _i32),
     "hsc_fp32_peak_probe": ([_vp, _i32, _i32, _vp, ctypes.POINTER(_i64), _vp], _i32),
-    "hsc_tanh_peak_probe": ([_vp, _i32, _i32, _vp, ctypes.POINTER(_i64), _vp], _i32),
+    "hsc_tanh_peak_probe": ([_vp, _i32, _i32, _i32, _vp, ctypes.POINTER(_i64), _vp], _i32),
     "hsc_cmf_weights": ([_vp, _i32, _f32, _f32, _vp, _vp], _i32),
     "hsc_fold_xyz": ([_vp, _vp, _vp, _i32, _i32, _vp, _vp], _i32),
     "hsc_encode": ([_vp, _vp, _i32, _i32, _vp, _i32, _vp, _i32, _vp], _i32),
@@ -266,14 +266,17 @@ def hsc_fp32_peak_probe(ctx: Context, sink: torch.Tensor, iters: int, ctas: int 
     return int(ops.value)
 
 
-def hsc_tanh_peak_probe(ctx: Context, sink: torch.Tensor, iters: int, ctas: int = 0, stream=None) -> int:
-    """One launch of the MUFU tanh probe; returns its tanh operations.
-    sink: device float32 with at least ctas x 256 elements (ctas <= 0: 8 per SM)."""
+def hsc_tanh_peak_probe(ctx: Context, sink: torch.Tensor, iters: int, ctas: int = 0, packed: bool = False,
+                        stream=None) -> int:
+    """One launch of the MUFU tanh probe; returns its tanh results (FP32, or
+    f16 pairs when packed).  sink: device float32 with at least ctas x 256
+    elements (ctas <= 0: 8 per SM)."""
     n = int(ctas) if ctas > 0 else 8 * torch.cuda.get_device_properties(sink.device).multi_processor_count
     if sink.dtype != torch.float32 or sink.numel() < n * 256 or not sink.is_cuda:
         raise ValueError("sink must be a device float32 tensor of at least ctas x 256 elements")
     ops = ctypes.c_int64(0)
-    _check(_lib.hsc_tanh_peak_probe(ctx.handle, n, int(iters), _ptr(sink), ctypes.byref(ops), _stream(stream)))
+    _check(_lib.hsc_tanh_peak_probe(ctx.handle, n, int(iters), int(packed), _ptr(sink), ctypes.byref(ops),
+                                    _stream(stream)))
     return int(ops.value)
 
 

@@ -33,6 +33,11 @@ __host__ __device__ constexpr uint32_t instr_desc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// The same with A = B = F16 (format code 0 in bits 7-9 and 10-12).
+__host__ __device__ constexpr uint32_t instr_desc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 // Byte offset of element (row r, k-element e) in the no-swizzle K-major
 // canonical layout with K = 16 bf16: core matrices of 8 rows x 16 bytes,
 // the two K-halves 128 bytes apart (LBO), 8-row groups 256 bytes apart (SBO).

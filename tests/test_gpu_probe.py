@@ -59,3 +59,27 @@ def test_tanh_probe_counts_and_values():
     got = sink.cpu().numpy().astype(np.float64)
     assert np.max(np.abs(got - a.sum(axis=1))) < 8e-3
     ctx.close()
+
+
+def test_tanh_probe_packed_f16_pairs():
+    # the f16x2 form: two recurrences per register (the second starts 0.05
+    # higher), f16 rounding each step (2^-11) plus the approximation; the
+    # contraction keeps the sum of the 16 values within 3e-2 of FP64
+    import paper_2602_18741_gb300 as hsc
+    ctx = hsc.Context(0)
+    dev = torch.device("cuda:0")
+    ctas, iters = 2, 3
+    sink = torch.full((ctas * 256,), float("nan"), device=dev)
+    ops = hsc.hsc_tanh_peak_probe(ctx, sink, iters, ctas=ctas, packed=True)
+    hsc.hsc_sync(ctx)
+    assert ops == ctas * 256 * iters * 32 * 2
+    tid = np.tile(np.arange(256), ctas)
+    lo = (np.float32(tid * 1e-3)[:, None] + np.float32(np.arange(8) * 0.1)[None, :]).astype(np.float64)
+    a = np.concatenate([lo, lo + 0.05], axis=1)
+    for _ in range(4 * iters):
+        a = np.tanh(a + 0.25)
+    got = sink.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - a.sum(axis=1))) < 3e-2
+    with pytest.raises(Exception):
+        hsc.hsc_tanh_peak_probe(ctx, sink, iters, ctas=ctas, packed=2)
+    ctx.close()

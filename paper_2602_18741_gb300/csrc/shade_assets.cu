@@ -55,16 +55,43 @@ __device__ __forceinline__ float thread_code(const float* __restrict__ e, const 
   return v[0];
 }
 
+// The same sum with E and the spectrum read from shared memory (the staged
+// form): the same operations in the same order, so the same bits.
+__device__ __forceinline__ float thread_code_smem(const float* e, const float* s, int n) {
+  float v[32];
+#pragma unroll
+  for (int t = 0; t < 32; ++t) v[t] = 0.0f;
+  for (int i0 = 0; i0 < n; i0 += 32) {
+#pragma unroll
+    for (int t = 0; t < 32; ++t)
+      if (i0 + t < n) v[t] = __fmaf_rn(e[i0 + t], s[i0 + t], v[t]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int t = 0; t < o; ++t) v[t] = __fadd_rn(v[t], v[t + o]);
+  return v[0];
+}
+
 __device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
-template <int KC, bool SEC, bool RGB>
+// STAGE: E, the light spectra and the material spectra are first copied into
+// shared memory with coalesced loads (one pass over a few KB), and the codes
+// are summed from there, instead of every code reading its 2 n operands
+// from global memory.
+template <int KC, bool SEC, bool RGB, bool STAGE>
 __global__ void __launch_bounds__(kAssetBlock) shade_assets_kernel(const AssetArgs A) {
   constexpr int F4 = LightStage<KC, 1>::F4;
-  extern __shared__ float4 s_light[];  // L x F4 staged lights, then n_mat x KC material codes
+  // L x F4 staged lights, then n_mat x KC material codes, then (STAGE) E
+  // (KC x n), the light spectra (L x n) and the material spectra (n_mat x n)
+  extern __shared__ float4 s_light[];
   __shared__ float s_M[3 * KC];
   const ShadeArgs& a = A.a;
   float* sl = reinterpret_cast<float*>(s_light);
   float* s_mat = reinterpret_cast<float*>(s_light + a.L * F4);
+  float* s_E = s_mat + a.n_mat * KC;
+  float* s_spd = s_E + KC * A.n;
+  float* s_mspec = s_spd + a.L * A.n;
   // the tile's G-buffer lines into L1 now, so that the shading's loads after
   // the encode find them there (the encode's own loads run meanwhile)
 #pragma unroll
@@ -87,15 +114,23 @@ __global__ void __launch_bounds__(kAssetBlock) shade_assets_kernel(const AssetAr
     if (j < 3) sl[i] = __ldg(a.lpos + 3 * l + j);
     else if (j >= 3 + KC) sl[i] = 0.0f;
   }
+  if constexpr (STAGE) {
+    for (int i = threadIdx.x; i < KC * A.n; i += kAssetBlock) s_E[i] = __ldg(A.E + i);
+    for (int i = threadIdx.x; i < a.L * A.n; i += kAssetBlock) s_spd[i] = __ldg(A.spd + i);
+    for (int i = threadIdx.x; i < a.n_mat * A.n; i += kAssetBlock) s_mspec[i] = __ldg(A.mats + i);
+    __syncthreads();
+  }
   // one code value per thread: the light codes, then the material codes
   for (int w = threadIdx.x; w < (a.L + a.n_mat) * KC; w += kAssetBlock) {
     const int row = w / KC, c = w - row * KC;
     if (row < a.L) {
-      const float z = thread_code(A.E + (int64_t)c * A.n, A.spd + (int64_t)row * A.n, A.n);
+      const float z = STAGE ? thread_code_smem(s_E + c * A.n, s_spd + row * A.n, A.n)
+                            : thread_code(A.E + (int64_t)c * A.n, A.spd + (int64_t)row * A.n, A.n);
       sl[row * F4 * 4 + 3 + c] = __fmul_rn(z, __fmul_rn(__ldg(a.linten + row), kInvPi));
     } else {
       const int m = row - a.L;
-      s_mat[m * KC + c] = thread_code(A.E + (int64_t)c * A.n, A.mats + (int64_t)m * A.n, A.n);
+      s_mat[m * KC + c] = STAGE ? thread_code_smem(s_E + c * A.n, s_mspec + m * A.n, A.n)
+                                : thread_code(A.E + (int64_t)c * A.n, A.mats + (int64_t)m * A.n, A.n);
     }
   }
   stage_decode_matrix<KC, kAssetBlock>(a, s_M);
@@ -103,11 +138,17 @@ __global__ void __launch_bounds__(kAssetBlock) shade_assets_kernel(const AssetAr
   shade_tile<KC, kAssetPPT, SEC, kAssetBlock, 1, RGB>(a, blockIdx.x, s_light, true, s_M, s_mat);
 }
 
+constexpr size_t kAssetStageBytes = 48 * 1024;  // shared memory up to which the assets are staged
+
 template <int KC, bool SEC, bool RGB>
 hsc_status launch_assets_t(const AssetArgs& A, cudaStream_t s) {
   constexpr int F4 = LightStage<KC, 1>::F4;
   const size_t smem = (size_t)A.a.L * F4 * sizeof(float4) + (size_t)A.a.n_mat * KC * sizeof(float);
-  shade_assets_kernel<KC, SEC, RGB><<<(unsigned)A.a.tiles, kAssetBlock, smem, s>>>(A);
+  const size_t staged = smem + sizeof(float) * (size_t)A.n * (KC + A.a.L + A.a.n_mat);
+  if (staged <= kAssetStageBytes)
+    shade_assets_kernel<KC, SEC, RGB, true><<<(unsigned)A.a.tiles, kAssetBlock, staged, s>>>(A);
+  else
+    shade_assets_kernel<KC, SEC, RGB, false><<<(unsigned)A.a.tiles, kAssetBlock, smem, s>>>(A);
   return check_launch("shade_assets_kernel");
 }
 

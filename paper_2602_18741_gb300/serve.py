@@ -308,35 +308,50 @@ class GpuBackend:
         self.parts: Dict[str, float] = {}
 
     def reserve(self, requests, per_size: int = 16):
-        """Prepare before the first arrival: allocate `per_size` output buffers
-        of every request size, the descriptor ring, and run one request of
-        every (k, n) so that its kernels are loaded.  A device allocation or
-        the first launch of a kernel inside the serving loop can wait for all
-        queued work, which would stall every request behind it."""
+        """Prepare before the first arrival: the descriptor ring, a few
+        requests of every (k, n) through the real path so that their kernels
+        are loaded, and `per_size` output buffers of every request size.  A
+        device allocation or the first launch of a kernel inside the serving
+        loop can wait for all queued work, which would stall every request
+        behind it."""
         import torch
+        if self.mode == "latent":
+            self.hsc.hsc_shade_frames(self.ctx, [], stream=self.streams[0])   # allocates the descriptor ring
+        # the first launch of a kernel loads its code, which can wait for the
+        # device as well.  Kernels are specialised by light count too (all
+        # lights in one shared-memory stage or not), so each (k, n) runs with
+        # its fewest and its most lights
+        firsts = {}
+        for r in requests:
+            lo, hi = firsts.get((r.k, r.n), (r, r))
+            firsts[(r.k, r.n)] = (r if r.lights < lo.lights else lo, r if r.lights > hi.lights else hi)
+        warm = {id(x): x for pair in firsts.values() for x in pair}
+        handles = [self.launch([r]) for r in warm.values()]
+        torch.cuda.synchronize(self.sc.dev)
+        for _, outs in handles:
+            if self.keep:   # warm-up outputs are not the caller's
+                for _, xyz in outs:
+                    self.pool[xyz.shape[0]].append(xyz)
+                outs.clear()
+            else:
+                self._release(outs)
+        self.outputs.clear()
         sizes = collections.Counter(r.width * r.height for r in requests)
         for px in sorted(sizes):
             # outputs kept for the caller never return to the pool: one each
-            want = max(per_size, sizes[px] + 1) if self.keep else per_size
+            want = max(per_size, sizes[px]) if self.keep else per_size
             while len(self.pool[px]) < want:
                 self.pool[px].append(torch.empty(px, 3, device=self.sc.dev))
-        if self.mode == "latent":
-            self.hsc.hsc_shade_frames(self.ctx, [], stream=self.streams[0])   # allocates the descriptor ring
-        # one request of every (k, n) through the real path: the first launch of
-        # a kernel loads its code, which can wait for the device as well
-        firsts = {}
-        for r in requests:
-            firsts.setdefault((r.k, r.n), r)
-        handles = [self.launch([r]) for r in firsts.values()]
-        torch.cuda.synchronize(self.sc.dev)
-        for _, outs in handles:
-            self._release(outs)
-        self.outputs.clear()
 
-    def _buffer(self, px: int):
+    def _buffer(self, px: int, stream=None):
         import torch
         free = self.pool[px]
-        return free.pop() if free else torch.empty(px, 3, device=self.sc.dev)
+        if free:
+            return free.pop()
+        # a pool that ran dry: allocate on the launch's stream, so that the
+        # caching allocator orders the buffer's reuse after this launch
+        with torch.cuda.stream(stream if stream is not None else torch.cuda.current_stream(self.sc.dev)):
+            return torch.empty(px, 3, device=self.sc.dev)
 
     def start(self):
         import torch
@@ -360,41 +375,38 @@ class GpuBackend:
         return t1
 
     def launch(self, requests):
+        """Every call below takes the stream explicitly, so the launch does not
+        switch torch's current stream (a device guard and two stream switches
+        per launch on the host's critical path)."""
         import torch
-        t_in = time.perf_counter()
+        t = time.perf_counter()
         stream = self.streams[self.si]
         self.si = (self.si + 1) % len(self.streams)
         outs = []
-        with torch.cuda.stream(stream):
-            self._part("enter", t_in)
-            if self.mode == "latent":
-                frames = []
-                t = time.perf_counter()
-                for r in requests:
-                    g1, lights, zm, zl, M = self.sc.frame_inputs(r)
-                    xyz = self._buffer(r.width * r.height)
-                    frames.append(self.hsc.BatchFrame(g1, None, zm, lights, zl, M, xyz))
-                    outs.append((r.rid, xyz))
-                t = self._part("inputs", t)
-                self.hsc.hsc_shade_frames(self.ctx, frames, stream=stream)
-                self._part("shade_frames", t)
-            else:
-                t = time.perf_counter()
-                for r in requests:
-                    g1 = self.sc.gbuf[(r.scene, r.width, r.height)]
-                    lpos, linten = self.sc.lights[r.scene]
-                    lights = self.hsc.Lights(lpos[:r.lights], linten[:r.lights])
-                    xyz = self._buffer(r.width * r.height)
-                    self.hsc.hsc_shade_spectral(self.ctx, g1, None, self.sc.mats[(r.scene, r.n)], lights,
-                                                self.sc.spd[(r.scene, r.n)][:r.lights], self.sc.T[r.n], xyz,
-                                                stream=stream)
-                    outs.append((r.rid, xyz))
-                self._part("shade_spectral", t)
-            t = time.perf_counter()
-            ev = torch.cuda.Event(enable_timing=True)
-            ev.record(stream)
-            t_exit = self._part("event", t)
-        self._part("exit", t_exit)
+        if self.mode == "latent":
+            frames = []
+            for r in requests:
+                g1, lights, zm, zl, M = self.sc.frame_inputs(r)
+                xyz = self._buffer(r.width * r.height, stream)
+                frames.append(self.hsc.BatchFrame(g1, None, zm, lights, zl, M, xyz))
+                outs.append((r.rid, xyz))
+            t = self._part("inputs", t)
+            self.hsc.hsc_shade_frames(self.ctx, frames, stream=stream)
+            t = self._part("shade_frames", t)
+        else:
+            for r in requests:
+                g1 = self.sc.gbuf[(r.scene, r.width, r.height)]
+                lpos, linten = self.sc.lights[r.scene]
+                lights = self.hsc.Lights(lpos[:r.lights], linten[:r.lights])
+                xyz = self._buffer(r.width * r.height, stream)
+                self.hsc.hsc_shade_spectral(self.ctx, g1, None, self.sc.mats[(r.scene, r.n)], lights,
+                                            self.sc.spd[(r.scene, r.n)][:r.lights], self.sc.T[r.n], xyz,
+                                            stream=stream)
+                outs.append((r.rid, xyz))
+            t = self._part("shade_spectral", t)
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(stream)
+        self._part("event", t)
         if self.keep:
             for rid, xyz in outs:
                 self.outputs[rid] = xyz

@@ -393,7 +393,9 @@ def test_decode_xyz_from_reduced_latents(env):
 
 @pytest.mark.parametrize("k,n,P", [(6, 81, 1000), (9, 81, 4097), (6, 31, 63), (96, 128, 70), (3, 1, 5),
                                    (6, 81, 160_077), (8, 128, 160_077), (9, 81, 160_077), (10, 96, 1000),
-                                   (11, 81, 1000)])
+                                   (11, 81, 1000),
+                                   # the split form's largest tiles: one CTA per SM
+                                   (9, 128, 160_077), (10, 128, 5000)])
 def test_decode_spectra_f32(env, k, n, P):
     hsc, ctx, dev = env
     import torch

@@ -27,7 +27,8 @@ def env():
 # 160,077 pixels: 1,251 tiles, several per persistent CTA, so the staging
 # tiles are reused while earlier stores may still be in flight
 @pytest.mark.parametrize("k,n,P", [(6, 81, 128), (6, 81, 4096 + 77), (9, 81, 3 * 128), (9, 31, 1000), (16, 128, 257),
-                                   (3, 16, 5), (6, 1, 300), (12, 96, 131), (6, 81, 160_077), (16, 128, 160_077)])
+                                   (3, 16, 5), (6, 1, 300), (12, 96, 131), (6, 81, 160_077), (16, 128, 160_077),
+                                   (9, 81, 160_077)])   # odd k: element loads over many tiles
 def test_decode_spectra_bf16(env, k, n, P):
     hsc, ctx, dev = env
     import torch
@@ -42,7 +43,8 @@ def test_decode_spectra_bf16(env, k, n, P):
     assert rel_err_rows(out.cpu().numpy(), ref) <= 1e-5
 
 
-@pytest.mark.parametrize("k,n,P", [(6, 81, 8192 + 5), (9, 81, 640), (9, 31, 129), (6, 81, 160_077)])
+@pytest.mark.parametrize("k,n,P", [(6, 81, 8192 + 5), (9, 81, 640), (9, 31, 129), (6, 81, 160_077),
+                                   (9, 81, 160_077), (3, 128, 70_001)])
 def test_decode_spectra_fp8(env, k, n, P):
     hsc, ctx, dev = env
     import torch

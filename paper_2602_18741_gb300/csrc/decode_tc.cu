@@ -83,7 +83,8 @@ constexpr int seg_width() { return KB == 4 ? 10 : 8; }
 // or the six segments of the three-part split (KB = 3, 4).
 template <int KB>
 struct RawRow {
-  // KB = 1: elements as 16-bit units, two per word (bf16 bits, or an fp8 byte);
+  // KB = 1: two elements per word (bf16 bits as 16-bit halves; fp8 codes as
+  // the two low bytes);
   // KB = 3, 4: the FP32 values of codes 0 .. SW - 1
   uint32_t v[KB == 1 ? 8 : seg_width<KB>()];
 };
@@ -123,6 +124,10 @@ __device__ __forceinline__ void load_a_raw(const TcArgs& a, int64_t p, bool vali
       const unsigned char* src = reinterpret_cast<const unsigned char*>(a.latent) + p * a.k;
 #pragma unroll
       for (int e = 0; e < 16; ++e) b[e] = (valid && e < a.k) ? (uint32_t)__ldg(src + e) : 0u;
+      // byte pairs, as the whole-pair path loads them
+#pragma unroll
+      for (int j = 0; j < 8; ++j) r.v[j] = b[2 * j] | (b[2 * j + 1] << 8);
+      return;
     } else {
       const unsigned short* src = reinterpret_cast<const unsigned short*>(a.latent) + p * a.k;
 #pragma unroll
@@ -142,7 +147,7 @@ __device__ __forceinline__ void pack_a_row(const TcArgs& a, const RawRow<KB>& r,
     w[e >> 1] |= bits << ((e & 1) * 16);
   };
   if constexpr (KB == 1) {
-    if (a.dt == HSC_FP8_E4M3 && a.pairs) {
+    if (a.dt == HSC_FP8_E4M3) {
       // each word holds two e4m3 codes (byte pairs): to f16x2 in one
       // conversion, then to bf16x2; every step is exact for e4m3 values
 #pragma unroll
@@ -152,12 +157,6 @@ __device__ __forceinline__ void pack_a_row(const TcArgs& a, const RawRow<KB>& r,
         const __half2 h2 = *reinterpret_cast<const __half2*>(&hh);
         const __nv_bfloat162 b2 = __floats2bfloat162_rn(__low2float(h2), __high2float(h2));
         w[j] = *reinterpret_cast<const uint32_t*>(&b2);
-      }
-    } else if (a.dt == HSC_FP8_E4M3) {
-#pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        if (e >= a.k) break;
-        put(e, fp8_e4m3_to_float((unsigned char)(r.v[e >> 1] >> ((e & 1) * 16))));
       }
     } else {
 #pragma unroll

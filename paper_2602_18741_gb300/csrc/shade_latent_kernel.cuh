@@ -40,26 +40,63 @@ struct LightStage {
   static constexpr int F4 = VEC == 1 ? (3 + KC + 3) / 4 : (3 + KC + 1) / 2;
 };
 
+// Code element i as float for one storage format (the conversions of
+// load_code, with the format fixed at compile time).
+template <int DT>
+__device__ __forceinline__ float code_at(const void* base, int64_t i) {
+  if constexpr (DT == HSC_F32) {
+    return __ldg(reinterpret_cast<const float*>(base) + i);
+  } else {
+    const unsigned short u = __ldg(reinterpret_cast<const unsigned short*>(base) + i);
+    if constexpr (DT == HSC_BF16)
+      return __uint_as_float(((unsigned int)u) << 16);
+    else
+      return __half2float(__ushort_as_half(u));
+  }
+}
+
+// Staging loads each thread issues before it writes any of them to shared
+// memory: every CTA stages at its start, so the loads' latency is paid once
+// per batch instead of once per element.
+constexpr int kStageBatch = 8;
+
 // Stages lights l0 .. l0+nl-1 of one launch: positions and the code channels
 // c0 .. c0+KC-1 pre-multiplied by I/pi, laid out as LightStage describes.
+// Every load of a batch has an in-range address (the light index and the
+// channel are clamped) and is selected afterwards, so a batch's loads issue
+// back to back.
+template <int KC, int VEC, int BLOCK, int DT>
+__device__ __forceinline__ void stage_light_codes_dt(const ShadeArgs& a, float* s, int l0, int nl) {
+  constexpr int per = LightStage<KC, VEC>::F4 * 4;
+  const int n = nl * per;
+  for (int base = threadIdx.x; base < n; base += kStageBatch * BLOCK) {
+    float v[kStageBatch];
+#pragma unroll
+    for (int r = 0; r < kStageBatch; ++r) {
+      const int idx = min(base + r * BLOCK, n - 1);
+      const int l = idx / per, j0 = idx - l * per;
+      const int j = VEC == 1 ? j0 : (j0 >> 1);
+      const int lg = l0 + l;
+      const float pos = __ldg(a.lpos + 3 * lg + min(j, 2));
+      const float code = code_at<DT>(a.light_codes, (int64_t)lg * a.k + a.c0 + min(max(j - 3, 0), KC - 1));
+      const float sc = __fmul_rn(__ldg(a.linten + lg), kInvPi);
+      v[r] = j < 3 ? pos : (j < 3 + KC ? __fmul_rn(code, sc) : 0.0f);
+    }
+#pragma unroll
+    for (int r = 0; r < kStageBatch; ++r)
+      if (base + r * BLOCK < n) s[base + r * BLOCK] = v[r];
+  }
+}
+
 template <int KC, int VEC, int BLOCK>
 __device__ __forceinline__ void stage_light_codes(const ShadeArgs& a, float4* s_light, int l0, int nl) {
-  constexpr int F4 = LightStage<KC, VEC>::F4;
   float* s = reinterpret_cast<float*>(s_light);
-  constexpr int per = F4 * 4;
-  for (int idx = threadIdx.x; idx < nl * per; idx += BLOCK) {
-    const int l = idx / per, j0 = idx - l * per;
-    const int j = VEC == 1 ? j0 : (j0 >> 1);
-    const int lg = l0 + l;
-    float v = 0.0f;
-    if (j < 3) {
-      v = __ldg(a.lpos + 3 * lg + j);
-    } else if (j < 3 + KC) {
-      const float sc = __fmul_rn(__ldg(a.linten + lg), kInvPi);
-      v = __fmul_rn(load_code(a.light_codes, a.code_dt, (int64_t)lg * a.k + a.c0 + (j - 3)), sc);
-    }
-    s[idx] = v;
-  }
+  if (a.code_dt == HSC_F32)
+    stage_light_codes_dt<KC, VEC, BLOCK, HSC_F32>(a, s, l0, nl);
+  else if (a.code_dt == HSC_BF16)
+    stage_light_codes_dt<KC, VEC, BLOCK, HSC_BF16>(a, s, l0, nl);
+  else
+    stage_light_codes_dt<KC, VEC, BLOCK, HSC_F16>(a, s, l0, nl);
 }
 
 // Material code tables of at most kMatStage values (n_mat x KC) are staged
@@ -71,12 +108,31 @@ constexpr int kMatStage = 4096;
 template <int KC>
 __host__ __device__ __forceinline__ bool mat_staged(int n_mat) { return (int64_t)n_mat * KC <= kMatStage; }
 
+template <int KC, int BLOCK, int DT>
+__device__ __forceinline__ void stage_material_codes_dt(const ShadeArgs& a, float* s_mat) {
+  const int n = a.n_mat * KC;
+  for (int base = threadIdx.x; base < n; base += kStageBatch * BLOCK) {
+    float v[kStageBatch];
+#pragma unroll
+    for (int r = 0; r < kStageBatch; ++r) {
+      const int i = min(base + r * BLOCK, n - 1);
+      const int row = i / KC, c = i - row * KC;
+      v[r] = code_at<DT>(a.mat_codes, (int64_t)row * a.k + a.c0 + c);
+    }
+#pragma unroll
+    for (int r = 0; r < kStageBatch; ++r)
+      if (base + r * BLOCK < n) s_mat[base + r * BLOCK] = v[r];
+  }
+}
+
 template <int KC, int BLOCK>
 __device__ __forceinline__ void stage_material_codes(const ShadeArgs& a, float* s_mat) {
-  for (int i = threadIdx.x; i < a.n_mat * KC; i += BLOCK) {
-    const int row = i / KC, c = i - row * KC;
-    s_mat[i] = load_code(a.mat_codes, a.code_dt, (int64_t)row * a.k + a.c0 + c);
-  }
+  if (a.code_dt == HSC_F32)
+    stage_material_codes_dt<KC, BLOCK, HSC_F32>(a, s_mat);
+  else if (a.code_dt == HSC_BF16)
+    stage_material_codes_dt<KC, BLOCK, HSC_BF16>(a, s_mat);
+  else
+    stage_material_codes_dt<KC, BLOCK, HSC_F16>(a, s_mat);
 }
 
 // Resident CTAs per SM asked of the compiler: the 128-thread scalar form with
@@ -362,6 +418,10 @@ __global__ void __launch_bounds__(BLOCK, (latent_min_blocks<KC, PPT, BLOCK, VEC>
   const bool staged = a.L <= kLightTile;
   unsigned int* cmax = a.chan_max ? s_cmax : nullptr;
   if (threadIdx.x < KC) s_cmax[threadIdx.x] = 0u;
+  // dynamic schedule: the first tile is claimed before the staging, so the
+  // atomic's latency overlaps it
+  __shared__ int64_t s_next;
+  if (a.queue && threadIdx.x == 0) s_next = (int64_t)atomicAdd(a.queue, 1u);
   float* s_mat = mat_staged<KC>(a.n_mat)
                      ? reinterpret_cast<float*>(s_light + min(a.L, kLightTile) * LightStage<KC, VEC>::F4)
                      : nullptr;
@@ -371,14 +431,13 @@ __global__ void __launch_bounds__(BLOCK, (latent_min_blocks<KC, PPT, BLOCK, VEC>
   __syncthreads();
   if (a.queue) {
     // dynamic schedule: persistent CTAs take the next tile from a counter
-    __shared__ int64_t s_next;
     for (;;) {
-      if (threadIdx.x == 0) s_next = (int64_t)atomicAdd(a.queue, 1u);
-      __syncthreads();
       const int64_t tile = s_next;
-      __syncthreads();
+      __syncthreads();  // every thread has read s_next before it is replaced
       if (tile >= a.tiles) break;
       shade_tile<KC, PPT, SEC, BLOCK, VEC, RGB>(a, tile, s_light, staged, s_M, s_mat, cmax);
+      if (threadIdx.x == 0) s_next = (int64_t)atomicAdd(a.queue, 1u);
+      __syncthreads();
     }
     release_queue(a.queue);
   } else {

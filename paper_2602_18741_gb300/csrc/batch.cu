@@ -51,7 +51,7 @@ __device__ __forceinline__ void run_tile(const ShadeArgs& a, int64_t local_tile,
   constexpr int V = (VEC == 2 && !SEC && PPT == 1) ? 1 : VEC;
   if (restage) {
     __syncthreads();
-    if (staged) stage_light_codes<KC, V, BLOCK>(a, s_light, 0, a.L);
+    if (staged) restage_light_codes<KC, V, BLOCK>(a, s_light, 0, a.L);
     stage_decode_matrix<KC, BLOCK>(a, s_M);
     __syncthreads();
   }

@@ -62,9 +62,9 @@ constexpr int kStageBatch = 8;
 
 // Stages lights l0 .. l0+nl-1 of one launch: positions and the code channels
 // c0 .. c0+KC-1 pre-multiplied by I/pi, laid out as LightStage describes.
-// Every load of a batch has an in-range address (the light index and the
-// channel are clamped) and is selected afterwards, so a batch's loads issue
-// back to back.
+// The prologue form: every load of a batch has an in-range address (the light
+// index and the channel are clamped) and is selected afterwards, so a
+// batch's loads issue back to back.
 template <int KC, int VEC, int BLOCK, int DT>
 __device__ __forceinline__ void stage_light_codes_dt(const ShadeArgs& a, float* s, int l0, int nl) {
   constexpr int per = LightStage<KC, VEC>::F4 * 4;
@@ -85,6 +85,28 @@ __device__ __forceinline__ void stage_light_codes_dt(const ShadeArgs& a, float* 
 #pragma unroll
     for (int r = 0; r < kStageBatch; ++r)
       if (base + r * BLOCK < n) s[base + r * BLOCK] = v[r];
+  }
+}
+
+// The same values one load at a time: the form used between light tiles
+// inside the tile loop, where the batch's registers would add to the live
+// accumulators.
+template <int KC, int VEC, int BLOCK>
+__device__ __forceinline__ void restage_light_codes(const ShadeArgs& a, float4* s_light, int l0, int nl) {
+  constexpr int per = LightStage<KC, VEC>::F4 * 4;
+  float* s = reinterpret_cast<float*>(s_light);
+  for (int idx = threadIdx.x; idx < nl * per; idx += BLOCK) {
+    const int l = idx / per, j0 = idx - l * per;
+    const int j = VEC == 1 ? j0 : (j0 >> 1);
+    const int lg = l0 + l;
+    float v = 0.0f;
+    if (j < 3) {
+      v = __ldg(a.lpos + 3 * lg + j);
+    } else if (j < 3 + KC) {
+      const float sc = __fmul_rn(__ldg(a.linten + lg), kInvPi);
+      v = __fmul_rn(load_code(a.light_codes, a.code_dt, (int64_t)lg * a.k + a.c0 + (j - 3)), sc);
+    }
+    s[idx] = v;
   }
 }
 
@@ -180,7 +202,7 @@ __device__ __forceinline__ void shade_tile(const ShadeArgs& a, int64_t tile, flo
   static_assert(VEC == 1 || NPT % 2 == 0, "paired points need an even point count");
   const int tid = threadIdx.x;
   const bool multi_tile = !staged;
-  auto stage = [&](int l0, int nl) { stage_light_codes<KC, VEC, BLOCK>(a, s_light, l0, nl); };
+  auto stage = [&](int l0, int nl) { restage_light_codes<KC, VEC, BLOCK>(a, s_light, l0, nl); };
   {
     float px[NPT], py[NPT], pz[NPT], nx[NPT], ny[NPT], nz[NPT];
     float hb[PPT];          // bounce term of each pixel (SEC)

@@ -52,20 +52,49 @@ struct SpecArgs {
 // (I/pi)-scaled spectrum, zero beyond n.
 __device__ __forceinline__ int spec_f4(const SpecArgs& a) { return 1 + a.npad / 4; }
 
+// Staging loads each thread issues before it writes any of them to shared
+// memory (every load of a batch has an in-range address and its value is
+// selected afterwards), so a CTA waits for memory once per batch instead of
+// once per staged value.  The prologue stages this way; restaging between
+// light tiles inside the tile loop (BATCH = 1) loads one value at a time, so
+// that no batch registers add to the live accumulators there.
+constexpr int kSpecStageBatch = 8;
+
+template <int BATCH>
 __device__ __forceinline__ void stage_lights(const SpecArgs& a, float4* s_light, int l0, int nl) {
   float* s = reinterpret_cast<float*>(s_light);
   const int per = spec_f4(a) * 4;
-  for (int idx = threadIdx.x; idx < nl * per; idx += blockDim.x) {
-    const int l = idx / per, j = idx - l * per;
-    const int lg = l0 + l;
-    float v = 0.0f;
-    if (j < 3) {
-      v = __ldg(a.lpos + 3 * lg + j);
-    } else if (j >= 4 && j - 4 < a.n) {
-      const float sc = __fmul_rn(__ldg(a.linten + lg), kInvPi);
-      v = __fmul_rn(__ldg(a.spd + (int64_t)lg * a.n + (j - 4)), sc);
+  if constexpr (BATCH == 1) {
+    for (int idx = threadIdx.x; idx < nl * per; idx += blockDim.x) {
+      const int l = idx / per, j = idx - l * per;
+      const int lg = l0 + l;
+      float v = 0.0f;
+      if (j < 3) {
+        v = __ldg(a.lpos + 3 * lg + j);
+      } else if (j >= 4 && j - 4 < a.n) {
+        const float sc = __fmul_rn(__ldg(a.linten + lg), kInvPi);
+        v = __fmul_rn(__ldg(a.spd + (int64_t)lg * a.n + (j - 4)), sc);
+      }
+      s[idx] = v;
     }
-    s[idx] = v;
+    return;
+  }
+  const int total = nl * per;
+  for (int base = threadIdx.x; base < total; base += BATCH * (int)blockDim.x) {
+    float v[BATCH];
+#pragma unroll
+    for (int q = 0; q < BATCH; ++q) {
+      const int idx = min(base + q * (int)blockDim.x, total - 1);
+      const int l = idx / per, j = idx - l * per;
+      const int lg = l0 + l;
+      const float pos = __ldg(a.lpos + 3 * lg + min(j, 2));
+      const float sc = __fmul_rn(__ldg(a.linten + lg), kInvPi);
+      const float x = __ldg(a.spd + (int64_t)lg * a.n + min(max(j - 4, 0), a.n - 1));
+      v[q] = j < 3 ? pos : ((j >= 4 && j - 4 < a.n) ? __fmul_rn(x, sc) : 0.0f);
+    }
+#pragma unroll
+    for (int q = 0; q < BATCH; ++q)
+      if (base + q * (int)blockDim.x < total) s[base + q * (int)blockDim.x] = v[q];
   }
 }
 
@@ -155,7 +184,7 @@ __device__ __forceinline__ void sweep_all(const SpecArgs& a, float4* s_light, bo
       const int nl = min(kSpecLightTile, a.L - l0);
       if (!staged) {
         __syncthreads();
-        stage_lights(a, s_light, l0, nl);
+        stage_lights<1>(a, s_light, l0, nl);
         __syncthreads();
       }
       sweep_x2<CW, PTS>(s_light, f4, c0, nl, pt, acc2);
@@ -169,7 +198,7 @@ __device__ __forceinline__ void sweep_all(const SpecArgs& a, float4* s_light, bo
       const int nl = min(kSpecLightTile, a.L - l0);
       if (!staged) {
         __syncthreads();
-        stage_lights(a, s_light, l0, nl);
+        stage_lights<1>(a, s_light, l0, nl);
         __syncthreads();
       }
       sweep<CW, PTS>(s_light, f4, c0, nl, pt, acc);
@@ -206,7 +235,7 @@ __global__ void __launch_bounds__(BLOCK) shade_spectral_kernel(const SpecArgs a)
   extern __shared__ float4 s_light[];
   const bool staged = a.L <= kSpecLightTile;
   if (staged) {
-    stage_lights(a, s_light, 0, a.L);
+    stage_lights<kSpecStageBatch>(a, s_light, 0, a.L);
     __syncthreads();
   }
   constexpr int PXT = (PTS == 2 && !SEC) ? 2 : 1;  // pixels per thread
@@ -335,18 +364,36 @@ __device__ __forceinline__ int lane_row_sample(int r, int n) {
 // the stage to a whole number of kLB lights with far-away dark lights
 // (spectrum 0: every FMA with them adds +0 to a non-negative sum, which
 // leaves it unchanged bit for bit).
-template <int TL, int R, int BLOCK>
+template <int TL, int R, int BLOCK, int BATCH>
 __device__ __forceinline__ void stage_lane_lights(const SpecArgs& a, float* s_V, float4* s_pos, int l0, int nl) {
   constexpr int VROW = LaneShape<TL, R>::VROW;
   const int npad = (nl + kLB - 1) / kLB * kLB;
-  for (int i = threadIdx.x; i < npad * VROW; i += BLOCK) {
-    const int l = i / VROW, r = i - l * VROW, lam = lane_row_sample<TL, R>(r, a.n);
-    float v = 0.0f;
-    if (lam >= 0 && l < nl) {
-      const float sc = __fmul_rn(__ldg(a.linten + l0 + l), kInvPi);
-      v = __fmul_rn(__ldg(a.spd + (int64_t)(l0 + l) * a.n + lam), sc);
+  const int total = npad * VROW;
+  if constexpr (BATCH == 1) {
+    for (int i = threadIdx.x; i < total; i += BLOCK) {
+      const int l = i / VROW, r = i - l * VROW, lam = lane_row_sample<TL, R>(r, a.n);
+      float v = 0.0f;
+      if (lam >= 0 && l < nl) {
+        const float sc = __fmul_rn(__ldg(a.linten + l0 + l), kInvPi);
+        v = __fmul_rn(__ldg(a.spd + (int64_t)(l0 + l) * a.n + lam), sc);
+      }
+      s_V[i] = v;
     }
-    s_V[i] = v;
+  }
+  for (int base = threadIdx.x; BATCH > 1 && base < total; base += BATCH * BLOCK) {
+    float v[BATCH];
+#pragma unroll
+    for (int q = 0; q < BATCH; ++q) {
+      const int i = min(base + q * BLOCK, total - 1);
+      const int l = i / VROW, r = i - l * VROW, lam = lane_row_sample<TL, R>(r, a.n);
+      const int lc = min(l, nl - 1);
+      const float sc = __fmul_rn(__ldg(a.linten + l0 + lc), kInvPi);
+      const float x = __ldg(a.spd + (int64_t)(l0 + lc) * a.n + max(lam, 0));
+      v[q] = (lam >= 0 && l < nl) ? __fmul_rn(x, sc) : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < BATCH; ++q)
+      if (base + q * BLOCK < total) s_V[base + q * BLOCK] = v[q];
   }
   for (int l = threadIdx.x; l < npad; l += BLOCK)
     s_pos[l] = l < nl ? make_float4(__ldg(a.lpos + 3 * (l0 + l)), __ldg(a.lpos + 3 * (l0 + l) + 1),
@@ -378,7 +425,7 @@ __global__ void __launch_bounds__(128, TL <= 12 ? 4 : 2) shade_spectral_lanes_ke
     const int c = i / VROW, r = i - c * VROW, lam = lane_row_sample<TL, R>(r, a.n);
     s_T[i] = lam >= 0 ? __ldg(a.T + c * a.n + lam) : 0.0f;
   }
-  if (ONE) stage_lane_lights<TL, R, BLOCK>(a, s_V, s_pos, 0, a.L);
+  if (ONE) stage_lane_lights<TL, R, BLOCK, kSpecStageBatch>(a, s_V, s_pos, 0, a.L);
   __syncthreads();
   float* gx = s_gx + (tid >> 5) * (kLB * 32);
   const float* vr = s_V + grp * VS;            // this lane's group row of light 0
@@ -473,7 +520,7 @@ __global__ void __launch_bounds__(128, TL <= 12 ? 4 : 2) shade_spectral_lanes_ke
       for (int l0 = 0; l0 < a.L; l0 += kLT) {
         const int nl = min(kLT, a.L - l0);
         __syncthreads();
-        stage_lane_lights<TL, R, BLOCK>(a, s_V, s_pos, l0, nl);
+        stage_lane_lights<TL, R, BLOCK, 1>(a, s_V, s_pos, l0, nl);
         __syncthreads();
         sweep_stage(nl);
       }

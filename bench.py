@@ -227,11 +227,10 @@ def run_hsc(args, rank: int, world: int):
         flush.zero_()
         torch.sum(flush_read, dim=0, out=flush_sink)
     evals = f.evals
-    gpu_launches_per_step = 3
+    gpu_launches_per_step = 2
 
     def frame(ev=None):
-        hsc.hsc_encode(ctx, Ed, mats, zm)
-        hsc.hsc_encode(ctx, Ed, spd, zl)
+        hsc.hsc_encode_assets(ctx, Ed, mats, zm, spd, zl)
         if ev is not None:
             ev[0].record(stream)
         hsc.hsc_shade_latent(ctx, g1, g2, zm, lights, zl, hsc.HSC_FUSED, lat, xyz_out=xyz, M_xyz=M, srgb8_out=rgb)
@@ -723,7 +722,8 @@ def group_rows(args, hsc, ctx, dev, timed, before_serve=None):
 
 def small_frame_rows(args, hsc, ctx, dev, replays: int = 200):
     """The 256x256 frame (n = 31, k = 6, 4 lights, direct only): launch
-    bound, so the latent frame (two encodes + fused shade with XYZ), the
+    bound, so the latent frame (one encode launch for materials and lights
+    + fused shade with XYZ), the
     latent shade alone (assets already encoded), the latent frame with the
     encode inside the shading launch (hsc_shade_latent_assets) and the
     spectral frame are each captured once in a CUDA graph and replayed back
@@ -749,8 +749,7 @@ def small_frame_rows(args, hsc, ctx, dev, replays: int = 200):
     xyz_s = torch.empty(f.pixels, 3, device=dev)
 
     def latent():
-        hsc.hsc_encode(ctx, Ed, mats, zm)
-        hsc.hsc_encode(ctx, Ed, spd, zl)
+        hsc.hsc_encode_assets(ctx, Ed, mats, zm, spd, zl)
         hsc.hsc_shade_latent(ctx, g1, None, zm, lights, zl, hsc.HSC_FUSED, lat, xyz_out=xyz_l, M_xyz=M)
 
     def latent_shade():
@@ -1144,8 +1143,7 @@ def e2e_leg(args, hsc, ctx, f, dev, stream, Ed, M, evals):
         stream.wait_event(b["in_done"])
         if used[i % 2]:
             stream.wait_event(b["out_done"])             # frame i - 2's outputs have been copied out
-        hsc.hsc_encode(ctx, Ed, b["d"]["mats"], b["zm"], stream=stream)
-        hsc.hsc_encode(ctx, Ed, b["d"]["spd"], b["zl"], stream=stream)
+        hsc.hsc_encode_assets(ctx, Ed, b["d"]["mats"], b["zm"], b["d"]["spd"], b["zl"], stream=stream)
         hsc.hsc_shade_latent(ctx, b["g1"], b["g2"], b["zm"], b["lights"], b["zl"], hsc.HSC_FUSED, b["lat"],
                              xyz_out=b["xyz"], M_xyz=M, srgb8_out=b["rgb"], stream=stream)
         b["comp_done"].record(stream)

@@ -210,6 +210,20 @@ HSC_API hsc_status hsc_fold_xyz(hsc_ctx* ctx, const float* T, const float* D, in
 HSC_API hsc_status hsc_encode(hsc_ctx* ctx, const float* E, int k, int n, const float* spectra, int m,
                       void* codes_out, hsc_dtype out_dt, void* stream);
 
+/* Encode a scene's material reflectances and light SPDs in one launch
+ * (Eq. 4, Fig. 2b).  Every code value is summed exactly as hsc_encode sums
+ * it, so the codes are the bits of hsc_encode on each set; one launch
+ * instead of two is what a per-frame encode (a changing scene) saves.
+ *   E: device k x n float32;  mat_spectra: device n_mat x n float32;
+ *   light_spd: device n_lights x n float32;
+ *   mat_codes_out: device n_mat x k and light_codes_out: device n_lights x k,
+ *   both of out_dt (F32, BF16 or F16, round-to-nearest-even).
+ *   n_mat, n_lights >= 0; a set with count 0 is skipped (its pointers may be NULL).
+ *   1 <= n <= HSC_MAX_N, 1 <= k <= HSC_MAX_K.                                */
+HSC_API hsc_status hsc_encode_assets(hsc_ctx* ctx, const float* E, int k, int n, const float* mat_spectra,
+                             int n_mat, void* mat_codes_out, const float* light_spd, int n_lights,
+                             void* light_codes_out, hsc_dtype out_dt, void* stream);
+
 /* ----------------------------------------------------------- latent shade */
 
 /* Shade one RGB pass: code channels 3b..3b+2 of every pixel (Fig. 2b: the

@@ -88,6 +88,7 @@ _SIGS = {
     "hsc_cmf_weights": ([_vp, _i32, _f32, _f32, _vp, _vp], _i32),
     "hsc_fold_xyz": ([_vp, _vp, _vp, _i32, _i32, _vp, _vp], _i32),
     "hsc_encode": ([_vp, _vp, _i32, _i32, _vp, _i32, _vp, _i32, _vp], _i32),
+    "hsc_encode_assets": ([_vp, _vp, _i32, _i32, _vp, _i32, _vp, _vp, _i32, _vp, _i32, _vp], _i32),
     "hsc_shade_pass": ([_vp, _GB, _GB, _i64, _vp, _i32, _LI, _vp, _i32, _i32, _i32, _vp, _vp], _i32),
     "hsc_reassemble": ([_vp, ctypes.POINTER(_vp), _i32, _i64, _vp, _vp], _i32),
     "hsc_shade_latent": ([_vp, _GB, _GB, _i64, _vp, _i32, _LI, _vp, _i32, _i32, _i32, _vp, _i32, _vp, _vp, _vp,
@@ -306,6 +307,22 @@ def hsc_encode(ctx: Context, E: torch.Tensor, spectra: torch.Tensor, codes_out: 
         raise ValueError("E and spectra must be float32")
     _check(_lib.hsc_encode(ctx.handle, _ptr(E), int(k), int(n), _ptr(spectra), int(m), _ptr(codes_out),
                            _dt(codes_out), _stream(stream)))
+
+
+def hsc_encode_assets(ctx: Context, E: torch.Tensor, mat_spectra: torch.Tensor, mat_codes_out: torch.Tensor,
+                      light_spd: torch.Tensor, light_codes_out: torch.Tensor, stream=None):
+    k, n = E.shape
+    nm, nl = mat_spectra.shape[0], light_spd.shape[0]
+    if (mat_spectra.shape != (nm, n) or light_spd.shape != (nl, n) or mat_codes_out.shape != (nm, k)
+            or light_codes_out.shape != (nl, k)):
+        raise ValueError("shapes: E (k,n), mat_spectra (n_mat,n), light_spd (L,n), codes (n_mat,k) and (L,k)")
+    if E.dtype != torch.float32 or mat_spectra.dtype != torch.float32 or light_spd.dtype != torch.float32:
+        raise ValueError("E and spectra must be float32")
+    if mat_codes_out.dtype != light_codes_out.dtype:
+        raise ValueError("material and light codes must have one dtype")
+    _check(_lib.hsc_encode_assets(ctx.handle, _ptr(E), int(k), int(n), _ptr(mat_spectra), int(nm),
+                                  _ptr(mat_codes_out), _ptr(light_spd), int(nl), _ptr(light_codes_out),
+                                  _dt(mat_codes_out), _stream(stream)))
 
 
 def hsc_shade_pass(ctx: Context, g1: GBuffer, g2: Optional[GBuffer], mat_codes: torch.Tensor, lights: Lights,

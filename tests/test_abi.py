@@ -73,3 +73,7 @@ def test_null_context_is_rejected(lib_path):
                                                                             ctypes.c_void_p, ctypes.c_int,
                                                                             ctypes.c_void_p]
     assert lib.hsc_encode(None, None, 6, 31, None, 4, None, 0, None) == 1
+    lib.hsc_encode_assets.argtypes = ([ctypes.c_void_p] * 2 + [ctypes.c_int] * 2 +
+                                      [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p] * 2 +
+                                      [ctypes.c_int, ctypes.c_void_p])
+    assert lib.hsc_encode_assets(None, None, 6, 81, None, 288, None, None, 64, None, 0, None) == 1

@@ -85,6 +85,36 @@ def test_encode_f32(env, k, n, m):
     assert rel_err_rows(out.cpu().numpy(), ref) <= 1e-6
 
 
+@pytest.mark.parametrize("dtname", ["float32", "bfloat16", "float16"])
+@pytest.mark.parametrize("k,n,nm,nl", [(6, 81, 288, 64), (9, 31, 5, 0), (3, 97, 0, 7), (96, 128, 33, 2)])
+def test_encode_assets_is_two_encodes(env, dtname, k, n, nm, nl):
+    """One launch for both asset sets gives the bits of hsc_encode on each
+    (n = 128: four loads per lane; 31, 81, 97: ragged), and the FP32 codes
+    match the oracle's z = W_enc s (Eq. 4)."""
+    hsc, ctx, dev = env
+    import torch
+    dt = getattr(torch, dtname)
+    bits = torch.int32 if dt == torch.float32 else torch.int16
+    rng = np.random.default_rng(k * 1000 + n + nm + nl)
+    E = rng.uniform(0, 1.0 / n, (k, n)).astype(np.float32)
+    Sm = rng.uniform(0, 1, (nm, n)).astype(np.float32)
+    Sl = rng.uniform(0, 1, (nl, n)).astype(np.float32)
+    Ed, Smd, Sld = (torch.from_numpy(x).to(dev) for x in (E, Sm, Sl))
+    zm = torch.full((nm, k), -1.0, device=dev, dtype=dt)
+    zl = torch.full((nl, k), -1.0, device=dev, dtype=dt)
+    hsc.hsc_encode_assets(ctx, Ed, Smd, zm, Sld, zl)
+    rm, rl = torch.empty_like(zm), torch.empty_like(zl)
+    hsc.hsc_encode(ctx, Ed, Smd, rm)
+    hsc.hsc_encode(ctx, Ed, Sld, rl)
+    torch.cuda.synchronize()
+    assert torch.equal(zm.view(bits), rm.view(bits))
+    assert torch.equal(zl.view(bits), rl.view(bits))
+    if dt == torch.float32:
+        for got, S in ((zm, Sm), (zl, Sl)):
+            if S.shape[0]:
+                assert rel_err_rows(got.cpu().numpy(), codec.encode(E, S)) <= 1e-6
+
+
 @pytest.mark.parametrize("dtname", ["bfloat16", "float16"])
 def test_encode_reduced_precision_rounds_correctly(env, dtname):
     hsc, ctx, dev = env

@@ -1095,8 +1095,10 @@ def _M(hsc, ctx, T, Dd):
 
 def e2e_leg(args, hsc, ctx, f, dev, stream, Ed, M, evals):
     """Same latent frame through the public API with host buffers: pinned
-    host G-buffers, lights and spectra copied in, XYZ and sRGB8 copied out,
-    every step, all inside the timed region.  Frames stream through two
+    host G-buffers, lights and spectra copied in and the frame's displayed
+    result, its 8-bit sRGB image, copied out, every step, all inside the
+    timed region (the kernels still write the latent and XYZ images too, as
+    in the device-timed step).  Frames stream through two
     buffer sets: the copy-in of frame i + 1 (one copy stream) and the copy-out
     of frame i - 1 (another) overlap the kernels of frame i (one compute
     stream, so the shading launches keep their one-at-a-time order); events
@@ -1120,7 +1122,6 @@ def e2e_leg(args, hsc, ctx, f, dev, stream, Ed, M, evals):
             "lat": torch.empty(P, k, device=dev),
             "xyz": torch.empty(P, 3, device=dev),
             "rgb": torch.empty(P, 3, device=dev, dtype=torch.uint8),
-            "xyz_h": torch.empty(P, 3).pin_memory(),
             "rgb_h": torch.empty(P, 3, dtype=torch.uint8).pin_memory(),
             "g1": hsc.GBuffer(d["n1"], d["x1"], d["m1"]),
             "g2": hsc.GBuffer(d["n2"], d["x2"], d["m2"]),
@@ -1128,7 +1129,7 @@ def e2e_leg(args, hsc, ctx, f, dev, stream, Ed, M, evals):
             "in_done": torch.cuda.Event(), "comp_done": torch.cuda.Event(), "out_done": torch.cuda.Event(),
         })
     h2d = sum(t.numel() * t.element_size() for t in h.values())
-    d2h = sets[0]["xyz_h"].numel() * 4 + sets[0]["rgb_h"].numel()
+    d2h = sets[0]["rgb_h"].numel()
     s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
     used = [False, False]
 
@@ -1149,7 +1150,6 @@ def e2e_leg(args, hsc, ctx, f, dev, stream, Ed, M, evals):
         b["comp_done"].record(stream)
         with torch.cuda.stream(s_out):
             s_out.wait_event(b["comp_done"])
-            b["xyz_h"].copy_(b["xyz"], non_blocking=True)
             b["rgb_h"].copy_(b["rgb"], non_blocking=True)
             b["out_done"].record(s_out)
         used[i % 2] = True

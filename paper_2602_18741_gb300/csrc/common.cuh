@@ -246,9 +246,14 @@ __device__ __forceinline__ float srgb_oetf(float v) {
   return (v <= 0.0031308f) ? __fmul_rn(12.92f, v) : __fmaf_rn(1.055f, __powf(v, 1.0f / 2.4f), -0.055f);
 }
 
-// u8 = floor(255 v + 0.5): one conversion rounding toward minus infinity.
+// u8 = floor(255 v + 0.5) for v in [0, 1].  x = 255 v + 0.5 lies in
+// [0.5, 255.5]; adding 2^23 rounded toward minus infinity gives exactly
+// 2^23 + floor(x) (the spacing of floats in [2^23, 2^24) is 1), whose low
+// mantissa bits are floor(x): an FP32 add and a mask instead of a
+// float-to-integer conversion.
 __device__ __forceinline__ uint8_t srgb_u8(float v) {
-  return (uint8_t)__float2uint_rd(__fmaf_rn(v, 255.0f, 0.5f));
+  const float x = __fmaf_rn(v, 255.0f, 0.5f);
+  return (uint8_t)(__float_as_uint(__fadd_rd(x, 8388608.0f)) & 0xFFu);
 }
 
 __device__ __forceinline__ void xyz_to_srgb8(float X, float Y, float Z, uint8_t* out) {

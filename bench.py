@@ -237,6 +237,14 @@ def run_hsc(args, rank: int, world: int):
         if ev is not None:
             ev[1].record(stream)
 
+    def frame_on_current_stream(ev):
+        # the same calls on the capturing stream (the binding launches on torch's current stream)
+        cur = torch.cuda.current_stream()
+        hsc.hsc_encode_assets(ctx, Ed, mats, zm, spd, zl)
+        ev[0].record(cur)
+        hsc.hsc_shade_latent(ctx, g1, g2, zm, lights, zl, hsc.HSC_FUSED, lat, xyz_out=xyz, M_xyz=M, srgb8_out=rgb)
+        ev[1].record(cur)
+
     def timed(fn, steps, warmup, inner_events=False):
         """Per-iteration device times (ms) with an L2 flush before each."""
         for _ in range(warmup):
@@ -266,6 +274,18 @@ def run_hsc(args, rank: int, world: int):
         frame()
     torch.cuda.synchronize()
     hsc.hsc_sync(ctx)
+    # The frame's two API calls (tuned by the eager warm-up) are captured once
+    # in a CUDA graph and replayed every step: the same two kernels without
+    # the stream-launch gaps.  The shading launch is bracketed by timing
+    # events recorded inside the graph; the L2 flush and the step's own events
+    # stay outside it.
+    graph = make_frame_graph(torch, frame_on_current_stream, dev)
+    step_launch = "CUDA graph of the frame's API calls, replayed per step" if graph else "stream launches"
+    if graph is not None:
+        for _ in range(args.warmup):
+            l2_flush()
+            graph[0].replay()
+        torch.cuda.synchronize()
     clocks = ClockSampler(dev.index) if rank == 0 else None
     if world > 1:
         dist.barrier()
@@ -274,7 +294,10 @@ def run_hsc(args, rank: int, world: int):
         clocks.start()
         time.sleep(0.3)
     wall0 = time.perf_counter()
-    per_step, shade_ms = timed(frame, args.steps, 0, inner_events=True)
+    if graph is not None:
+        per_step, shade_ms = timed_graph(graph, args.steps, l2_flush, stream)
+    else:
+        per_step, shade_ms = timed(frame, args.steps, 0, inner_events=True)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -333,7 +356,7 @@ def run_hsc(args, rank: int, world: int):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded G-buffers, spectra, lights)",
             "config": {"workload": WORKLOAD, "pixels": f.pixels, "lights": f.lights, "k": k, "n": 81,
                        "evals_per_step": evals, "l2": "flushed before every timed step (256 MB write, then 256 MB read so its writebacks fall outside the timed region)",
-                       "parallelism": f"replicas x{world}"},
+                       "launch": step_launch, "parallelism": f"replicas x{world}"},
             "frame_ms": {"p50": _pct(per_step, 50), "p99": _pct(per_step, 99), "min": min(per_step)},
             "gpu_launches": gpu_launches_per_step * args.steps,
             "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "rows": rows, "autotune": tune,
@@ -411,6 +434,46 @@ TRAFFIC_SOURCES = ("paper_2602_18741_gb300/csrc/shade_latent_kernel.cuh",
                    "paper_2602_18741_gb300/csrc/shade_latent.cuh",
                    "paper_2602_18741_gb300/csrc/common.cuh",
                    "paper_2602_18741_gb300/csrc/shade_latent_k6.cu")
+
+
+def make_frame_graph(torch, frame_fn, dev):
+    """Captures frame_fn(events) once in a CUDA graph on a side stream.
+    Returns (graph, (ev_before_shade, ev_after_shade)), the events recorded
+    inside the graph as timing nodes, or None where this PyTorch cannot
+    record timing events inside a graph (the step then launches on the
+    stream)."""
+    try:
+        evs = (torch.cuda.Event(enable_timing=True, external=True),
+               torch.cuda.Event(enable_timing=True, external=True))
+    except TypeError:
+        return None
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            frame_fn(evs)
+    torch.cuda.synchronize(dev)
+    return g, evs
+
+
+def timed_graph(graph, steps, l2_flush, stream):
+    """Per-step device times (ms) of graph replays with an L2 flush before
+    each, and the shading launch's time from the events inside the graph
+    (read after each replay, before the next one records them again)."""
+    import torch
+    g, (e0, e1) = graph
+    outer, inner = [], []
+    for _ in range(steps):
+        l2_flush()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.replay()
+        b.record(stream)
+        b.synchronize()
+        outer.append(a.elapsed_time(b))
+        inner.append(e0.elapsed_time(e1))
+    return outer, inner
 
 
 def kernel_source_hash() -> str:

@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--rows-only", default="",
                     help="comma list of secondary row groups to run: core, precision, small, batch, chains, "
                          "upsample, pathtrace, sweep, serve (default: all)")
+    ap.add_argument("--step-launch", choices=("graph", "stream"), default="graph",
+                    help="the timed frame step as a CUDA graph of its API calls (default) or as stream launches")
     ap.add_argument("--sweep-epochs", type=int, default=150,
                     help="epoch cap of the 700-variant codec sweep (0 = skip the sweep row)")
     return ap.parse_args()
@@ -279,7 +281,7 @@ def run_hsc(args, rank: int, world: int):
     # the stream-launch gaps.  The shading launch is bracketed by timing
     # events recorded inside the graph; the L2 flush and the step's own events
     # stay outside it.
-    graph = make_frame_graph(torch, frame_on_current_stream, dev)
+    graph = make_frame_graph(torch, frame_on_current_stream, dev) if args.step_launch == "graph" else None
     step_launch = "CUDA graph of the frame's API calls, replayed per step" if graph else "stream launches"
     if graph is not None:
         for _ in range(args.warmup):
@@ -303,6 +305,11 @@ def run_hsc(args, rank: int, world: int):
         dist.barrier()
     wall = time.perf_counter() - wall0
     hsc.hsc_sync(ctx)
+    if graph is not None:
+        # the step's graph is freed before the secondary rows
+        graph[0].reset()
+        graph = None
+        torch.cuda.synchronize()
     total_ms = max_over_ranks(sum(per_step), world, dev)
     ms_per_step = total_ms / args.steps
     value = whole_job_rate(evals * args.steps, world, total_ms)
@@ -783,14 +790,16 @@ def group_rows(args, hsc, ctx, dev, timed, before_serve=None):
     return rows
 
 
-def small_frame_rows(args, hsc, ctx, dev, replays: int = 200):
+def small_frame_rows(args, hsc, ctx, dev, replays: int = 20, frames_per_graph: int = 10):
     """The 256x256 frame (n = 31, k = 6, 4 lights, direct only): launch
     bound, so the latent frame (one encode launch for materials and lights
     + fused shade with XYZ), the
     latent shade alone (assets already encoded), the latent frame with the
     encode inside the shading launch (hsc_shade_latent_assets) and the
-    spectral frame are each captured once in a CUDA graph and replayed back
-    to back; microseconds per frame (inputs of ~4 MB stay in L2)."""
+    spectral frame are each captured in a CUDA graph of `frames_per_graph`
+    frames, replayed back to back (the host's cost per replay is spread over
+    the frames, so the device's time per frame is what is measured);
+    microseconds per frame (inputs of ~4 MB stay in L2)."""
     import torch
     f = hi.frame_config1()
     E, D = hi.load_codec(6, 31)
@@ -838,7 +847,8 @@ def small_frame_rows(args, hsc, ctx, dev, replays: int = 200):
         side.wait_stream(torch.cuda.current_stream(dev))
         with torch.cuda.stream(side):
             with torch.cuda.graph(g, stream=side):
-                fn()
+                for _ in range(frames_per_graph):
+                    fn()
         torch.cuda.synchronize(dev)
         for _ in range(3):
             g.replay()
@@ -849,9 +859,10 @@ def small_frame_rows(args, hsc, ctx, dev, replays: int = 200):
         b.record()
         b.synchronize()
         hsc.hsc_sync(ctx)
-        us = a.elapsed_time(b) * 1e3 / replays
+        us = a.elapsed_time(b) * 1e3 / (replays * frames_per_graph)
         out[name] = {"us_per_frame": us, "evals_per_s": f.evals / (us * 1e-6)}
     return {"small_frame_256x256_graph": {"frame": "256x256, n = 31, 4 lights, direct only", "replays": replays,
+                                          "frames_per_graph": frames_per_graph,
                                           "evals": f.evals, **out,
                                           "speedup_latent_vs_spectral":
                                               out["spectral_n31"]["us_per_frame"] / out["latent_k6"]["us_per_frame"],

@@ -287,6 +287,11 @@ class ResidentScenes:
         return g1, lights, zm, zl[:req.lights], self.M[(req.k, req.n)]
 
 
+def _ceil_log2(v: int) -> int:
+    """The smallest b with 2^b >= v (the tuner's bucket of a count)."""
+    return max(0, (int(v) - 1).bit_length())
+
+
 class GpuBackend:
     """Launches admitted requests on the GPU.  mode 'latent': one batched
     launch per admitted group (hsc_shade_frames); mode 'spectral': one
@@ -326,6 +331,15 @@ class GpuBackend:
             lo, hi = firsts.get((r.k, r.n), (r, r))
             firsts[(r.k, r.n)] = (r if r.lights < lo.lights else lo, r if r.lights > hi.lights else hi)
         warm = {id(x): x for pair in firsts.values() for x in pair}
+        # the spectral launch is tuned per shape class (light and pixel counts
+        # rounded up to powers of two) on the class's first call, which times
+        # every candidate and waits for the device: one request of every class
+        # in the stream runs here, so that no tuning happens in the loop
+        classes = {}
+        for r in requests:
+            classes.setdefault((r.k, r.n, _ceil_log2(r.lights), _ceil_log2(r.width * r.height)), r)
+        for r in classes.values():
+            warm[id(r)] = r
         handles = [self.launch([r]) for r in warm.values()]
         torch.cuda.synchronize(self.sc.dev)
         for _, outs in handles:

@@ -292,6 +292,33 @@ def _ceil_log2(v: int) -> int:
     return max(0, (int(v) - 1).bit_length())
 
 
+def tuning_class(r) -> tuple:
+    """The shape class a request's launch is tuned for: code length, sample
+    count, and the light and pixel counts rounded up to powers of two."""
+    return (r.k, r.n, _ceil_log2(r.lights), _ceil_log2(r.width * r.height))
+
+
+def warmup_requests(requests) -> list:
+    """The requests the warm-up runs before the first arrival, each once.
+    The first launch of a kernel loads its code, which can wait for the
+    device; kernels are specialised by light count too (all lights in one
+    shared-memory stage or not), so each (k, n) runs with its fewest and its
+    most lights.  The spectral launch is tuned on the first call of each
+    shape class, which times every candidate and waits for the device, so
+    one request of every class in the stream runs as well."""
+    firsts = {}
+    for r in requests:
+        lo, hi = firsts.get((r.k, r.n), (r, r))
+        firsts[(r.k, r.n)] = (r if r.lights < lo.lights else lo, r if r.lights > hi.lights else hi)
+    warm = {id(x): x for pair in firsts.values() for x in pair}
+    classes = {}
+    for r in requests:
+        classes.setdefault(tuning_class(r), r)
+    for r in classes.values():
+        warm[id(r)] = r
+    return list(warm.values())
+
+
 class GpuBackend:
     """Launches admitted requests on the GPU.  mode 'latent': one batched
     launch per admitted group (hsc_shade_frames); mode 'spectral': one
@@ -322,25 +349,7 @@ class GpuBackend:
         import torch
         if self.mode == "latent":
             self.hsc.hsc_shade_frames(self.ctx, [], stream=self.streams[0])   # allocates the descriptor ring
-        # the first launch of a kernel loads its code, which can wait for the
-        # device as well.  Kernels are specialised by light count too (all
-        # lights in one shared-memory stage or not), so each (k, n) runs with
-        # its fewest and its most lights
-        firsts = {}
-        for r in requests:
-            lo, hi = firsts.get((r.k, r.n), (r, r))
-            firsts[(r.k, r.n)] = (r if r.lights < lo.lights else lo, r if r.lights > hi.lights else hi)
-        warm = {id(x): x for pair in firsts.values() for x in pair}
-        # the spectral launch is tuned per shape class (light and pixel counts
-        # rounded up to powers of two) on the class's first call, which times
-        # every candidate and waits for the device: one request of every class
-        # in the stream runs here, so that no tuning happens in the loop
-        classes = {}
-        for r in requests:
-            classes.setdefault((r.k, r.n, _ceil_log2(r.lights), _ceil_log2(r.width * r.height)), r)
-        for r in classes.values():
-            warm[id(r)] = r
-        handles = [self.launch([r]) for r in warm.values()]
+        handles = [self.launch([r]) for r in warmup_requests(requests)]
         torch.cuda.synchronize(self.sc.dev)
         for _, outs in handles:
             if self.keep:   # warm-up outputs are not the caller's

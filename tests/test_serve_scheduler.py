@@ -129,3 +129,22 @@ def test_host_usage_counters():
     d = _serve.usage_delta(u0, _serve.host_usage())
     assert d["cpu_s"] >= 0.0 and d["nivcsw"] >= 0.0 and d["nvcsw"] >= 0.0
     assert set(u0) >= {"cpu_s", "nvcsw", "nivcsw"}
+
+
+def test_tuning_bucket_is_the_smallest_covering_power_of_two():
+    for v in list(range(1, 5000)) + [2 ** 21 - 1, 2 ** 21, 2 ** 21 + 1, 3840 * 2160]:
+        b = _serve._ceil_log2(v)
+        assert 2 ** b >= v and (b == 0 or 2 ** (b - 1) < v), v
+
+
+def test_warmup_covers_every_tuning_class_and_light_extreme():
+    reqs = hi.request_stream(seed=11, rate_hz=400.0, duration_s=5.0)
+    warm = _serve.warmup_requests(reqs)
+    assert len({id(r) for r in warm}) == len(warm)          # each request once
+    assert {_serve.tuning_class(r) for r in warm} == {_serve.tuning_class(r) for r in reqs}
+    for kn in {(r.k, r.n) for r in reqs}:
+        lights = [r.lights for r in reqs if (r.k, r.n) == kn]
+        got = [r.lights for r in warm if (r.k, r.n) == kn]
+        assert min(lights) in got and max(lights) in got
+    # a class is warmed by one of its own requests
+    assert all(r in reqs for r in warm)

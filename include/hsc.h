@@ -134,7 +134,9 @@ HSC_API size_t hsc_shade_latent_scratch_bytes(int64_t pixels, int k, hsc_mode mo
  * (kernel, channels, bounce on/off, light and pixel counts rounded up to
  * powers of two) times every candidate on its own inputs -- synchronising
  * the stream once -- and caches the fastest; calls made while a stream is
- * captured never tune.                                                      */
+ * captured never tune.  A latency-bound caller (a serving loop) runs one
+ * call of every shape class it will meet before its first deadline, or
+ * loads a saved table with hsc_tune_load, so that no call tunes later.      */
 HSC_API hsc_status hsc_set_autotune(hsc_ctx* ctx, int enable);
 /* Text table of the tuned shape classes and candidate timings (valid until
  * the next tuning call on this context).                                   */
